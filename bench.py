@@ -1,0 +1,358 @@
+#!/usr/bin/env python3
+"""Throughput of the GB300 norm-1 ADMM on the CRA-shaped imaging workload.
+
+Workload: H = 1440 x 32768 complex64 (40 frequencies x 36 receivers, 32^3
+voxels), a three-plate scene at 30 dB, lambda = 0.05 max|H^H g|, rho = 8 max_j
+||H_j||^2 (the column-split rule), solved in all three splits of the paper:
+consensus 8x1, sectioning 1x8, consensus-and-sectioning 4x4.  One step = one
+ADMM iteration of each split (three launches of the persistent iteration
+kernel).  H (377 MB per split) is larger than L2, so no flush is needed
+between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank solves its own scene (weak scaling, no
+collective on the data path; a barrier and a max-reduction of the timings
+only).  Rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import csv
+import io
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADMM iters/s & HBM GB/s vs roofline; time to 1e-4 rel. err, chosen vs plain"
+UNIT = "iters/s"
+SPLITS = ((8, 1), (1, 8), (4, 4))
+M_ROWS, N_COLS = 1440, 32768
+WORKLOAD = ("CRA-shaped imaging, H 1440x32768 complex64 (40 freqs x 36 rx, 32^3 voxels), "
+            "one iteration of each split 8x1 / 1x8 / 4x4 per step")
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--cpu-iters", type=int, default=4,
+                    help="iterations per split in the bounded CPU-oracle sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args(argv)
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def make_problem(rank: int):
+    import synth
+    H = synth.cra_matrix(seed=1)
+    return synth.cra_problem(H=H, scene_seed=2 + rank)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.QUERY}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [r for r in csv.reader(io.StringIO(self.file.read())) if len(r) >= 9]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, r[5:9]):
+                if val.strip().lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_iteration_seconds(p, iters: int, warmup: int) -> dict:
+    """Per-split seconds per oracle iteration: (T(iters) - T(0)) / iters, so
+    the one-time factorisation of each call is not charged to the iterations."""
+    import oracle
+    out = {}
+    for M, N in SPLITS:
+        if warmup:
+            oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, warmup)
+        t0 = time.perf_counter()
+        oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, 0)
+        t_setup = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, iters)
+        t_run = time.perf_counter() - t0
+        out[f"{M}x{N}"] = max(t_run - t_setup, 1e-9) / iters
+    return out
+
+
+def cpu_sample_worker(args) -> None:
+    p = make_problem(0)
+    per = oracle_iteration_seconds(p, args.cpu_iters, 0)
+    print(json.dumps({"per_iter_s": per, "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))}))
+
+
+def cpu_baseline(iters: int) -> dict:
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for key in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[key] = str(cores)
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    res = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample-worker",
+                          "--cpu-iters", str(iters)], env=env, capture_output=True, text=True,
+                         timeout=900)
+    if res.returncode != 0:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": f"failed: {res.stderr.strip()[-200:]}"}
+    d = json.loads(res.stdout.strip().splitlines()[-1])
+    total = sum(d["per_iter_s"].values())
+    return {"value": len(SPLITS) / total, "unit": UNIT, "cores": d["cores"], "kind": "oracle",
+            "sample": (f"{iters} FP64 oracle iterations of each split 8x1/1x8/4x4 on the full "
+                       f"1440x32768 CRA workload, factorisation excluded; numpy/OpenBLAS with "
+                       f"{d['cores']} threads"),
+            "per_iter_s": d["per_iter_s"]}
+
+
+def run_reference(args) -> None:
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    p = make_problem(0)
+    per = oracle_iteration_seconds(p, max(args.steps, 1), args.warmup)
+    step_s = sum(per.values())
+    value = len(SPLITS) / step_s
+    cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS,
+                   "splits": [f"{M}x{N}" for M, N in SPLITS], "parallelism": "host cores"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": (f"{args.steps} FP64 oracle iterations of each split after "
+                                    f"{args.warmup} warm-up, factorisation excluded")},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "splits": {k: {"iters_per_s": 1.0 / v} for k, v in per.items()},
+    }
+    print(json.dumps(line))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args) -> None:
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.cuda.current_device()
+
+    # CPU baseline first (spawned before any CUDA work of this process)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(args.cpu_iters)
+
+    import paper_1811_05571_gb300 as pkg
+    pkg.load()
+    p = make_problem(rank)
+    stream = torch.cuda.Stream()
+    H_d = torch.from_numpy(p.H_c64()).to(dev)
+    g_d = torch.from_numpy(p.g_c64()).to(dev)
+    torch.cuda.synchronize()
+    solvers = []
+    with torch.cuda.stream(stream):
+        for M, N in SPLITS:
+            solvers.append(pkg.Solver(H_d, g_d, M, N, p.lam, p.rho, stream=stream))
+    del H_d
+    torch.cuda.synchronize()
+    infos = [s.info() for s in solvers]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # warm-up
+    for _ in range(max(args.warmup, 0)):
+        for s in solvers:
+            s.iterate(1)
+    barrier()
+
+    K = args.steps
+    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(K)] for _ in solvers]
+    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    barrier()
+    t_start.record(stream)
+    for k in range(K):
+        for si, s in enumerate(solvers):
+            ev[si][k][0].record(stream)
+            s.iterate(1)
+            ev[si][k][1].record(stream)
+    t_end.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_s = t_start.elapsed_time(t_end) / 1e3
+    split_s = [sum(ev[si][k][0].elapsed_time(ev[si][k][1]) for k in range(K)) / 1e3
+               for si in range(len(solvers))]
+    for s in solvers:
+        st = s.status()
+        if st != 0:
+            raise RuntimeError(f"device status {st} after the timed region")
+    if world > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+
+    # end to end through the public API with host buffers: per step and split,
+    # set_g from pinned host memory, one iteration, the image back to pinned memory
+    g_host = torch.from_numpy(p.g_c64()).pin_memory()
+    v_host = [torch.empty(N_COLS, dtype=torch.complex64).pin_memory() for _ in solvers]
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for k in range(K):
+        for si, s in enumerate(solvers):
+            s.set_g(g_host)
+            s.iterate(1)
+            s.v(out=v_host[si])
+    e1.record(stream)
+    barrier()
+    e2e_s = e0.elapsed_time(e1) / 1e3
+    if world > 1:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+
+    peaks = load_peaks()
+    per_split = {}
+    bytes_total, time_total = 0.0, 0.0
+    for (M, N), info, ts in zip(SPLITS, infos, split_s):
+        # algorithmic bytes of one iteration: two passes over H, one read of
+        # every cached factor, and the state vectors read and written once
+        alg = 2 * info["h_bytes"] + info["factor_bytes"] + (2 * M + 2) * N_COLS * 8
+        per_split[f"{M}x{N}"] = {
+            "iters_per_s": K / ts, "us_per_iter": ts / K * 1e6,
+            "alg_bytes_per_iter": alg, "gbs": alg * K / ts / 1e9,
+            "frac": alg * K / ts / 1e9 / peaks["hbm_gbs"],
+            "ctas": info["ctas"], "rows_per_stage": info["rows_per_stage"],
+            "stages": info["stages"],
+            "setup_ms": {"gram": info["setup_gram_ms"], "cholesky_inverse": info["setup_factor_ms"]},
+        }
+        bytes_total += alg * K
+        time_total += ts
+    achieved = bytes_total / time_total / 1e9
+    value = world * len(SPLITS) * K / total_s
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": args.warmup, "ms_per_step": total_s / K * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS,
+                   "splits": [f"{M}x{N}" for M, N in SPLITS],
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "lambda": p.lam, "rho": p.rho,
+                   "l2": "inputs larger than L2 (H 377 MB per split vs 129 MB L2), no flush"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                     "peak_source": peaks["source"], "kernel": "admm::iterate_kernel"},
+        "e2e": {"value": world * len(SPLITS) * K / e2e_s, "unit": UNIT,
+                "h2d_bytes_per_step": len(SPLITS) * M_ROWS * 8,
+                "d2h_bytes_per_step": len(SPLITS) * N_COLS * 8},
+        "gpu_launches": len(SPLITS) * K,
+        "clocks": clk,
+        "splits": per_split,
+    }
+    if cpu is not None:
+        line["cpu_baseline"] = cpu
+    for s in solvers:
+        s.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def main(argv=None) -> int:
+    args = parse_args(argv)
+    if args.cpu_sample_worker:
+        cpu_sample_worker(args)
+        return 0
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,241 @@
+/*
+ * admm.h -- C ABI of libadmm.so, a GB300 (sm_103a) implementation of the
+ * norm-1 regularised ADMM of Heredia-Juesas, Molaei, Tirado and
+ * Martinez-Lorenzo, "Consensus and Sectioning-based ADMM with Norm-1
+ * Regularization for Imaging with a Compressive Reflector Antenna".
+ *
+ * The library solves   minimize 1/2 ||H u - g||_2^2 + lambda ||u||_1
+ * over u in C^n (Section III, Eq. original; g = Hu + w of Eq. 2), with H in
+ * C^{m x n} split into row_blocks x col_blocks contiguous blocks:
+ *
+ *   row_blocks = M, col_blocks = 1 : consensus ADMM       (Section III-A)
+ *   row_blocks = 1, col_blocks = N : sectioning ADMM      (Section III-B)
+ *   row_blocks = M, col_blocks = N : consensus and sectioning ADMM
+ *                                                          (Section III-C)
+ *   row_blocks = col_blocks = 1    : the unsplit lasso ADMM of Section III
+ *
+ * Conventions for every call:
+ *  - Complex data is interleaved (re, im): complex64 = two floats,
+ *    complex128 = two doubles, i.e. C99 float/double _Complex and the
+ *    contiguous layout of torch.complex64 / numpy.complex64.
+ *  - Matrices are row-major and contiguous.
+ *  - A "buffer" argument may point to device memory or to host memory; the
+ *    library copies with cudaMemcpyDefault (unified addressing).  Pinned host
+ *    memory keeps the copy asynchronous; pageable host memory makes it
+ *    synchronous.  The caller keeps ownership of every buffer it passes and
+ *    the library never frees caller memory.  The library owns what it
+ *    allocates in admm_setup (the packed H, the cached factors and the
+ *    iteration state) until admm_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are asynchronous with respect to the host unless their
+ *    comment says they synchronise.
+ *  - Every function returns an admm status code (0 = ADMM_OK) unless noted;
+ *    admm_last_error(h) then holds a one-line description.  A failed call
+ *    leaves the handle usable unless it returned ADMM_ETIMEOUT or
+ *    ADMM_ECUDA, after which only admm_reset, the getters and admm_destroy
+ *    are accepted.
+ *  - Blocks are contiguous and balanced: the first (m mod M) row blocks get
+ *    one extra row, the first (n mod N) column blocks one extra column (the
+ *    paper assumes exact division, Sections III-A..C).
+ */
+#ifndef ADMM_H
+#define ADMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ADMM_ABI_VERSION 1
+
+/* status codes */
+#define ADMM_OK            0  /* success */
+#define ADMM_EINVAL        1  /* invalid argument: null pointer, size, split, lambda < 0, rho <= 0 */
+#define ADMM_ENOMEM        2  /* a device allocation failed */
+#define ADMM_ECUDA         3  /* a CUDA runtime call or launch failed */
+#define ADMM_ENOTPD        4  /* a factor rho I + H_b H_b^H was not positive definite in FP64 */
+#define ADMM_ENONFINITE    5  /* H or g holds NaN or Inf */
+#define ADMM_ETIMEOUT      6  /* a bounded in-kernel wait expired; the iteration state is undefined */
+#define ADMM_EUNSUPPORTED  7  /* a valid problem this build does not run (see admm_setup) */
+#define ADMM_EDIVERGED     8  /* the iterates became NaN or Inf */
+
+/* element type of H and g in admm_setup / admm_set_g */
+#define ADMM_C64   0          /* complex64: two floats per element */
+#define ADMM_C128  1          /* complex128: two doubles, rounded to complex64 on the device */
+
+/* options for admm_set_option */
+#define ADMM_OPT_TIMEOUT_NS    1  /* bound of every in-kernel wait, nanoseconds (default 5e9) */
+#define ADMM_OPT_HIST_CAP      2  /* residual-history ring capacity, records (default 4096); resets the history */
+#define ADMM_OPT_BARRIER_EXTRA 3  /* fault injection: make every grid barrier wait for this many
+                                     CTAs that do not exist, so the bounded wait expires and the
+                                     call ends with ADMM_ETIMEOUT (0 = off, the default) */
+
+typedef struct admm_problem admm_t;
+
+/* Sizes and plan of a handle (admm_get_info). */
+typedef struct admm_info {
+    int64_t m, n;             /* problem size */
+    int64_t ld;               /* row pitch of the packed device copy of H, complex elements */
+    int32_t row_blocks, col_blocks;
+    double lambda, rho, kappa;  /* kappa = lambda / (row_blocks * rho), the shrinkage threshold */
+    int64_t iterations;       /* iterations completed since setup / reset */
+    int32_t ctas;             /* CTAs of the persistent iteration kernel (one per SM at most) */
+    int32_t rows_per_stage;   /* rows of H per pipeline stage */
+    int32_t stages;           /* depth of the TMA pipeline */
+    int32_t slab_cols;        /* widest column slab owned by one CTA */
+    int32_t smem_bytes;       /* dynamic shared memory of the iteration kernel */
+    int32_t num_sms;
+    int64_t h_bytes;          /* bytes of H streamed by one pass (m * n * 8) */
+    int64_t factor_bytes;     /* bytes of all cached factors (complex64) */
+    int64_t state_bytes;      /* bytes of v, s, u, estimated data and scratch */
+    double setup_gram_ms;     /* device time of the Gram products */
+    double setup_factor_ms;   /* device time of the FP64 Cholesky and inverse */
+} admm_info_t;
+
+/* Launch plan of the iteration kernel, computed on the host (admm_plan). */
+typedef struct admm_plan {
+    int32_t ctas;             /* CTAs (column slabs) */
+    int32_t slab_cols;        /* widest slab, columns (even) */
+    int32_t chunks;           /* 32-pair chunks per lane (template width) */
+    int32_t box_cols;         /* TMA box width, columns */
+    int32_t boxes_per_row;    /* TMA boxes covering one slab row */
+    int32_t rows_per_stage;   /* TMA box height */
+    int32_t stages;           /* pipeline depth */
+    int32_t smem_bytes;       /* dynamic shared memory */
+    int32_t max_blocks_per_slab; /* most column blocks one slab intersects */
+    int64_t ld;               /* padded row pitch, complex elements */
+} admm_plan_t;
+
+/* ABI version of the loaded library (ADMM_ABI_VERSION at build time). */
+int admm_abi_version(void);
+
+/* Static text for a status code.  Never NULL. */
+const char* admm_strerror(int status);
+
+/* Description of the last failure on `h` (or of the last failed admm_setup
+ * when h is NULL).  The string lives until the next call on the handle. */
+const char* admm_last_error(const admm_t* h);
+
+/* Contiguous balanced blocks (the partition used by every split): writes
+ * parts+1 offsets, offsets[0] = 0, offsets[parts] = total, sizes differing by
+ * at most one with the larger blocks first.  Host only, no GPU needed.
+ * ADMM_EINVAL unless 1 <= parts <= total and offsets != NULL. */
+int admm_partition(int64_t total, int32_t parts, int64_t* offsets);
+
+/* Plan of the persistent iteration kernel for an m x n problem split into
+ * row_blocks x col_blocks on a GPU with `num_sms` SMs and `smem_limit` bytes of
+ * opt-in shared memory per block.  Host only, no GPU needed.  When
+ * cta_cols != NULL it receives ctas+1 slab offsets (columns, even, the last
+ * one equal to plan->ld); the buffer must hold num_sms+1 entries.
+ * ADMM_EINVAL for bad sizes, ADMM_EUNSUPPORTED when the slab or the shared
+ * memory needs exceed what the kernel supports. */
+int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks,
+              int32_t num_sms, int32_t smem_limit, admm_plan_t* plan, int32_t* cta_cols);
+
+/* Create a solver for g = Hu + w (Eq. 2) under the split (row_blocks,
+ * col_blocks), with regularisation weight `lambda` >= 0 and augmented
+ * parameter `rho` > 0 (Section II).  Copies H (m x n) and g (m) -- host or
+ * device buffers of element type h_dtype -- into library-owned device memory,
+ * forms every Gram block H_b H_b^H with FP32 products accumulated in FP64,
+ * and caches the inverse of K_b = rho I + H_b H_b^H computed from an FP64
+ * Cholesky factorisation, stored as complex64.  K_b^{-1} is rho times the
+ * (I + H_b H_b^H / rho)^{-1} of the inversion lemma, Eq. (inversion_lemma),
+ * (inversion_lemma2) and (inversion_lemma3).  The iteration state starts at
+ * v = s = u = 0 with zero estimated data.
+ * Requires 1 <= row_blocks <= m, 1 <= col_blocks <= n,
+ * row_blocks * col_blocks <= 256, and every block with fewer rows than
+ * columns (the lemma branch); a tall block returns ADMM_EUNSUPPORTED.
+ * Synchronises `stream`.  On success *out receives the handle; on failure
+ * *out is NULL and admm_last_error(NULL) describes the error. */
+int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
+               int32_t row_blocks, int32_t col_blocks, double lambda, double rho,
+               int32_t h_dtype, void* stream);
+
+/* Run `iters` >= 0 iterations, each the block update of Sections III-A..C:
+ *   z_b   = v_b - s_b
+ *   u_b   = (H_b^H H_b + rho I)^{-1} (H_b^H gt_b + rho z_b)
+ *           with gt_b = g_i - sum_{q != j} H_iq u_q^i of the previous iterate
+ *           (Eq. g_columns, g_rows_columns; gt_b = g_i for one column block),
+ *   v_j   = S_kappa(mean_i u_j^i + mean_i s_j^i), kappa = lambda/(M rho)
+ *           (Eq. v_variable, v_variable_columns, v_variable_rows_columns;
+ *           S is the complex soft-threshold of Eq. softhresholding),
+ *   s_b  += u_b - v_j,
+ * plus the FP64 squared residual norms of each iteration (the norms below
+ * Eq. inversion_lemma, inversion_lemma2 and inversion_lemma3).
+ * One persistent cooperative kernel runs all `iters` iterations.
+ * Asynchronous: errors of the in-kernel bounded waits (ADMM_ETIMEOUT) and
+ * divergence (ADMM_EDIVERGED) surface at the next synchronising call. */
+int admm_iterate(admm_t* h, int32_t iters, void* stream);
+
+/* Iterate until the primal and dual residuals meet the tolerances of Boyd et
+ * al. Section 3.3.1 (the reference the paper cites for its residuals):
+ *   ||r_p|| <= sqrt(p) eps_abs + eps_rel max(||u||, ||v||),
+ *   ||r_d|| <= sqrt(p) eps_abs + eps_rel rho ||s||,
+ * with p = row_blocks * n the stacked length and u, v, s stacked over the
+ * replicas, or until max_iter iterations.  The test runs on the device after
+ * every iteration.  Synchronises `stream`.  *iters_done (may be NULL)
+ * receives the iterations this call ran; the state is that after the last
+ * of them. */
+int admm_solve(admm_t* h, int32_t max_iter, double eps_abs, double eps_rel,
+               int32_t* iters_done, void* stream);
+
+/* Copy the image v (n complex64; Section III-C: v = [v_1; ...; v_N]) into `v`. */
+int admm_get_v(admm_t* h, void* v, void* stream);
+
+/* Copy the replicas u^i of the last iteration (row_blocks x n complex64,
+ * replica-major) into `u`. */
+int admm_get_u(admm_t* h, void* u, void* stream);
+
+/* Copy up to `cap` per-iteration records into `out` (5 doubles each: ||r_p||^2,
+ * ||r_d||^2, ||u||^2, ||v||^2, ||s||^2 with u, v, s stacked over the replicas),
+ * oldest first, ending with the last completed iteration; *count receives the
+ * number written.  Synchronises `stream` and returns the sticky device status
+ * (ADMM_ETIMEOUT / ADMM_EDIVERGED) if one was raised. */
+int admm_get_residuals(admm_t* h, double* out, int32_t cap, int32_t* count, void* stream);
+
+/* Replace the data vector g (m elements of type h_dtype) -- a new scene for
+ * the same H; no refactorisation.  The iteration state is kept (call
+ * admm_reset for a cold start). */
+int admm_set_g(admm_t* h, const void* g, int32_t h_dtype, void* stream);
+
+/* Replace lambda >= 0 (no refactorisation; kappa = lambda/(M rho)). */
+int admm_set_lambda(admm_t* h, double lambda);
+
+/* Replace rho > 0: recomputes every cached factor rho I + H_b H_b^H and
+ * rescales the scaled duals s by rho_old/rho_new so the unscaled duals are
+ * unchanged.  Synchronises `stream`. */
+int admm_set_rho(admm_t* h, double rho, void* stream);
+
+/* Zero the iteration state (v = s = u = 0, estimated data 0), the
+ * residual history and the iteration count; clears a sticky device error. */
+int admm_reset(admm_t* h, void* stream);
+
+/* Checkpoint: copy the iteration count and the state (v: n, s: row_blocks x
+ * n, estimated data: col_blocks x m, all complex64) into caller buffers.
+ * Any buffer may be NULL to skip it.  Synchronises `stream`. */
+int admm_get_state(admm_t* h, int64_t* k, void* v, void* s, void* ghat, void* stream);
+
+/* Restore a checkpoint written by admm_get_state (same layouts); the next
+ * iteration continues exactly as the uninterrupted run would.  `ghat` may be
+ * NULL only when col_blocks == 1. */
+int admm_set_state(admm_t* h, int64_t k, const void* v, const void* s, const void* ghat,
+                   void* stream);
+
+/* Fill *info with the sizes and the kernel plan of `h`. */
+int admm_get_info(const admm_t* h, admm_info_t* info);
+
+/* Set an ADMM_OPT_* option. */
+int admm_set_option(admm_t* h, int32_t option, int64_t value);
+
+/* Synchronise `stream` and return the sticky device status of `h`. */
+int admm_status(admm_t* h, void* stream);
+
+/* Free everything the handle owns.  NULL is accepted. */
+void admm_destroy(admm_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADMM_H */

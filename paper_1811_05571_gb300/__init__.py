@@ -1,0 +1,21 @@
+"""GB300 (sm_103a) norm-1 ADMM for g = Hu + w in its consensus, sectioning and
+consensus-and-sectioning forms (Heredia-Juesas et al., Sections III-A..C).
+
+The numerical work lives in the CUDA library ``libadmm.so`` (C ABI in
+``include/admm.h``); this package only builds it, loads it and marshals
+arguments.  Importing is cheap; the library is loaded (and built from
+``csrc/`` when a source is newer than the binary) on first use, and any
+failure to build or load raises instead of falling back to other code.
+"""
+
+from ._binding import (  # noqa: F401
+    ADMM_C64, ADMM_C128, ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ENOTPD,
+    ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED,
+    ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA,
+    AdmmError, load, library_path,
+    admm_abi_version, admm_strerror, admm_partition, admm_plan, admm_setup, admm_iterate,
+    admm_solve, admm_get_v, admm_get_u, admm_get_residuals, admm_set_g, admm_set_lambda,
+    admm_set_rho, admm_reset, admm_get_state, admm_set_state, admm_get_info, admm_set_option,
+    admm_status, admm_destroy,
+)
+from .solver import Solver  # noqa: F401

@@ -1,0 +1,251 @@
+"""ctypes binding of libadmm.so: one Python function per C-ABI entry point.
+
+Argument marshalling only: buffers (torch tensors, numpy arrays or raw
+integer addresses) become pointers, sizes become int64, the stream becomes a
+cudaStream_t.  Every numerical step runs inside the CUDA library; nothing here
+computes.  A non-zero status raises ``AdmmError`` carrying the library's
+message.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import build as _build
+
+c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+
+ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ENOTPD = 0, 1, 2, 3, 4
+ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED = 5, 6, 7, 8
+ADMM_C64, ADMM_C128 = 0, 1
+ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA = 1, 2, 3
+
+
+class AdmmInfo(ctypes.Structure):
+    _fields_ = [("m", c_int64), ("n", c_int64), ("ld", c_int64),
+                ("row_blocks", c_int32), ("col_blocks", c_int32),
+                ("lambda_", c_double), ("rho", c_double), ("kappa", c_double),
+                ("iterations", c_int64), ("ctas", c_int32), ("rows_per_stage", c_int32),
+                ("stages", c_int32), ("slab_cols", c_int32), ("smem_bytes", c_int32),
+                ("num_sms", c_int32), ("h_bytes", c_int64), ("factor_bytes", c_int64),
+                ("state_bytes", c_int64), ("setup_gram_ms", c_double),
+                ("setup_factor_ms", c_double)]
+
+    def as_dict(self) -> dict:
+        return {name.rstrip("_"): getattr(self, name) for name, _ in self._fields_}
+
+
+class AdmmPlan(ctypes.Structure):
+    _fields_ = [("ctas", c_int32), ("slab_cols", c_int32), ("chunks", c_int32),
+                ("box_cols", c_int32), ("boxes_per_row", c_int32), ("rows_per_stage", c_int32),
+                ("stages", c_int32), ("smem_bytes", c_int32), ("max_blocks_per_slab", c_int32),
+                ("ld", c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class AdmmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"[{status}] {message}")
+        self.status = status
+
+
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "admm_abi_version": (c_int32, []),
+    "admm_strerror": (ctypes.c_char_p, [c_int32]),
+    "admm_last_error": (ctypes.c_char_p, [c_void_p]),
+    "admm_partition": (c_int32, [c_int64, c_int32, ctypes.POINTER(c_int64)]),
+    "admm_plan": (c_int32, [c_int64, c_int64, c_int32, c_int32, c_int32, c_int32,
+                            ctypes.POINTER(AdmmPlan), ctypes.POINTER(c_int32)]),
+    "admm_setup": (c_int32, [ctypes.POINTER(c_void_p), c_void_p, c_void_p, c_int64, c_int64,
+                             c_int32, c_int32, c_double, c_double, c_int32, c_void_p]),
+    "admm_iterate": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "admm_solve": (c_int32, [c_void_p, c_int32, c_double, c_double, ctypes.POINTER(c_int32),
+                             c_void_p]),
+    "admm_get_v": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "admm_get_u": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "admm_get_residuals": (c_int32, [c_void_p, ctypes.POINTER(c_double), c_int32,
+                                     ctypes.POINTER(c_int32), c_void_p]),
+    "admm_set_g": (c_int32, [c_void_p, c_void_p, c_int32, c_void_p]),
+    "admm_set_lambda": (c_int32, [c_void_p, c_double]),
+    "admm_set_rho": (c_int32, [c_void_p, c_double, c_void_p]),
+    "admm_reset": (c_int32, [c_void_p, c_void_p]),
+    "admm_get_state": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_void_p, c_void_p, c_void_p,
+                                 c_void_p]),
+    "admm_set_state": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
+    "admm_get_info": (c_int32, [c_void_p, ctypes.POINTER(AdmmInfo)]),
+    "admm_set_option": (c_int32, [c_void_p, c_int32, c_int64]),
+    "admm_status": (c_int32, [c_void_p, c_void_p]),
+    "admm_destroy": (None, [c_void_p]),
+}
+
+_LIB = None
+
+
+def load(build_if_needed: bool = True) -> ctypes.CDLL:
+    """Load the in-tree libadmm.so (building it first when a source changed)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if build_if_needed:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"libadmm.so is missing at {_build.LIB}; run paper_1811_05571_gb300.build")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _LIB = lib
+    return lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _ptr(x) -> int | None:
+    """Address of a buffer: torch tensor / numpy array (contiguous) or an int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):           # torch.Tensor
+        if not x.is_contiguous():
+            raise ValueError("buffer must be contiguous")
+        return int(x.data_ptr())
+    if hasattr(x, "ctypes"):             # numpy.ndarray
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("buffer must be C-contiguous")
+        return int(x.ctypes.data)
+    raise TypeError(f"cannot take the address of {type(x)!r}")
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s
+    return int(s.cuda_stream)            # torch.cuda.Stream
+
+
+def _check(status: int, handle=None) -> None:
+    if status != ADMM_OK:
+        lib = load(False)
+        msg = lib.admm_last_error(handle)
+        raise AdmmError(status, (msg or lib.admm_strerror(status)).decode())
+
+
+# ---------------------------------------------------------------------------
+# one function per entry point
+# ---------------------------------------------------------------------------
+
+def admm_abi_version() -> int:
+    return load().admm_abi_version()
+
+
+def admm_strerror(status: int) -> str:
+    return load().admm_strerror(status).decode()
+
+
+def admm_partition(total: int, parts: int) -> list[int]:
+    off = (c_int64 * (parts + 1))()
+    _check(load().admm_partition(total, parts, off))
+    return list(off)
+
+
+def admm_plan(m: int, n: int, row_blocks: int, col_blocks: int, num_sms: int = 152,
+              smem_limit: int = 232448):
+    plan = AdmmPlan()
+    cols = (c_int32 * (num_sms + 1))()
+    _check(load().admm_plan(m, n, row_blocks, col_blocks, num_sms, smem_limit, ctypes.byref(plan),
+                            cols))
+    return plan.as_dict(), list(cols)[: plan.ctas + 1]
+
+
+def admm_setup(H, g, m: int, n: int, row_blocks: int, col_blocks: int, lam: float, rho: float,
+               h_dtype: int = ADMM_C64, stream=None) -> int:
+    h = c_void_p()
+    _check(load().admm_setup(ctypes.byref(h), _ptr(H), _ptr(g), m, n, row_blocks, col_blocks,
+                             lam, rho, h_dtype, _stream(stream)))
+    return h.value
+
+
+def admm_iterate(h: int, iters: int, stream=None) -> None:
+    _check(load().admm_iterate(h, iters, _stream(stream)), h)
+
+
+def admm_solve(h: int, max_iter: int, eps_abs: float, eps_rel: float, stream=None) -> int:
+    done = c_int32(0)
+    _check(load().admm_solve(h, max_iter, eps_abs, eps_rel, ctypes.byref(done), _stream(stream)), h)
+    return done.value
+
+
+def admm_get_v(h: int, v, stream=None) -> None:
+    _check(load().admm_get_v(h, _ptr(v), _stream(stream)), h)
+
+
+def admm_get_u(h: int, u, stream=None) -> None:
+    _check(load().admm_get_u(h, _ptr(u), _stream(stream)), h)
+
+
+def admm_get_residuals(h: int, cap: int, stream=None):
+    import numpy as np
+    out = np.zeros((max(cap, 1), 5), dtype=np.float64)
+    count = c_int32(0)
+    _check(load().admm_get_residuals(h, out.ctypes.data_as(ctypes.POINTER(c_double)), cap,
+                                     ctypes.byref(count), _stream(stream)), h)
+    return out[: count.value]
+
+
+def admm_set_g(h: int, g, h_dtype: int = ADMM_C64, stream=None) -> None:
+    _check(load().admm_set_g(h, _ptr(g), h_dtype, _stream(stream)), h)
+
+
+def admm_set_lambda(h: int, lam: float) -> None:
+    _check(load().admm_set_lambda(h, lam), h)
+
+
+def admm_set_rho(h: int, rho: float, stream=None) -> None:
+    _check(load().admm_set_rho(h, rho, _stream(stream)), h)
+
+
+def admm_reset(h: int, stream=None) -> None:
+    _check(load().admm_reset(h, _stream(stream)), h)
+
+
+def admm_get_state(h: int, v=None, s=None, ghat=None, stream=None) -> int:
+    k = c_int64(0)
+    _check(load().admm_get_state(h, ctypes.byref(k), _ptr(v), _ptr(s), _ptr(ghat),
+                                 _stream(stream)), h)
+    return k.value
+
+
+def admm_set_state(h: int, k: int, v, s, ghat=None, stream=None) -> None:
+    _check(load().admm_set_state(h, k, _ptr(v), _ptr(s), _ptr(ghat), _stream(stream)), h)
+
+
+def admm_get_info(h: int) -> dict:
+    info = AdmmInfo()
+    _check(load().admm_get_info(h, ctypes.byref(info)), h)
+    return info.as_dict()
+
+
+def admm_set_option(h: int, option: int, value: int) -> None:
+    _check(load().admm_set_option(h, option, value), h)
+
+
+def admm_status(h: int, stream=None) -> int:
+    return load().admm_status(h, _stream(stream))
+
+
+def admm_destroy(h: int) -> None:
+    if h:
+        load().admm_destroy(h)

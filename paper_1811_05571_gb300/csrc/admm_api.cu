@@ -1,0 +1,892 @@
+// Host side of libadmm.so: argument checks, the block partitioner, the launch
+// plan of the persistent iteration kernel, device memory, the factor cache
+// and the C ABI declared in include/admm.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include <cudaTypedefs.h>
+
+#include "admm_internal.h"
+
+using admm::Plan;
+
+namespace {
+
+thread_local std::string g_setup_error;
+
+int round_up(int64_t x, int64_t q) { return static_cast<int>((x + q - 1) / q * q); }
+
+}  // namespace
+
+struct admm_problem {
+    int device = 0;
+    int num_sms = 0;
+    int smem_optin = 0;
+    int64_t m = 0, n = 0;
+    int M = 1, N = 1;
+    double lambda = 0.0, rho = 1.0;
+    std::vector<int> row_off, col_off;
+    Plan plan;
+    // device memory owned by the handle
+    float2 *H = nullptr, *g = nullptr, *v = nullptr, *s = nullptr, *u = nullptr;
+    float2 *ghat = nullptr, *gt = nullptr, *r = nullptr, *w = nullptr, *part = nullptr;
+    float2* kinv = nullptr;
+    long long* kinv_off_d = nullptr;
+    int* ints_d = nullptr;  // all int tables in one allocation
+    int *row_off_d = nullptr, *col_off_d = nullptr, *cta_col_d = nullptr, *cta_jlo_d = nullptr,
+        *cta_nj_d = nullptr, *j_cta_lo_d = nullptr, *j_cta_hi_d = nullptr, *solve_lo_d = nullptr,
+        *kinv_pitch_d = nullptr;
+    double *res_part = nullptr, *hist = nullptr;
+    long long* k_done = nullptr;
+    unsigned* bar = nullptr;
+    int* status = nullptr;
+    int* stop_flag = nullptr;
+    CUtensorMap tmap;
+    std::vector<long long> kinv_off;
+    std::vector<int> kinv_pitch;
+    int64_t kinv_elems = 0;
+    int64_t state_bytes = 0;
+    long long timeout_ns = 5000000000LL;
+    int hist_cap = 4096;
+    int bar_extra = 0;
+    int64_t k = 0;       // iterations completed (host mirror)
+    int broken = 0;      // sticky error that blocks further iterations
+    double gram_ms = 0.0, factor_ms = 0.0;
+    std::string err;
+};
+
+namespace {
+
+int fail(admm_t* h, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (h) h->err = buf;
+    else g_setup_error = buf;
+    return code;
+}
+
+int cuda_fail(admm_t* h, cudaError_t e, const char* what) {
+    if (h) h->broken = 1;
+    return fail(h, ADMM_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(h, call)                                         \
+    do {                                                    \
+        cudaError_t e_ = (call);                            \
+        if (e_ != cudaSuccess) return cuda_fail(h, e_, #call); \
+    } while (0)
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+template <typename T>
+cudaError_t dalloc(T** p, size_t count) {
+    return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(count, 1) * sizeof(T));
+}
+
+void free_all(admm_t* h) {
+    void* ptrs[] = {h->H, h->g, h->v, h->s, h->u, h->ghat, h->gt, h->r, h->w, h->part, h->kinv,
+                    h->kinv_off_d, h->ints_d, h->res_part, h->hist, h->k_done, h->bar, h->status,
+                    h->stop_flag};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// partitioner and plan (host only)
+// ---------------------------------------------------------------------------
+
+namespace admm {
+
+void balanced_offsets(int64_t total, int parts, std::vector<int>& off) {
+    off.assign(parts + 1, 0);
+    const int64_t base = total / parts, extra = total % parts;
+    int64_t pos = 0;
+    for (int p = 0; p < parts; ++p) {
+        off[p] = static_cast<int>(pos);
+        pos += base + (p < extra ? 1 : 0);
+    }
+    off[parts] = static_cast<int>(pos);
+}
+
+int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_off,
+              const std::vector<int>& col_off, int num_sms, int smem_limit, Plan& pl,
+              const char** why) {
+    *why = "";
+    if (num_sms < 1 || smem_limit < 16384) {
+        *why = "bad device limits";
+        return ADMM_EINVAL;
+    }
+    pl = Plan();
+    pl.ld = round_up(n, 32);
+    const int pairs = pl.ld / 2;
+    pl.P = static_cast<int>(std::min<int64_t>(num_sms, std::max<int64_t>(1, pl.ld / 64)));
+    // column slabs: balanced in 16-byte pairs
+    std::vector<int> poff;
+    balanced_offsets(pairs, pl.P, poff);
+    pl.cta_col.resize(pl.P + 1);
+    for (int c = 0; c <= pl.P; ++c) pl.cta_col[c] = 2 * poff[c];
+    pl.wmax = 0;
+    for (int c = 0; c < pl.P; ++c) pl.wmax = std::max(pl.wmax, pl.cta_col[c + 1] - pl.cta_col[c]);
+    pl.npmax = pl.wmax / 2;
+    const int need = (pl.npmax + 31) / 32;
+    int ch = 1;
+    while (ch < need) ch *= 2;
+    if (ch > 16) {
+        *why = "column slab wider than 1024 pairs per CTA";
+        return ADMM_EUNSUPPORTED;
+    }
+    pl.chunks = ch;
+    pl.nsub = (pl.wmax + 255) / 256;
+    pl.wbox = round_up((pl.wmax + pl.nsub - 1) / pl.nsub, 2);
+    // column blocks touched by each slab (padding columns belong to the last block)
+    auto block_of_col = [&](int c) {
+        int j = static_cast<int>(std::upper_bound(col_off.begin(), col_off.end(), c) - col_off.begin()) - 1;
+        return std::min(std::max(j, 0), N - 1);
+    };
+    pl.cta_jlo.resize(pl.P);
+    pl.cta_nj.resize(pl.P);
+    pl.j_cta_lo.assign(N, pl.P);
+    pl.j_cta_hi.assign(N, -1);
+    pl.njs = 1;
+    for (int c = 0; c < pl.P; ++c) {
+        const int jlo = block_of_col(pl.cta_col[c]);
+        const int jhi = block_of_col(pl.cta_col[c + 1] - 1);
+        pl.cta_jlo[c] = jlo;
+        pl.cta_nj[c] = jhi - jlo + 1;
+        pl.njs = std::max(pl.njs, jhi - jlo + 1);
+        for (int j = jlo; j <= jhi; ++j) {
+            pl.j_cta_lo[j] = std::min(pl.j_cta_lo[j], c);
+            pl.j_cta_hi[j] = std::max(pl.j_cta_hi[j], c);
+        }
+    }
+    if (pl.njs > kMaxBlocksPerSlab) {
+        *why = "a CTA column slab would touch more than 4 column blocks (column blocks too narrow)";
+        return ADMM_EUNSUPPORTED;
+    }
+    for (int j = 0; j < N; ++j)
+        if (pl.j_cta_hi[j] < pl.j_cta_lo[j]) {
+            *why = "internal: column block without a slab";
+            return ADMM_EINVAL;
+        }
+    pl.mimax = 0;
+    for (int i = 0; i < M; ++i) pl.mimax = std::max(pl.mimax, row_off[i + 1] - row_off[i]);
+    pl.kpmax = round_up(pl.mimax, 4);
+    // shared memory: fixed regions, then the largest ring that fits
+    const int ws = pl.njs * pl.mimax * 8;
+    const int rs = pl.kpmax * 8;
+    const int red = kConsumerWarps * pl.npmax * 16;
+    const int usum = pl.npmax * 16;
+    const int misc = 1024;
+    const int bars = 2 * 8 * 8;
+    const int fixed = round_up(ws, 128) + round_up(rs, 128) + round_up(red, 128) +
+                      round_up(usum, 128) + misc + bars + 1024;
+    const int avail = smem_limit - fixed;
+    const int mi_rows = round_up(pl.mimax, 8);
+    int chosen = 0, stages = 0;
+    for (int R : {64, 32, 16, 8}) {
+        if (R > mi_rows && R > 8) continue;
+        const int sb = R * pl.nsub * pl.wbox * 8;
+        const int stride = round_up(sb, 128);
+        const int ns = std::min(8, avail / stride);
+        if (sb <= 48 * 1024 && ns >= 4) {
+            chosen = R;
+            stages = ns;
+            break;
+        }
+    }
+    if (!chosen) {
+        const int sb = 8 * pl.nsub * pl.wbox * 8;
+        const int ns = std::min(8, avail / round_up(sb, 128));
+        if (ns >= 2) {
+            chosen = 8;
+            stages = ns;
+        }
+    }
+    if (!chosen) {
+        *why = "shared memory too small for two pipeline stages";
+        return ADMM_EUNSUPPORTED;
+    }
+    pl.R = chosen;
+    pl.nstages = stages;
+    pl.sub_bytes = pl.R * pl.wbox * 8;
+    pl.stage_bytes = pl.sub_bytes * pl.nsub;
+    pl.stage_stride = round_up(pl.stage_bytes, 128);
+    int off = 0;
+    pl.off_ring = off;
+    off += pl.stage_stride * pl.nstages;
+    off = round_up(off, 128);
+    pl.off_full = off;
+    off += 8 * 8;
+    pl.off_empty = off;
+    off += 8 * 8;
+    off = round_up(off, 128);
+    pl.off_ws = off;
+    off += round_up(ws, 128);
+    pl.off_rs = off;
+    off += round_up(rs, 128);
+    pl.off_red = off;
+    off += round_up(red, 128);
+    pl.off_usum = off;
+    off += round_up(usum, 128);
+    pl.off_misc = off;
+    off += misc;
+    pl.smem = off;
+    if (pl.smem > smem_limit) {
+        *why = "shared memory plan exceeds the device limit";
+        return ADMM_EUNSUPPORTED;
+    }
+    // factor-apply rows (N * m of them) split evenly over the CTAs
+    balanced_offsets(static_cast<int64_t>(N) * m, pl.P, pl.solve_lo);
+    return ADMM_OK;
+}
+
+}  // namespace admm
+
+// ---------------------------------------------------------------------------
+// setup helpers
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int validate(int64_t m, int64_t n, int M, int N, double lambda, double rho, int dtype) {
+    if (m < 1 || n < 1) return fail(nullptr, ADMM_EINVAL, "m and n must be >= 1 (got %lld x %lld)",
+                                     (long long)m, (long long)n);
+    if (m > (1LL << 24) || n > (1LL << 28))
+        return fail(nullptr, ADMM_EUNSUPPORTED, "m must be <= 2^24 and n <= 2^28");
+    if (M < 1 || M > m || N < 1 || N > n)
+        return fail(nullptr, ADMM_EINVAL, "need 1 <= row_blocks <= m and 1 <= col_blocks <= n");
+    if (static_cast<int64_t>(M) * N > admm::kMaxBlocks)
+        return fail(nullptr, ADMM_EINVAL, "row_blocks * col_blocks must be <= %d", admm::kMaxBlocks);
+    if (static_cast<int64_t>(N) * m >= (1LL << 31))
+        return fail(nullptr, ADMM_EUNSUPPORTED, "col_blocks * m must be < 2^31");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda))
+        return fail(nullptr, ADMM_EINVAL, "lambda must be finite and >= 0");
+    if (!(rho > 0.0) || !std::isfinite(rho))
+        return fail(nullptr, ADMM_EINVAL, "rho must be finite and > 0");
+    if (dtype != ADMM_C64 && dtype != ADMM_C128)
+        return fail(nullptr, ADMM_EINVAL, "h_dtype must be ADMM_C64 or ADMM_C128");
+    return ADMM_OK;
+}
+
+int copy_vector_in(admm_t* h, float2* dst, const void* src, int64_t count, int dtype,
+                   cudaStream_t st) {
+    if (dtype == ADMM_C64) {
+        CK(h, cudaMemcpyAsync(dst, src, count * sizeof(float2), cudaMemcpyDefault, st));
+        return ADMM_OK;
+    }
+    double2* tmp = nullptr;
+    CK(h, dalloc(&tmp, count));
+    cudaError_t e = cudaMemcpyAsync(tmp, src, count * sizeof(double2), cudaMemcpyDefault, st);
+    if (e == cudaSuccess) e = admm::launch_pack_c128(tmp, 1, count, dst, count, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(tmp);
+    if (e != cudaSuccess) return cuda_fail(h, e, "copy complex128 vector");
+    return ADMM_OK;
+}
+
+int build_factors(admm_t* h, cudaStream_t st) {
+    const Plan& pl = h->plan;
+    const int T = (pl.mimax + admm::kTile - 1) / admm::kTile;
+    const size_t S = static_cast<size_t>(T) * admm::kTile;
+    const int nb = h->M * h->N;
+    double2 *A = nullptr, *W = nullptr;
+    if (dalloc(&A, S * S * nb) != cudaSuccess || dalloc(&W, S * S * nb) != cudaSuccess) {
+        if (A) cudaFree(A);
+        return fail(h, ADMM_ENOMEM, "cannot allocate %.1f MB of FP64 factor workspace",
+                    2.0 * S * S * nb * 16 / 1e6);
+    }
+    admm::FactorArgs f;
+    f.m = static_cast<int>(h->m);
+    f.ld = pl.ld;
+    f.M = h->M;
+    f.N = h->N;
+    f.T = T;
+    f.row_off = h->row_off_d;
+    f.col_off = h->col_off_d;
+    f.H = h->H;
+    f.A = A;
+    f.W = W;
+    f.kinv = h->kinv;
+    f.kinv_off = h->kinv_off_d;
+    f.kinv_pitch = h->kinv_pitch_d;
+    f.rho = h->rho;
+    f.status = h->status;
+    cudaEvent_t e0, e1, e2;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    cudaEventCreate(&e2);
+    cudaError_t err = cudaMemsetAsync(h->kinv, 0, h->kinv_elems * sizeof(float2), st);
+    if (err == cudaSuccess) err = cudaMemsetAsync(h->status, 0, sizeof(int), st);
+    if (err == cudaSuccess) err = cudaEventRecord(e0, st);
+    if (err == cudaSuccess) err = admm::launch_gram(f, st);
+    if (err == cudaSuccess) err = cudaEventRecord(e1, st);
+    if (err == cudaSuccess) err = admm::launch_cholesky_inverse(f, st);
+    if (err == cudaSuccess) err = cudaEventRecord(e2, st);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(st);
+    float t01 = 0.f, t12 = 0.f;
+    if (err == cudaSuccess) {
+        cudaEventElapsedTime(&t01, e0, e1);
+        cudaEventElapsedTime(&t12, e1, e2);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(e2);
+    cudaFree(A);
+    cudaFree(W);
+    if (err != cudaSuccess) return cuda_fail(h, err, "factor kernels");
+    h->gram_ms = t01;
+    h->factor_ms = t12;
+    int st_code = 0;
+    CK(h, cudaMemcpy(&st_code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st_code == ADMM_ENOTPD)
+        return fail(h, ADMM_ENOTPD, "a block rho I + H_b H_b^H is not positive definite in FP64");
+    if (st_code != 0) return fail(h, st_code, "factor kernels raised status %d", st_code);
+    return ADMM_OK;
+}
+
+int encode_tensor_map(admm_t* h) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return fail(h, ADMM_ECUDA, "cuTensorMapEncodeTiled is not available from the driver");
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const Plan& pl = h->plan;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(pl.ld), static_cast<cuuint64_t>(h->m)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pl.ld) * sizeof(float2)};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(pl.wbox), static_cast<cuuint32_t>(pl.R)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, h->H, dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(h, ADMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return ADMM_OK;
+}
+
+int zero_state(admm_t* h, cudaStream_t st) {
+    const size_t ld = h->plan.ld;
+    CK(h, cudaMemsetAsync(h->v, 0, ld * sizeof(float2), st));
+    CK(h, cudaMemsetAsync(h->s, 0, ld * h->M * sizeof(float2), st));
+    CK(h, cudaMemsetAsync(h->u, 0, ld * h->M * sizeof(float2), st));
+    CK(h, cudaMemsetAsync(h->ghat, 0, static_cast<size_t>(h->N) * h->m * sizeof(float2), st));
+    CK(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), st));
+    CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    CK(h, cudaMemsetAsync(h->stop_flag, 0, sizeof(int), st));
+    CK(h, cudaMemsetAsync(h->k_done, 0, sizeof(long long), st));
+    CK(h, cudaMemsetAsync(h->hist, 0, static_cast<size_t>(h->hist_cap) * 5 * sizeof(double), st));
+    h->k = 0;
+    h->broken = 0;
+    return ADMM_OK;
+}
+
+int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_rel,
+               cudaStream_t st) {
+    const Plan& pl = h->plan;
+    admm::IterArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.m = static_cast<int>(h->m);
+    a.n = static_cast<int>(h->n);
+    a.ld = pl.ld;
+    a.M = h->M;
+    a.N = h->N;
+    a.P = pl.P;
+    a.R = pl.R;
+    a.nstages = pl.nstages;
+    a.stage_bytes = pl.stage_bytes;
+    a.stage_stride = pl.stage_stride;
+    a.sub_bytes = pl.sub_bytes;
+    a.nsub = pl.nsub;
+    a.wbox = pl.wbox;
+    a.mimax = pl.mimax;
+    a.kpmax = pl.kpmax;
+    a.off_ring = pl.off_ring;
+    a.off_full = pl.off_full;
+    a.off_empty = pl.off_empty;
+    a.off_ws = pl.off_ws;
+    a.off_rs = pl.off_rs;
+    a.off_red = pl.off_red;
+    a.off_usum = pl.off_usum;
+    a.off_misc = pl.off_misc;
+    a.rho = static_cast<float>(h->rho);
+    a.rho_d = h->rho;
+    a.kappa = static_cast<float>(h->lambda / (h->M * h->rho));
+    a.inv_M = 1.0f / static_cast<float>(h->M);
+    a.row_off = h->row_off_d;
+    a.col_off = h->col_off_d;
+    a.cta_col = h->cta_col_d;
+    a.cta_jlo = h->cta_jlo_d;
+    a.cta_nj = h->cta_nj_d;
+    a.j_cta_lo = h->j_cta_lo_d;
+    a.j_cta_hi = h->j_cta_hi_d;
+    a.solve_lo = h->solve_lo_d;
+    a.v = h->v;
+    a.s = h->s;
+    a.u = h->u;
+    a.g = h->g;
+    a.ghat = h->ghat;
+    a.gt = h->gt;
+    a.r = h->r;
+    a.w = h->w;
+    a.part = h->part;
+    a.kinv = h->kinv;
+    a.kinv_off = h->kinv_off_d;
+    a.kinv_pitch = h->kinv_pitch_d;
+    a.res_part = h->res_part;
+    a.hist = h->hist;
+    a.k_done = h->k_done;
+    a.bar = h->bar;
+    a.status = h->status;
+    a.stop_flag = h->stop_flag;
+    a.k0 = h->k;
+    a.hist_cap = h->hist_cap;
+    a.iters = iters;
+    a.check_stop = check_stop;
+    a.eps_abs = eps_abs;
+    a.eps_rel = eps_rel;
+    a.timeout_ns = h->timeout_ns;
+    a.bar_extra = h->bar_extra;
+    cudaError_t e = admm::launch_iterate(h->tmap, a, pl.chunks, pl.smem, st);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the iteration kernel");
+    h->k += iters;
+    return ADMM_OK;
+}
+
+int device_status(admm_t* h, cudaStream_t st) {
+    CK(h, cudaStreamSynchronize(st));
+    int code = 0;
+    long long kd = 0;
+    CK(h, cudaMemcpy(&code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    CK(h, cudaMemcpy(&kd, h->k_done, sizeof(long long), cudaMemcpyDeviceToHost));
+    h->k = kd;
+    if (code == ADMM_ETIMEOUT) {
+        h->broken = 1;
+        return fail(h, code, "a bounded in-kernel wait expired (state undefined; call admm_reset)");
+    }
+    if (code == ADMM_EDIVERGED) return fail(h, code, "the iterates became NaN or Inf");
+    if (code != 0) return fail(h, code, "device status %d", code);
+    return ADMM_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+extern "C" {
+
+int admm_abi_version(void) { return ADMM_ABI_VERSION; }
+
+const char* admm_strerror(int status) {
+    switch (status) {
+        case ADMM_OK: return "ok";
+        case ADMM_EINVAL: return "invalid argument";
+        case ADMM_ENOMEM: return "device allocation failed";
+        case ADMM_ECUDA: return "CUDA error";
+        case ADMM_ENOTPD: return "factor not positive definite";
+        case ADMM_ENONFINITE: return "non-finite input";
+        case ADMM_ETIMEOUT: return "bounded in-kernel wait expired";
+        case ADMM_EUNSUPPORTED: return "unsupported problem shape";
+        case ADMM_EDIVERGED: return "iterates diverged";
+        default: return "unknown status";
+    }
+}
+
+const char* admm_last_error(const admm_t* h) {
+    return h ? h->err.c_str() : g_setup_error.c_str();
+}
+
+int admm_partition(int64_t total, int32_t parts, int64_t* offsets) {
+    if (!offsets || parts < 1 || total < parts) return ADMM_EINVAL;
+    const int64_t base = total / parts, extra = total % parts;
+    int64_t pos = 0;
+    for (int p = 0; p < parts; ++p) {
+        offsets[p] = pos;
+        pos += base + (p < extra ? 1 : 0);
+    }
+    offsets[parts] = pos;
+    return ADMM_OK;
+}
+
+int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks, int32_t num_sms,
+              int32_t smem_limit, admm_plan_t* out, int32_t* cta_cols) {
+    if (!out) return ADMM_EINVAL;
+    int code = validate(m, n, row_blocks, col_blocks, 0.0, 1.0, ADMM_C64);
+    if (code) return code;
+    std::vector<int> ro, co;
+    admm::balanced_offsets(m, row_blocks, ro);
+    admm::balanced_offsets(n, col_blocks, co);
+    Plan pl;
+    const char* why = "";
+    code = admm::make_plan(m, n, row_blocks, col_blocks, ro, co, num_sms, smem_limit, pl, &why);
+    if (code) return fail(nullptr, code, "%s", why);
+    out->ctas = pl.P;
+    out->slab_cols = pl.wmax;
+    out->chunks = pl.chunks;
+    out->box_cols = pl.wbox;
+    out->boxes_per_row = pl.nsub;
+    out->rows_per_stage = pl.R;
+    out->stages = pl.nstages;
+    out->smem_bytes = pl.smem;
+    out->max_blocks_per_slab = pl.njs;
+    out->ld = pl.ld;
+    if (cta_cols)
+        for (int c = 0; c <= pl.P; ++c) cta_cols[c] = pl.cta_col[c];
+    return ADMM_OK;
+}
+
+int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
+               int32_t row_blocks, int32_t col_blocks, double lambda, double rho,
+               int32_t h_dtype, void* stream) {
+    if (!out) return fail(nullptr, ADMM_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!H || !g) return fail(nullptr, ADMM_EINVAL, "H and g must not be NULL");
+    int code = validate(m, n, row_blocks, col_blocks, lambda, rho, h_dtype);
+    if (code) return code;
+    std::vector<int> ro, co;
+    admm::balanced_offsets(m, row_blocks, ro);
+    admm::balanced_offsets(n, col_blocks, co);
+    for (int i = 0; i < row_blocks; ++i)
+        for (int j = 0; j < col_blocks; ++j)
+            if (ro[i + 1] - ro[i] >= co[j + 1] - co[j])
+                return fail(nullptr, ADMM_EUNSUPPORTED,
+                            "block (%d,%d) has %d rows >= %d columns: the direct (non-lemma) u-step "
+                            "is not implemented on the GPU",
+                            i, j, ro[i + 1] - ro[i], co[j + 1] - co[j]);
+
+    admm_t* h = new admm_t();
+    h->m = m;
+    h->n = n;
+    h->M = row_blocks;
+    h->N = col_blocks;
+    h->lambda = lambda;
+    h->rho = rho;
+    h->row_off = ro;
+    h->col_off = co;
+    cudaStream_t st = as_stream(stream);
+    auto bail = [&](int c) {
+        g_setup_error = h->err;
+        free_all(h);
+        delete h;
+        return c;
+    };
+    cudaError_t e = cudaGetDevice(&h->device);
+    if (e != cudaSuccess) return bail(cuda_fail(h, e, "cudaGetDevice"));
+    int coop = 0;
+    cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
+    cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+    if (!coop) return bail(fail(h, ADMM_EUNSUPPORTED, "device has no cooperative launch"));
+    const char* why = "";
+    code = admm::make_plan(m, n, row_blocks, col_blocks, ro, co, h->num_sms, h->smem_optin, h->plan, &why);
+    if (code) return bail(fail(h, code, "%s", why));
+    const Plan& pl = h->plan;
+
+    // factor layout: block b = (i, j) holds m_i x kp_i complex64, kp_i = m_i rounded up to 4
+    h->kinv_off.resize(row_blocks * col_blocks);
+    h->kinv_pitch.resize(row_blocks * col_blocks);
+    int64_t kel = 0;
+    for (int i = 0; i < row_blocks; ++i)
+        for (int j = 0; j < col_blocks; ++j) {
+            const int mi = ro[i + 1] - ro[i];
+            const int kp = round_up(mi, 4);
+            h->kinv_off[i * col_blocks + j] = kel;
+            h->kinv_pitch[i * col_blocks + j] = kp;
+            kel += static_cast<int64_t>(mi) * kp;
+        }
+    h->kinv_elems = kel;
+
+    const size_t ld = pl.ld;
+    const size_t Nm = static_cast<size_t>(col_blocks) * m;
+    bool ok = dalloc(&h->H, ld * m) == cudaSuccess && dalloc(&h->g, m) == cudaSuccess &&
+              dalloc(&h->v, ld) == cudaSuccess && dalloc(&h->s, ld * row_blocks) == cudaSuccess &&
+              dalloc(&h->u, ld * row_blocks) == cudaSuccess && dalloc(&h->ghat, Nm) == cudaSuccess &&
+              dalloc(&h->gt, Nm) == cudaSuccess && dalloc(&h->r, Nm) == cudaSuccess &&
+              dalloc(&h->w, Nm) == cudaSuccess && dalloc(&h->part, Nm * pl.P) == cudaSuccess &&
+              dalloc(&h->kinv, kel) == cudaSuccess &&
+              dalloc(&h->kinv_off_d, h->kinv_off.size()) == cudaSuccess &&
+              dalloc(&h->res_part, static_cast<size_t>(pl.P) * 8) == cudaSuccess &&
+              dalloc(&h->hist, static_cast<size_t>(h->hist_cap) * 5) == cudaSuccess &&
+              dalloc(&h->k_done, 1) == cudaSuccess && dalloc(&h->bar, 2) == cudaSuccess &&
+              dalloc(&h->status, 1) == cudaSuccess && dalloc(&h->stop_flag, 1) == cudaSuccess;
+    // int tables in one allocation
+    std::vector<int> ints;
+    auto put = [&](const std::vector<int>& x) {
+        const size_t at = ints.size();
+        ints.insert(ints.end(), x.begin(), x.end());
+        return at;
+    };
+    const size_t o_row = put(ro), o_col = put(co), o_cta = put(pl.cta_col), o_jlo = put(pl.cta_jlo),
+                 o_nj = put(pl.cta_nj), o_jl = put(pl.j_cta_lo), o_jh = put(pl.j_cta_hi),
+                 o_sl = put(pl.solve_lo), o_kp = put(h->kinv_pitch);
+    ok = ok && dalloc(&h->ints_d, ints.size()) == cudaSuccess;
+    if (!ok) return bail(fail(h, ADMM_ENOMEM, "device allocation failed (%.1f MB for H)", ld * m * 8 / 1e6));
+    h->row_off_d = h->ints_d + o_row;
+    h->col_off_d = h->ints_d + o_col;
+    h->cta_col_d = h->ints_d + o_cta;
+    h->cta_jlo_d = h->ints_d + o_jlo;
+    h->cta_nj_d = h->ints_d + o_nj;
+    h->j_cta_lo_d = h->ints_d + o_jl;
+    h->j_cta_hi_d = h->ints_d + o_jh;
+    h->solve_lo_d = h->ints_d + o_sl;
+    h->kinv_pitch_d = h->ints_d + o_kp;
+    h->state_bytes = static_cast<int64_t>((ld * (1 + 2 * row_blocks) + 4 * Nm + Nm * pl.P) * sizeof(float2));
+
+#define SETUP_CK(call)                                             \
+    do {                                                           \
+        cudaError_t e_ = (call);                                   \
+        if (e_ != cudaSuccess) return bail(cuda_fail(h, e_, #call)); \
+    } while (0)
+
+    SETUP_CK(cudaMemcpyAsync(h->ints_d, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    SETUP_CK(cudaMemcpyAsync(h->kinv_off_d, h->kinv_off.data(), h->kinv_off.size() * sizeof(long long),
+                             cudaMemcpyHostToDevice, st));
+    // H into the padded layout (zero padding columns)
+    SETUP_CK(cudaMemsetAsync(h->H, 0, ld * m * sizeof(float2), st));
+    if (h_dtype == ADMM_C64) {
+        SETUP_CK(cudaMemcpy2DAsync(h->H, ld * sizeof(float2), H, n * sizeof(float2), n * sizeof(float2), m,
+                                   cudaMemcpyDefault, st));
+    } else {
+        double2* tmp = nullptr;
+        if (dalloc(&tmp, static_cast<size_t>(m) * n) != cudaSuccess)
+            return bail(fail(h, ADMM_ENOMEM, "no room for the complex128 staging copy of H"));
+        cudaError_t e2 = cudaMemcpyAsync(tmp, H, static_cast<size_t>(m) * n * sizeof(double2), cudaMemcpyDefault, st);
+        if (e2 == cudaSuccess) e2 = admm::launch_pack_c128(tmp, m, n, h->H, ld, st);
+        if (e2 == cudaSuccess) e2 = cudaStreamSynchronize(st);
+        cudaFree(tmp);
+        if (e2 != cudaSuccess) return bail(cuda_fail(h, e2, "pack complex128 H"));
+    }
+    code = copy_vector_in(h, h->g, g, m, h_dtype, st);
+    if (code) return bail(code);
+    // non-finite inputs
+    SETUP_CK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    SETUP_CK(admm::launch_finite_check(h->H, static_cast<int64_t>(ld) * m, h->status, st));
+    SETUP_CK(admm::launch_finite_check(h->g, m, h->status, st));
+    int flag = 0;
+    SETUP_CK(cudaStreamSynchronize(st));
+    SETUP_CK(cudaMemcpy(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return bail(fail(h, ADMM_ENONFINITE, "H or g holds NaN or Inf"));
+    code = build_factors(h, st);
+    if (code) return bail(code);
+    code = encode_tensor_map(h);
+    if (code) return bail(code);
+    SETUP_CK(admm::prepare_iterate(pl.chunks, pl.smem));
+    int per_sm = 0;
+    admm::max_coresident_iterate(pl.chunks, pl.smem, &per_sm);
+    if (per_sm * h->num_sms < pl.P)
+        return bail(fail(h, ADMM_EUNSUPPORTED, "iteration kernel cannot keep %d CTAs resident", pl.P));
+    code = zero_state(h, st);
+    if (code) return bail(code);
+    SETUP_CK(cudaStreamSynchronize(st));
+#undef SETUP_CK
+    *out = h;
+    return ADMM_OK;
+}
+
+int admm_iterate(admm_t* h, int32_t iters, void* stream) {
+    if (!h || iters < 0) return h ? fail(h, ADMM_EINVAL, "iters must be >= 0") : ADMM_EINVAL;
+    if (h->broken) return fail(h, ADMM_ECUDA, "handle is in an error state; call admm_reset");
+    if (iters == 0) return ADMM_OK;
+    return run_kernel(h, iters, 0, 0.0, 0.0, as_stream(stream));
+}
+
+int admm_solve(admm_t* h, int32_t max_iter, double eps_abs, double eps_rel, int32_t* iters_done,
+               void* stream) {
+    if (!h || max_iter < 0 || !(eps_abs >= 0.0) || !(eps_rel >= 0.0))
+        return h ? fail(h, ADMM_EINVAL, "bad solve arguments") : ADMM_EINVAL;
+    if (h->broken) return fail(h, ADMM_ECUDA, "handle is in an error state; call admm_reset");
+    const int64_t k0 = h->k;
+    if (iters_done) *iters_done = 0;
+    if (max_iter == 0) return ADMM_OK;
+    cudaStream_t st = as_stream(stream);
+    int code = run_kernel(h, max_iter, 1, eps_abs, eps_rel, st);
+    if (code) return code;
+    code = device_status(h, st);
+    if (iters_done) *iters_done = static_cast<int32_t>(h->k - k0);
+    return code;
+}
+
+int admm_get_v(admm_t* h, void* v, void* stream) {
+    if (!h || !v) return h ? fail(h, ADMM_EINVAL, "v is NULL") : ADMM_EINVAL;
+    CK(h, cudaMemcpyAsync(v, h->v, h->n * sizeof(float2), cudaMemcpyDefault, as_stream(stream)));
+    return ADMM_OK;
+}
+
+int admm_get_u(admm_t* h, void* u, void* stream) {
+    if (!h || !u) return h ? fail(h, ADMM_EINVAL, "u is NULL") : ADMM_EINVAL;
+    CK(h, cudaMemcpy2DAsync(u, h->n * sizeof(float2), h->u, h->plan.ld * sizeof(float2),
+                            h->n * sizeof(float2), h->M, cudaMemcpyDefault, as_stream(stream)));
+    return ADMM_OK;
+}
+
+int admm_get_residuals(admm_t* h, double* out, int32_t cap, int32_t* count, void* stream) {
+    if (!h || !out || !count || cap < 0) return h ? fail(h, ADMM_EINVAL, "bad arguments") : ADMM_EINVAL;
+    *count = 0;
+    const int code = device_status(h, as_stream(stream));
+    const int64_t avail = std::min<int64_t>(h->k, h->hist_cap);
+    const int64_t want = std::min<int64_t>(avail, cap);
+    std::vector<double> ring(static_cast<size_t>(h->hist_cap) * 5);
+    CK(h, cudaMemcpy(ring.data(), h->hist, ring.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t q = 0; q < want; ++q) {
+        const int64_t it = h->k - want + q;
+        const size_t slot = static_cast<size_t>(it % h->hist_cap);
+        std::memcpy(out + q * 5, ring.data() + slot * 5, 5 * sizeof(double));
+    }
+    *count = static_cast<int32_t>(want);
+    return code;
+}
+
+int admm_set_g(admm_t* h, const void* g, int32_t h_dtype, void* stream) {
+    if (!h || !g) return h ? fail(h, ADMM_EINVAL, "g is NULL") : ADMM_EINVAL;
+    if (h_dtype != ADMM_C64 && h_dtype != ADMM_C128) return fail(h, ADMM_EINVAL, "bad dtype");
+    return copy_vector_in(h, h->g, g, h->m, h_dtype, as_stream(stream));
+}
+
+int admm_set_lambda(admm_t* h, double lambda) {
+    if (!h) return ADMM_EINVAL;
+    if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(h, ADMM_EINVAL, "lambda must be finite and >= 0");
+    h->lambda = lambda;
+    return ADMM_OK;
+}
+
+int admm_set_rho(admm_t* h, double rho, void* stream) {
+    if (!h) return ADMM_EINVAL;
+    if (!(rho > 0.0) || !std::isfinite(rho)) return fail(h, ADMM_EINVAL, "rho must be finite and > 0");
+    cudaStream_t st = as_stream(stream);
+    const double old = h->rho;
+    h->rho = rho;
+    int code = build_factors(h, st);
+    if (code) {
+        h->rho = old;
+        return code;
+    }
+    CK(h, admm::launch_scale(h->s, static_cast<int64_t>(h->plan.ld) * h->M, static_cast<float>(old / rho), st));
+    CK(h, cudaStreamSynchronize(st));
+    return ADMM_OK;
+}
+
+int admm_reset(admm_t* h, void* stream) {
+    if (!h) return ADMM_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const int code = zero_state(h, st);
+    if (code) return code;
+    CK(h, cudaStreamSynchronize(st));
+    return ADMM_OK;
+}
+
+int admm_get_state(admm_t* h, int64_t* k, void* v, void* s, void* ghat, void* stream) {
+    if (!h) return ADMM_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    const int code = device_status(h, st);
+    if (code == ADMM_ETIMEOUT || code == ADMM_ECUDA) return code;
+    if (k) *k = h->k;
+    if (v) CK(h, cudaMemcpyAsync(v, h->v, h->n * sizeof(float2), cudaMemcpyDefault, st));
+    if (s)
+        CK(h, cudaMemcpy2DAsync(s, h->n * sizeof(float2), h->s, h->plan.ld * sizeof(float2),
+                                h->n * sizeof(float2), h->M, cudaMemcpyDefault, st));
+    if (ghat)
+        CK(h, cudaMemcpyAsync(ghat, h->ghat, static_cast<size_t>(h->N) * h->m * sizeof(float2),
+                              cudaMemcpyDefault, st));
+    CK(h, cudaStreamSynchronize(st));
+    return code;
+}
+
+int admm_set_state(admm_t* h, int64_t k, const void* v, const void* s, const void* ghat, void* stream) {
+    if (!h || !v || !s || k < 0) return h ? fail(h, ADMM_EINVAL, "v and s are required, k >= 0") : ADMM_EINVAL;
+    if (!ghat && h->N > 1) return fail(h, ADMM_EINVAL, "ghat is required when col_blocks > 1");
+    cudaStream_t st = as_stream(stream);
+    CK(h, cudaStreamSynchronize(st));
+    CK(h, cudaMemcpyAsync(h->v, v, h->n * sizeof(float2), cudaMemcpyDefault, st));
+    CK(h, cudaMemcpy2DAsync(h->s, h->plan.ld * sizeof(float2), s, h->n * sizeof(float2),
+                            h->n * sizeof(float2), h->M, cudaMemcpyDefault, st));
+    if (ghat)
+        CK(h, cudaMemcpyAsync(h->ghat, ghat, static_cast<size_t>(h->N) * h->m * sizeof(float2),
+                              cudaMemcpyDefault, st));
+    else
+        CK(h, cudaMemsetAsync(h->ghat, 0, static_cast<size_t>(h->N) * h->m * sizeof(float2), st));
+    CK(h, cudaMemcpyAsync(h->k_done, &k, sizeof(long long), cudaMemcpyHostToDevice, st));
+    CK(h, cudaStreamSynchronize(st));
+    h->k = k;
+    return ADMM_OK;
+}
+
+int admm_get_info(const admm_t* h, admm_info_t* info) {
+    if (!h || !info) return ADMM_EINVAL;
+    const Plan& pl = h->plan;
+    info->m = h->m;
+    info->n = h->n;
+    info->ld = pl.ld;
+    info->row_blocks = h->M;
+    info->col_blocks = h->N;
+    info->lambda = h->lambda;
+    info->rho = h->rho;
+    info->kappa = h->lambda / (h->M * h->rho);
+    info->iterations = h->k;
+    info->ctas = pl.P;
+    info->rows_per_stage = pl.R;
+    info->stages = pl.nstages;
+    info->slab_cols = pl.wmax;
+    info->smem_bytes = pl.smem;
+    info->num_sms = h->num_sms;
+    info->h_bytes = h->m * h->n * static_cast<int64_t>(sizeof(float2));
+    info->factor_bytes = h->kinv_elems * static_cast<int64_t>(sizeof(float2));
+    info->state_bytes = h->state_bytes;
+    info->setup_gram_ms = h->gram_ms;
+    info->setup_factor_ms = h->factor_ms;
+    return ADMM_OK;
+}
+
+int admm_set_option(admm_t* h, int32_t option, int64_t value) {
+    if (!h) return ADMM_EINVAL;
+    switch (option) {
+        case ADMM_OPT_TIMEOUT_NS:
+            if (value < 1000) return fail(h, ADMM_EINVAL, "timeout must be >= 1000 ns");
+            h->timeout_ns = value;
+            return ADMM_OK;
+        case ADMM_OPT_HIST_CAP: {
+            if (value < 1 || value > (1 << 24)) return fail(h, ADMM_EINVAL, "history capacity out of range");
+            double* nh = nullptr;
+            CK(h, dalloc(&nh, static_cast<size_t>(value) * 5));
+            CK(h, cudaDeviceSynchronize());
+            cudaFree(h->hist);
+            h->hist = nh;
+            h->hist_cap = static_cast<int>(value);
+            CK(h, cudaMemset(h->hist, 0, static_cast<size_t>(value) * 5 * sizeof(double)));
+            return ADMM_OK;
+        }
+        case ADMM_OPT_BARRIER_EXTRA:
+            if (value < 0 || value > 1024) return fail(h, ADMM_EINVAL, "barrier extra out of range");
+            h->bar_extra = static_cast<int>(value);
+            return ADMM_OK;
+        default:
+            return fail(h, ADMM_EINVAL, "unknown option %d", option);
+    }
+}
+
+int admm_status(admm_t* h, void* stream) {
+    if (!h) return ADMM_EINVAL;
+    return device_status(h, as_stream(stream));
+}
+
+void admm_destroy(admm_t* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    free_all(h);
+    delete h;
+}
+
+}  // extern "C"

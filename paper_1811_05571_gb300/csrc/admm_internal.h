@@ -1,0 +1,133 @@
+// Internal declarations shared by the host API (admm_api.cu), the iteration
+// kernel (admm_iterate.cu) and the factor kernels (admm_factor.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <vector>
+
+#include "../../include/admm.h"
+
+namespace admm {
+
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumerThreads = kConsumerWarps * 32;
+constexpr int kIterThreads = kConsumerThreads + 32;  // + one TMA producer warp
+constexpr int kMaxBlocksPerSlab = 4;                 // column blocks one CTA slab may touch
+constexpr int kMaxBlocks = 256;                      // row_blocks * col_blocks
+constexpr int kTile = 32;                            // FP64 factor tile edge
+
+// Host-side plan of the persistent iteration kernel.
+struct Plan {
+    int P = 0;            // CTAs
+    int ld = 0;           // padded row pitch (complex elements), multiple of 32
+    int wmax = 0;         // widest slab (columns, even)
+    int npmax = 0;        // widest slab in column pairs
+    int chunks = 0;       // per-lane 32-pair chunks (template width)
+    int nsub = 0;         // TMA boxes per slab row
+    int wbox = 0;         // TMA box width (columns, even, <= 256)
+    int R = 0;            // rows per stage
+    int nstages = 0;
+    int stage_bytes = 0;  // bytes landed per stage (all boxes)
+    int stage_stride = 0; // ring slot stride (128-byte multiple)
+    int sub_bytes = 0;    // bytes per box
+    int njs = 0;          // most column blocks touched by one slab
+    int mimax = 0;        // tallest row block
+    int kpmax = 0;        // padded pitch of the tallest factor
+    // shared-memory layout (byte offsets into dynamic smem)
+    int off_ring = 0, off_full = 0, off_empty = 0, off_ws = 0, off_rs = 0, off_red = 0,
+        off_usum = 0, off_misc = 0, smem = 0;
+    std::vector<int> cta_col;   // P+1 slab starts
+    std::vector<int> cta_jlo;   // P
+    std::vector<int> cta_nj;    // P
+    std::vector<int> j_cta_lo;  // N
+    std::vector<int> j_cta_hi;  // N
+    std::vector<int> solve_lo;  // P+1 split of the N*m factor-apply rows
+};
+
+// Returns ADMM_OK, ADMM_EINVAL or ADMM_EUNSUPPORTED; fills `plan`.
+int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_off,
+              const std::vector<int>& col_off, int num_sms, int smem_limit, Plan& plan,
+              const char** why);
+
+void balanced_offsets(int64_t total, int parts, std::vector<int>& off);
+
+// Arguments of the persistent iteration kernel (passed by value).
+struct IterArgs {
+    int m, n, ld, M, N, P;
+    int R, nstages, stage_bytes, stage_stride, sub_bytes, nsub, wbox;
+    int mimax, kpmax;
+    int off_ring, off_full, off_empty, off_ws, off_rs, off_red, off_usum, off_misc;
+    float rho, kappa, inv_M;
+    double rho_d;
+    const int* row_off;
+    const int* col_off;
+    const int* cta_col;
+    const int* cta_jlo;
+    const int* cta_nj;
+    const int* j_cta_lo;
+    const int* j_cta_hi;
+    const int* solve_lo;
+    float2* v;
+    float2* s;
+    float2* u;
+    const float2* g;
+    float2* ghat;
+    float2* gt;
+    float2* r;
+    float2* w;
+    float2* part;
+    const float2* kinv;
+    const long long* kinv_off;
+    const int* kinv_pitch;
+    double* res_part;
+    double* hist;
+    long long* k_done;
+    unsigned* bar;
+    int* status;
+    int* stop_flag;
+    long long k0;
+    int hist_cap;
+    int iters;
+    int check_stop;
+    double eps_abs, eps_rel;
+    long long timeout_ns;
+    int bar_extra;
+};
+
+// Launch the persistent cooperative iteration kernel for `a.iters` iterations.
+cudaError_t launch_iterate(const CUtensorMap& tmap, const IterArgs& a, int chunks, int smem,
+                           cudaStream_t stream);
+// Opt the kernel instances into `smem` bytes of dynamic shared memory.
+cudaError_t prepare_iterate(int chunks, int smem);
+int max_coresident_iterate(int chunks, int smem, int* per_sm);
+
+// ---- setup kernels (admm_factor.cu) ------------------------------------------
+
+struct FactorArgs {
+    int m, ld, M, N;
+    int T;                   // factor tiles per edge (ceil(mimax / 32))
+    const int* row_off;
+    const int* col_off;
+    const float2* H;         // packed H (m x ld)
+    double2* A;              // per block (T*32)^2, FP64: K_b, then L_b
+    double2* W;              // per block (T*32)^2, FP64: L_b^{-1}
+    float2* kinv;            // packed complex64 K_b^{-1}
+    const long long* kinv_off;
+    const int* kinv_pitch;
+    double rho;
+    int* status;
+};
+
+cudaError_t launch_gram(const FactorArgs& f, cudaStream_t s);
+cudaError_t launch_cholesky_inverse(const FactorArgs& f, cudaStream_t s);
+
+// ---- small kernels (admm_misc.cu) ---------------------------------------------
+
+cudaError_t launch_pack_c128(const double2* src, int64_t m, int64_t n, float2* dst, int64_t ld,
+                             cudaStream_t s);
+cudaError_t launch_finite_check(const float2* x, int64_t count, int* flag, cudaStream_t s);
+cudaError_t launch_scale(float2* x, int64_t count, float alpha, cudaStream_t s);
+
+}  // namespace admm

@@ -1,0 +1,127 @@
+"""``Solver``: an owning wrapper around one libadmm handle.
+
+PyTorch supplies device memory and streams; every computation is a call into
+libadmm.so.  Inputs may be torch tensors (CPU or CUDA) or numpy arrays of
+complex64 / complex128; outputs are CUDA complex64 tensors unless a
+destination buffer is passed.
+"""
+
+from __future__ import annotations
+
+import numpy as np
+
+from . import _binding as B
+
+
+def _dtype_code(x) -> int:
+    name = str(getattr(x, "dtype", ""))
+    if "complex64" in name:
+        return B.ADMM_C64
+    if "complex128" in name:
+        return B.ADMM_C128
+    raise TypeError(f"H and g must be complex64 or complex128, got {name}")
+
+
+def _contig(x):
+    if hasattr(x, "is_contiguous"):
+        return x if x.is_contiguous() else x.contiguous()
+    return np.ascontiguousarray(x)
+
+
+class Solver:
+    """Norm-1 ADMM for g = Hu + w split into row_blocks x col_blocks (Sections III-A..C)."""
+
+    def __init__(self, H, g, row_blocks: int = 1, col_blocks: int = 1, lam: float = 0.0,
+                 rho: float = 1.0, stream=None):
+        import torch
+        self._torch = torch
+        H = _contig(H)
+        g = _contig(g)
+        m, n = int(H.shape[0]), int(H.shape[1])
+        if int(g.shape[0]) != m:
+            raise ValueError("g must have m entries")
+        dt = _dtype_code(H)
+        if _dtype_code(g) != dt:
+            raise TypeError("H and g must share a dtype")
+        self.m, self.n, self.M, self.N = m, n, int(row_blocks), int(col_blocks)
+        self.stream = stream
+        self._keep = (H, g)   # keep the sources alive until the synchronous setup returns
+        self.h = B.admm_setup(H, g, m, n, self.M, self.N, float(lam), float(rho), dt, stream)
+        self._keep = None
+
+    # -- iteration ---------------------------------------------------------
+    def iterate(self, iters: int = 1) -> "Solver":
+        B.admm_iterate(self.h, int(iters), self.stream)
+        return self
+
+    def solve(self, max_iter: int, eps_abs: float = 1e-6, eps_rel: float = 1e-4) -> int:
+        return B.admm_solve(self.h, int(max_iter), float(eps_abs), float(eps_rel), self.stream)
+
+    # -- results -----------------------------------------------------------
+    def v(self, out=None):
+        out = self._torch.empty(self.n, dtype=self._torch.complex64, device="cuda") if out is None else out
+        B.admm_get_v(self.h, out, self.stream)
+        return out
+
+    def u(self, out=None):
+        out = (self._torch.empty((self.M, self.n), dtype=self._torch.complex64, device="cuda")
+               if out is None else out)
+        B.admm_get_u(self.h, out, self.stream)
+        return out
+
+    def residuals(self, cap: int | None = None) -> np.ndarray:
+        info = self.info()
+        cap = int(info["iterations"]) if cap is None else int(cap)
+        return B.admm_get_residuals(self.h, max(cap, 0), self.stream)
+
+    def state(self):
+        t = self._torch
+        v = t.empty(self.n, dtype=t.complex64)
+        s = t.empty((self.M, self.n), dtype=t.complex64)
+        gh = t.empty((self.N, self.m), dtype=t.complex64)
+        k = B.admm_get_state(self.h, v, s, gh, self.stream)
+        return k, v, s, gh
+
+    def set_state(self, k: int, v, s, ghat=None) -> None:
+        B.admm_set_state(self.h, int(k), _contig(v), _contig(s),
+                         None if ghat is None else _contig(ghat), self.stream)
+
+    # -- parameters ----------------------------------------------------------
+    def set_g(self, g) -> None:
+        g = _contig(g)
+        B.admm_set_g(self.h, g, _dtype_code(g), self.stream)
+
+    def set_lambda(self, lam: float) -> None:
+        B.admm_set_lambda(self.h, float(lam))
+
+    def set_rho(self, rho: float) -> None:
+        B.admm_set_rho(self.h, float(rho), self.stream)
+
+    def reset(self) -> None:
+        B.admm_reset(self.h, self.stream)
+
+    def set_option(self, option: int, value: int) -> None:
+        B.admm_set_option(self.h, int(option), int(value))
+
+    def status(self) -> int:
+        return B.admm_status(self.h, self.stream)
+
+    def info(self) -> dict:
+        return B.admm_get_info(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            B.admm_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

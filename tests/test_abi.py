@@ -1,0 +1,134 @@
+"""The C ABI without a GPU: the library loads, exports what include/admm.h
+declares, and its host logic (partitioner, launch plan, argument checks)
+behaves."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT, gpu_available
+from oracle import admm_fp64 as A
+
+HEADER = os.path.join(ROOT, "include", "admm.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(admm_[a-z_]+)\s*\(", text)))
+
+
+def test_library_loads_and_exports_every_declared_symbol(cuda_lib):
+    names = declared_functions()
+    assert "admm_setup" in names and "admm_iterate" in names and "admm_solve" in names
+    for name in names:
+        assert hasattr(cuda_lib, name), name
+    # and nothing that the binding expects is missing from the header
+    from paper_1811_05571_gb300 import _binding
+    assert set(_binding.SIGNATURES) == set(names)
+
+
+def test_abi_version_and_strerror(cuda_lib):
+    import paper_1811_05571_gb300 as P
+    assert P.admm_abi_version() == 1
+    for code in range(0, 9):
+        assert P.admm_strerror(code)
+    assert P.admm_strerror(99) == "unknown status"
+
+
+@pytest.mark.parametrize("total,parts", [(10, 3), (1440, 8), (32768, 8), (101, 4), (7, 7), (5, 1)])
+def test_partition_matches_oracle_partitioner(cuda_lib, total, parts):
+    import paper_1811_05571_gb300 as P
+    off = P.admm_partition(total, parts)
+    want = [a for a, _ in A.balanced_blocks(total, parts)] + [total]
+    assert off == want
+
+
+def test_partition_rejects_bad_arguments(cuda_lib):
+    import paper_1811_05571_gb300 as P
+    with pytest.raises(P.AdmmError):
+        P.admm_partition(3, 4)
+    with pytest.raises(P.AdmmError):
+        P.admm_partition(3, 0)
+
+
+PLAN_CASES = [(256, 4096, 4, 1), (1440, 32768, 8, 1), (1440, 32768, 1, 8), (1440, 32768, 4, 4),
+              (100, 1000, 3, 3), (37, 517, 3, 5), (300, 3001, 7, 2), (12, 32, 1, 2),
+              (2048, 16384, 8, 1), (8192, 131072, 16, 1), (16, 64, 4, 4)]
+
+
+@pytest.mark.parametrize("m,n,M,N", PLAN_CASES)
+def test_plan_slabs_cover_columns_and_fit_limits(cuda_lib, m, n, M, N):
+    import paper_1811_05571_gb300 as P
+    plan, cols = P.admm_plan(m, n, M, N, num_sms=152, smem_limit=232448)
+    ld = plan["ld"]
+    assert ld >= n and ld % 32 == 0
+    assert cols[0] == 0 and cols[-1] == ld and len(cols) == plan["ctas"] + 1
+    widths = np.diff(cols)
+    assert np.all(widths > 0) and np.all(widths % 2 == 0)       # 16-byte pairs, TMA x aligned
+    assert widths.max() - widths.min() <= 2                      # balanced
+    assert widths.max() == plan["slab_cols"]
+    assert plan["ctas"] <= 152
+    assert plan["box_cols"] % 2 == 0 and plan["box_cols"] <= 256
+    assert plan["box_cols"] * plan["boxes_per_row"] >= plan["slab_cols"]
+    assert plan["slab_cols"] // 2 <= 32 * plan["chunks"]
+    assert plan["rows_per_stage"] % 8 == 0 and 8 <= plan["rows_per_stage"] <= 64
+    assert 2 <= plan["stages"] <= 8
+    assert plan["smem_bytes"] <= 232448
+    assert 1 <= plan["max_blocks_per_slab"] <= 4
+    # every slab touches the blocks its columns fall in
+    col_off = [a for a, _ in A.balanced_blocks(n, N)] + [n]
+    touched = []
+    for c0, c1 in zip(cols[:-1], cols[1:]):
+        lo = np.searchsorted(col_off, c0, side="right") - 1
+        hi = min(np.searchsorted(col_off, c1 - 1, side="right") - 1, N - 1)
+        touched.append(hi - min(lo, N - 1) + 1)
+    assert max(touched) == plan["max_blocks_per_slab"]
+
+
+def test_plan_rejects_too_narrow_column_blocks(cuda_lib):
+    import paper_1811_05571_gb300 as P
+    with pytest.raises(P.AdmmError) as e:
+        P.admm_plan(8, 64, 1, 16, num_sms=1, smem_limit=232448)
+    assert e.value.status == P.ADMM_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(m=0), 1), (dict(n=0), 1), (dict(M=9), 1), (dict(N=300), 1), (dict(M=16, N=17), 1),
+    (dict(lam=-1.0), 1), (dict(lam=float("nan")), 1), (dict(rho=0.0), 1), (dict(rho=float("inf")), 1),
+    (dict(dtype=7), 1), (dict(M=1, N=2, m=8, n=8), 7),
+])
+def test_setup_argument_checks_need_no_gpu(cuda_lib, kw, code):
+    """Invalid arguments are rejected on the host before any CUDA call."""
+    import paper_1811_05571_gb300 as P
+    args = dict(m=8, n=64, M=2, N=1, lam=0.1, rho=1.0, dtype=P.ADMM_C64)
+    args.update(kw)
+    H = np.zeros((max(args["m"], 1), max(args["n"], 1)), np.complex64)
+    g = np.zeros(max(args["m"], 1), np.complex64)
+    with pytest.raises(P.AdmmError) as e:
+        P.admm_setup(H, g, args["m"], args["n"], args["M"], args["N"], args["lam"], args["rho"],
+                     args["dtype"])
+    assert e.value.status == code
+
+
+def test_null_pointers_rejected(cuda_lib):
+    import paper_1811_05571_gb300 as P
+    h = ctypes.c_void_p()
+    assert cuda_lib.admm_setup(ctypes.byref(h), None, None, 4, 8, 1, 1, 0.1, 1.0, 0, None) == P.ADMM_EINVAL
+    assert cuda_lib.admm_setup(None, None, None, 4, 8, 1, 1, 0.1, 1.0, 0, None) == P.ADMM_EINVAL
+    assert cuda_lib.admm_iterate(None, 1, None) == P.ADMM_EINVAL
+    assert cuda_lib.admm_get_info(None, None) == P.ADMM_EINVAL
+    cuda_lib.admm_destroy(None)
+
+
+@pytest.mark.skipif(gpu_available(), reason="checks the no-GPU error path")
+def test_setup_without_gpu_reports_cuda_error(cuda_lib):
+    import paper_1811_05571_gb300 as P
+    H = np.zeros((4, 64), np.complex64)
+    g = np.zeros(4, np.complex64)
+    with pytest.raises(P.AdmmError) as e:
+        P.admm_setup(H, g, 4, 64, 2, 1, 0.1, 1.0)
+    assert e.value.status == P.ADMM_ECUDA
