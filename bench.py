@@ -47,9 +47,12 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--cpu-iters", type=int, default=4,
+    ap.add_argument("--cpu-iters", type=int, default=12,
                     help="iterations per split in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trace", type=int, default=0,
+                    help="after the timed region, run this many traced iterations per split and "
+                         "report the median time of each phase")
     ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -127,27 +130,32 @@ class ClockSampler:
 # the oracle on the host cores (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_iteration_seconds(p, iters: int, warmup: int) -> dict:
-    """Per-split seconds per oracle iteration: (T(iters) - T(0)) / iters, so
-    the one-time factorisation of each call is not charged to the iterations."""
+def oracle_iteration_seconds(p, iters: dict, warmup: int) -> dict:
+    """Per-split seconds per oracle iteration from two runs of the oracle as it
+    stands: (T(warmup + k) - T(warmup)) / k, so its one-time factorisation and
+    the warm-up iterations cancel.  `iters` maps a split name to k."""
     import oracle
     out = {}
     for M, N in SPLITS:
-        if warmup:
-            oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, warmup)
+        name = f"{M}x{N}"
+        k = max(int(iters[name]), 1)
         t0 = time.perf_counter()
-        oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, 0)
-        t_setup = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, iters)
-        t_run = time.perf_counter() - t0
-        out[f"{M}x{N}"] = max(t_run - t_setup, 1e-9) / iters
+        oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, warmup)
+        t1 = time.perf_counter()
+        oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, warmup + k)
+        t2 = time.perf_counter()
+        out[name] = max((t2 - t1) - (t1 - t0), 1e-9) / k
     return out
+
+
+def sample_iters(base: int) -> dict:
+    # the consensus oracle iteration is ~10x cheaper than the column splits'
+    return {"8x1": 8 * base, "1x8": base, "4x4": base}
 
 
 def cpu_sample_worker(args) -> None:
     p = make_problem(0)
-    per = oracle_iteration_seconds(p, args.cpu_iters, 0)
+    per = oracle_iteration_seconds(p, sample_iters(args.cpu_iters), 2)
     print(json.dumps({"per_iter_s": per, "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))}))
 
 
@@ -166,9 +174,9 @@ def cpu_baseline(iters: int) -> dict:
     d = json.loads(res.stdout.strip().splitlines()[-1])
     total = sum(d["per_iter_s"].values())
     return {"value": len(SPLITS) / total, "unit": UNIT, "cores": d["cores"], "kind": "oracle",
-            "sample": (f"{iters} FP64 oracle iterations of each split 8x1/1x8/4x4 on the full "
-                       f"1440x32768 CRA workload, factorisation excluded; numpy/OpenBLAS with "
-                       f"{d['cores']} threads"),
+            "sample": (f"FP64 oracle on the full 1440x32768 CRA workload: {sample_iters(iters)} "
+                       f"iterations per split after 2 warm-up, factorisation excluded "
+                       f"(difference of two runs); numpy/OpenBLAS with {d['cores']} threads"),
             "per_iter_s": d["per_iter_s"]}
 
 
@@ -177,7 +185,8 @@ def run_reference(args) -> None:
     if rank != 0:
         return
     p = make_problem(0)
-    per = oracle_iteration_seconds(p, max(args.steps, 1), args.warmup)
+    k = max(args.steps, 1)
+    per = oracle_iteration_seconds(p, {f"{M}x{N}": k for M, N in SPLITS}, args.warmup)
     step_s = sum(per.values())
     value = len(SPLITS) / step_s
     cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
@@ -190,7 +199,8 @@ def run_reference(args) -> None:
                    "splits": [f"{M}x{N}" for M, N in SPLITS], "parallelism": "host cores"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": (f"{args.steps} FP64 oracle iterations of each split after "
-                                    f"{args.warmup} warm-up, factorisation excluded")},
+                                    f"{args.warmup} warm-up, factorisation excluded "
+                                    f"(difference of two runs)")},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "splits": {k: {"iters_per_s": 1.0 / v} for k, v in per.items()},
     }
@@ -294,6 +304,23 @@ def run_ours(args) -> None:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
 
+    phases = None
+    if args.trace > 0:
+        import numpy as np
+        import paper_1811_05571_gb300 as pkg2
+        phases = {}
+        names = ["pass_up", "barrier1", "reduce", "barrier2", "factor", "barrier3", "pass_down"]
+        for (M, N), s in zip(SPLITS, solvers):
+            s.set_option(pkg2.ADMM_OPT_TRACE_ITERS, args.trace)
+            s.iterate(args.trace)
+            tr = s.trace(args.trace).astype(np.float64)   # (2, k, 8) ns
+            s.set_option(pkg2.ADMM_OPT_TRACE_ITERS, 0)
+            d = np.diff(tr[0], axis=1)                     # CTA 0
+            it_ns = np.diff(tr[0][:, 0]) if tr.shape[1] > 1 else np.array([tr[0][0, 7] - tr[0][0, 0]])
+            phases[f"{M}x{N}"] = {"us": {n: float(np.median(d[:, q])) / 1e3 for q, n in enumerate(names)},
+                                  "iteration_us": float(np.median(it_ns)) / 1e3}
+        torch.cuda.synchronize()
+
     peaks = load_peaks()
     per_split = {}
     bytes_total, time_total = 0.0, 0.0
@@ -334,6 +361,8 @@ def run_ours(args) -> None:
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if phases is not None:
+        line["phases"] = phases
     for s in solvers:
         s.close()
     if rank == 0:

@@ -70,6 +70,8 @@ extern "C" {
 #define ADMM_OPT_BARRIER_EXTRA 3  /* fault injection: make every grid barrier wait for this many
                                      CTAs that do not exist, so the bounded wait expires and the
                                      call ends with ADMM_ETIMEOUT (0 = off, the default) */
+#define ADMM_OPT_TRACE_ITERS   4  /* record %globaltimer phase stamps of the first `value`
+                                     iterations of each launch (0 = off, the default) */
 
 typedef struct admm_problem admm_t;
 
@@ -126,8 +128,12 @@ int admm_partition(int64_t total, int32_t parts, int64_t* offsets);
 /* Plan of the persistent iteration kernel for an m x n problem split into
  * row_blocks x col_blocks on a GPU with `num_sms` SMs and `smem_limit` bytes of
  * opt-in shared memory per block.  Host only, no GPU needed.  When
- * cta_cols != NULL it receives ctas+1 slab offsets (columns, even, the last
- * one equal to plan->ld); the buffer must hold num_sms+1 entries.
+ * cta_cols != NULL it receives 4*ctas entries, per CTA the [begin, end)
+ * column range (even numbers) of its slab of H followed by the [first, last+1)
+ * range of the columns whose state it owns; the buffer must hold 4*num_sms
+ * entries.  Slabs are aligned to column blocks when col_blocks <= ctas, and
+ * two neighbouring slabs then share the 16-byte column pair holding an odd
+ * block boundary, each owning one of its columns.
  * ADMM_EINVAL for bad sizes, ADMM_EUNSUPPORTED when the slab or the shared
  * memory needs exceed what the kernel supports. */
 int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks,
@@ -227,6 +233,15 @@ int admm_get_info(const admm_t* h, admm_info_t* info);
 
 /* Set an ADMM_OPT_* option. */
 int admm_set_option(admm_t* h, int32_t option, int64_t value);
+
+/* Phase trace of the last launch (needs ADMM_OPT_TRACE_ITERS > 0): for CTA 0
+ * and the last CTA, and for each of the first min(cap, trace length)
+ * iterations, 8 %globaltimer stamps in nanoseconds: iteration start, first
+ * pass over H done, first grid barrier passed, partial sums reduced, second
+ * barrier passed, factors applied, third barrier passed, second pass and
+ * state update done.  `out` holds 2 * cap * 8 int64 (CTA 0 first); *count
+ * receives the iterations written per CTA.  Synchronises `stream`. */
+int admm_get_trace(admm_t* h, int64_t* out, int32_t cap, int32_t* count, void* stream);
 
 /* Synchronise `stream` and return the sticky device status of `h`. */
 int admm_status(admm_t* h, void* stream);

@@ -11,11 +11,11 @@ failure to build or load raises instead of falling back to other code.
 from ._binding import (  # noqa: F401
     ADMM_C64, ADMM_C128, ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ENOTPD,
     ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED,
-    ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA,
+    ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS,
     AdmmError, load, library_path,
     admm_abi_version, admm_strerror, admm_partition, admm_plan, admm_setup, admm_iterate,
     admm_solve, admm_get_v, admm_get_u, admm_get_residuals, admm_set_g, admm_set_lambda,
     admm_set_rho, admm_reset, admm_get_state, admm_set_state, admm_get_info, admm_set_option,
-    admm_status, admm_destroy,
+    admm_get_trace, admm_status, admm_destroy,
 )
 from .solver import Solver  # noqa: F401

@@ -19,7 +19,7 @@ c_int32, c_int64, c_double, c_void_p = ctypes.c_int32, ctypes.c_int64, ctypes.c_
 ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ENOTPD = 0, 1, 2, 3, 4
 ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED = 5, 6, 7, 8
 ADMM_C64, ADMM_C128 = 0, 1
-ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA = 1, 2, 3
+ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS = 1, 2, 3, 4
 
 
 class AdmmInfo(ctypes.Structure):
@@ -78,6 +78,8 @@ SIGNATURES = {
     "admm_set_state": (c_int32, [c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_void_p]),
     "admm_get_info": (c_int32, [c_void_p, ctypes.POINTER(AdmmInfo)]),
     "admm_set_option": (c_int32, [c_void_p, c_int32, c_int64]),
+    "admm_get_trace": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32,
+                                 ctypes.POINTER(c_int32), c_void_p]),
     "admm_status": (c_int32, [c_void_p, c_void_p]),
     "admm_destroy": (None, [c_void_p]),
 }
@@ -163,11 +165,14 @@ def admm_partition(total: int, parts: int) -> list[int]:
 
 def admm_plan(m: int, n: int, row_blocks: int, col_blocks: int, num_sms: int = 152,
               smem_limit: int = 232448):
+    """Plan of the iteration kernel and, per CTA, (slab begin, slab end, first
+    owned column, one past the last owned column)."""
     plan = AdmmPlan()
-    cols = (c_int32 * (num_sms + 1))()
+    cols = (c_int32 * (4 * num_sms))()
     _check(load().admm_plan(m, n, row_blocks, col_blocks, num_sms, smem_limit, ctypes.byref(plan),
                             cols))
-    return plan.as_dict(), list(cols)[: plan.ctas + 1]
+    flat = list(cols)[: 4 * plan.ctas]
+    return plan.as_dict(), [tuple(flat[4 * c: 4 * c + 4]) for c in range(plan.ctas)]
 
 
 def admm_setup(H, g, m: int, n: int, row_blocks: int, col_blocks: int, lam: float, rho: float,
@@ -240,6 +245,18 @@ def admm_get_info(h: int) -> dict:
 
 def admm_set_option(h: int, option: int, value: int) -> None:
     _check(load().admm_set_option(h, option, value), h)
+
+
+def admm_get_trace(h: int, cap: int, stream=None):
+    """(2, k, 8) int64 phase stamps of CTA 0 and the last CTA (see include/admm.h)."""
+    import numpy as np
+    out = np.zeros((2, max(cap, 1), 8), dtype=np.int64)
+    count = c_int32(0)
+    _check(load().admm_get_trace(h, out.ctypes.data_as(ctypes.POINTER(c_int64)), cap,
+                                 ctypes.byref(count), _stream(stream)), h)
+    k = count.value
+    flat = out.reshape(-1)[: 2 * k * 8]
+    return flat.reshape(2, k, 8)
 
 
 def admm_status(h: int, stream=None) -> int:

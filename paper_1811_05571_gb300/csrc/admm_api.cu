@@ -38,7 +38,8 @@ struct admm_problem {
     float2* kinv = nullptr;
     long long* kinv_off_d = nullptr;
     int* ints_d = nullptr;  // all int tables in one allocation
-    int *row_off_d = nullptr, *col_off_d = nullptr, *cta_col_d = nullptr, *cta_jlo_d = nullptr,
+    int *row_off_d = nullptr, *col_off_d = nullptr, *cta_col_d = nullptr, *cta_end_d = nullptr,
+        *cta_own0_d = nullptr, *cta_own1_d = nullptr, *cta_jlo_d = nullptr,
         *cta_nj_d = nullptr, *j_cta_lo_d = nullptr, *j_cta_hi_d = nullptr, *solve_lo_d = nullptr,
         *kinv_pitch_d = nullptr;
     double *res_part = nullptr, *hist = nullptr;
@@ -54,6 +55,8 @@ struct admm_problem {
     long long timeout_ns = 5000000000LL;
     int hist_cap = 4096;
     int bar_extra = 0;
+    long long* trace = nullptr;  // phase timestamps, 2 x trace_iters x 8
+    int trace_iters = 0;
     int64_t k = 0;       // iterations completed (host mirror)
     int broken = 0;      // sticky error that blocks further iterations
     double gram_ms = 0.0, factor_ms = 0.0;
@@ -94,7 +97,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(admm_t* h) {
     void* ptrs[] = {h->H, h->g, h->v, h->s, h->u, h->ghat, h->gt, h->r, h->w, h->part, h->kinv,
                     h->kinv_off_d, h->ints_d, h->res_part, h->hist, h->k_done, h->bar, h->status,
-                    h->stop_flag};
+                    h->stop_flag, h->trace};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -128,15 +131,105 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     }
     pl = Plan();
     pl.ld = round_up(n, 32);
-    const int pairs = pl.ld / 2;
-    pl.P = static_cast<int>(std::min<int64_t>(num_sms, std::max<int64_t>(1, pl.ld / 64)));
-    // column slabs: balanced in 16-byte pairs
-    std::vector<int> poff;
-    balanced_offsets(pairs, pl.P, poff);
-    pl.cta_col.resize(pl.P + 1);
-    for (int c = 0; c <= pl.P; ++c) pl.cta_col[c] = 2 * poff[c];
+    const int ld = pl.ld;
+    const int P0 = static_cast<int>(std::min<int64_t>(num_sms, std::max<int64_t>(1, ld / 64)));
+    // column range of block j with the padding columns given to the last block
+    auto blk_lo = [&](int j) { return col_off[j]; };
+    auto blk_hi = [&](int j) { return j == N - 1 ? ld : col_off[j + 1]; };
+    pl.aligned = N <= P0;
+    if (pl.aligned) {
+        // CTAs per column block in proportion to its width (largest remainders),
+        // at least one each and never more than the block's 16-byte pairs
+        std::vector<int> cnt(N, 1), pairs(N);
+        std::vector<double> frac(N);
+        int used = 0;
+        for (int j = 0; j < N; ++j) {
+            const int a = blk_lo(j) & ~1, b = (blk_hi(j) + 1) & ~1;
+            pairs[j] = (b - a) / 2;
+            const double quota = static_cast<double>(P0) * (blk_hi(j) - blk_lo(j)) / ld;
+            cnt[j] = std::max(1, std::min(pairs[j], static_cast<int>(std::floor(quota))));
+            frac[j] = quota - std::floor(quota);
+            used += cnt[j];
+        }
+        while (used < P0) {
+            int best = -1;
+            for (int j = 0; j < N; ++j)
+                if (cnt[j] < pairs[j] && (best < 0 || frac[j] > frac[best])) best = j;
+            if (best < 0) break;
+            ++cnt[best];
+            frac[best] -= 1.0;
+            ++used;
+        }
+        while (used > P0) {
+            int best = -1;
+            for (int j = 0; j < N; ++j)
+                if (cnt[j] > 1 && (best < 0 || cnt[j] > cnt[best])) best = j;
+            --cnt[best];
+            --used;
+        }
+        pl.P = used;
+        for (int j = 0; j < N; ++j) {
+            const int a = blk_lo(j) & ~1;
+            std::vector<int> off;
+            balanced_offsets(pairs[j], cnt[j], off);
+            for (int q = 0; q < cnt[j]; ++q) {
+                const int beg = a + 2 * off[q], end = a + 2 * off[q + 1];
+                pl.cta_beg.push_back(beg);
+                pl.cta_end.push_back(end);
+                pl.cta_own0.push_back(q == 0 ? blk_lo(j) : beg);
+                pl.cta_own1.push_back(q == cnt[j] - 1 ? blk_hi(j) : end);
+                pl.cta_jlo.push_back(j);
+                pl.cta_nj.push_back(1);
+            }
+        }
+    } else {
+        // more column blocks than CTAs: balanced slabs, each meeting several blocks
+        pl.P = P0;
+        std::vector<int> poff;
+        balanced_offsets(ld / 2, pl.P, poff);
+        auto block_of_col = [&](int c) {
+            int j = static_cast<int>(std::upper_bound(col_off.begin(), col_off.end(), c) - col_off.begin()) - 1;
+            return std::min(std::max(j, 0), N - 1);
+        };
+        for (int c = 0; c < pl.P; ++c) {
+            const int beg = 2 * poff[c], end = 2 * poff[c + 1];
+            const int jlo = block_of_col(beg), jhi = block_of_col(end - 1);
+            pl.cta_beg.push_back(beg);
+            pl.cta_end.push_back(end);
+            pl.cta_own0.push_back(beg);
+            pl.cta_own1.push_back(end);
+            pl.cta_jlo.push_back(jlo);
+            pl.cta_nj.push_back(jhi - jlo + 1);
+        }
+    }
+    pl.j_cta_lo.assign(N, pl.P);
+    pl.j_cta_hi.assign(N, -1);
+    pl.njs = 1;
     pl.wmax = 0;
-    for (int c = 0; c < pl.P; ++c) pl.wmax = std::max(pl.wmax, pl.cta_col[c + 1] - pl.cta_col[c]);
+    for (int c = 0; c < pl.P; ++c) {
+        pl.wmax = std::max(pl.wmax, pl.cta_end[c] - pl.cta_beg[c]);
+        pl.njs = std::max(pl.njs, pl.cta_nj[c]);
+        for (int j = pl.cta_jlo[c]; j < pl.cta_jlo[c] + pl.cta_nj[c]; ++j) {
+            // a CTA contributes to block j only through columns it owns
+            if (std::max(pl.cta_own0[c], blk_lo(j)) >= std::min(pl.cta_own1[c], blk_hi(j))) continue;
+            pl.j_cta_lo[j] = std::min(pl.j_cta_lo[j], c);
+            pl.j_cta_hi[j] = std::max(pl.j_cta_hi[j], c);
+        }
+    }
+    if (pl.njs > kMaxBlocksPerSlab) {
+        *why = "a CTA column slab would touch more than 4 column blocks (column blocks too narrow)";
+        return ADMM_EUNSUPPORTED;
+    }
+    int most = 1;
+    for (int j = 0; j < N; ++j) {
+        if (pl.j_cta_hi[j] < pl.j_cta_lo[j]) {
+            *why = "internal: column block without a slab";
+            return ADMM_EINVAL;
+        }
+        most = std::max(most, pl.j_cta_hi[j] - pl.j_cta_lo[j] + 1);
+    }
+    pl.red_lanes = 1;
+    while (pl.red_lanes < 32 && pl.red_lanes * 4 < most) pl.red_lanes *= 2;
     pl.npmax = pl.wmax / 2;
     const int need = (pl.npmax + 31) / 32;
     int ch = 1;
@@ -148,79 +241,31 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     pl.chunks = ch;
     pl.nsub = (pl.wmax + 255) / 256;
     pl.wbox = round_up((pl.wmax + pl.nsub - 1) / pl.nsub, 2);
-    // column blocks touched by each slab (padding columns belong to the last block)
-    auto block_of_col = [&](int c) {
-        int j = static_cast<int>(std::upper_bound(col_off.begin(), col_off.end(), c) - col_off.begin()) - 1;
-        return std::min(std::max(j, 0), N - 1);
-    };
-    pl.cta_jlo.resize(pl.P);
-    pl.cta_nj.resize(pl.P);
-    pl.j_cta_lo.assign(N, pl.P);
-    pl.j_cta_hi.assign(N, -1);
-    pl.njs = 1;
-    for (int c = 0; c < pl.P; ++c) {
-        const int jlo = block_of_col(pl.cta_col[c]);
-        const int jhi = block_of_col(pl.cta_col[c + 1] - 1);
-        pl.cta_jlo[c] = jlo;
-        pl.cta_nj[c] = jhi - jlo + 1;
-        pl.njs = std::max(pl.njs, jhi - jlo + 1);
-        for (int j = jlo; j <= jhi; ++j) {
-            pl.j_cta_lo[j] = std::min(pl.j_cta_lo[j], c);
-            pl.j_cta_hi[j] = std::max(pl.j_cta_hi[j], c);
-        }
-    }
-    if (pl.njs > kMaxBlocksPerSlab) {
-        *why = "a CTA column slab would touch more than 4 column blocks (column blocks too narrow)";
-        return ADMM_EUNSUPPORTED;
-    }
-    for (int j = 0; j < N; ++j)
-        if (pl.j_cta_hi[j] < pl.j_cta_lo[j]) {
-            *why = "internal: column block without a slab";
-            return ADMM_EINVAL;
-        }
+    const int npitch = pl.wbox * pl.nsub / 2;   // pair pitch of the per-pair buffers
     pl.mimax = 0;
     for (int i = 0; i < M; ++i) pl.mimax = std::max(pl.mimax, row_off[i + 1] - row_off[i]);
     pl.kpmax = round_up(pl.mimax, 4);
-    // shared memory: fixed regions, then the largest ring that fits
-    const int ws = pl.njs * pl.mimax * 8;
+    pl.ws_all = static_cast<int64_t>(m) * pl.njs * 8 <= 48 * 1024;
+    pl.ws_rows = pl.ws_all ? static_cast<int>(m) : pl.mimax;
+    // shared memory: fixed regions, then the deepest ring that fits
+    const int ws = pl.njs * pl.ws_rows * 8;
     const int rs = pl.kpmax * 8;
-    const int red = kConsumerWarps * pl.npmax * 16;
-    const int usum = pl.npmax * 16;
+    pl.red_single = 2 * kConsumerWarps * npitch * 16 > 64 * 1024;
+    pl.sigma_global = static_cast<int64_t>(M) * npitch * 16 > 32 * 1024;
+    const int red = (pl.red_single ? 1 : 2) * kConsumerWarps * npitch * 16;
+    const int sigma = pl.sigma_global ? 0 : M * npitch * 16;
     const int misc = 1024;
-    const int bars = 2 * 8 * 8;
     const int fixed = round_up(ws, 128) + round_up(rs, 128) + round_up(red, 128) +
-                      round_up(usum, 128) + misc + bars + 1024;
-    const int avail = smem_limit - fixed;
-    const int mi_rows = round_up(pl.mimax, 8);
-    int chosen = 0, stages = 0;
-    for (int R : {64, 32, 16, 8}) {
-        if (R > mi_rows && R > 8) continue;
-        const int sb = R * pl.nsub * pl.wbox * 8;
-        const int stride = round_up(sb, 128);
-        const int ns = std::min(8, avail / stride);
-        if (sb <= 48 * 1024 && ns >= 4) {
-            chosen = R;
-            stages = ns;
-            break;
-        }
-    }
-    if (!chosen) {
-        const int sb = 8 * pl.nsub * pl.wbox * 8;
-        const int ns = std::min(8, avail / round_up(sb, 128));
-        if (ns >= 2) {
-            chosen = 8;
-            stages = ns;
-        }
-    }
-    if (!chosen) {
-        *why = "shared memory too small for two pipeline stages";
-        return ADMM_EUNSUPPORTED;
-    }
-    pl.R = chosen;
-    pl.nstages = stages;
+                      round_up(sigma, 128) + misc + 256 + 1024;
+    pl.R = rows_per_stage(pl.chunks);
     pl.sub_bytes = pl.R * pl.wbox * 8;
     pl.stage_bytes = pl.sub_bytes * pl.nsub;
     pl.stage_stride = round_up(pl.stage_bytes, 128);
+    pl.nstages = std::min(8, (smem_limit - fixed) / pl.stage_stride);
+    if (pl.nstages < 2) {
+        *why = "shared memory too small for two pipeline stages";
+        return ADMM_EUNSUPPORTED;
+    }
     int off = 0;
     pl.off_ring = off;
     off += pl.stage_stride * pl.nstages;
@@ -236,8 +281,8 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     off += round_up(rs, 128);
     pl.off_red = off;
     off += round_up(red, 128);
-    pl.off_usum = off;
-    off += round_up(usum, 128);
+    pl.off_sigma = off;
+    off += round_up(sigma, 128);
     pl.off_misc = off;
     off += misc;
     pl.smem = off;
@@ -419,8 +464,13 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.off_ws = pl.off_ws;
     a.off_rs = pl.off_rs;
     a.off_red = pl.off_red;
-    a.off_usum = pl.off_usum;
+    a.off_sigma = pl.off_sigma;
     a.off_misc = pl.off_misc;
+    a.red_lanes = pl.red_lanes;
+    a.ws_all = pl.ws_all ? 1 : 0;
+    a.ws_rows = pl.ws_rows;
+    a.sigma_global = pl.sigma_global ? 1 : 0;
+    a.red_single = pl.red_single ? 1 : 0;
     a.rho = static_cast<float>(h->rho);
     a.rho_d = h->rho;
     a.kappa = static_cast<float>(h->lambda / (h->M * h->rho));
@@ -428,6 +478,9 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.row_off = h->row_off_d;
     a.col_off = h->col_off_d;
     a.cta_col = h->cta_col_d;
+    a.cta_end = h->cta_end_d;
+    a.cta_own0 = h->cta_own0_d;
+    a.cta_own1 = h->cta_own1_d;
     a.cta_jlo = h->cta_jlo_d;
     a.cta_nj = h->cta_nj_d;
     a.j_cta_lo = h->j_cta_lo_d;
@@ -459,6 +512,8 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.eps_rel = eps_rel;
     a.timeout_ns = h->timeout_ns;
     a.bar_extra = h->bar_extra;
+    a.trace = h->trace;
+    a.trace_iters = h->trace_iters;
     cudaError_t e = admm::launch_iterate(h->tmap, a, pl.chunks, pl.smem, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the iteration kernel");
     h->k += iters;
@@ -544,8 +599,14 @@ int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks, int3
     out->smem_bytes = pl.smem;
     out->max_blocks_per_slab = pl.njs;
     out->ld = pl.ld;
-    if (cta_cols)
-        for (int c = 0; c <= pl.P; ++c) cta_cols[c] = pl.cta_col[c];
+    if (cta_cols) {
+        for (int c = 0; c < pl.P; ++c) {
+            cta_cols[4 * c] = pl.cta_beg[c];
+            cta_cols[4 * c + 1] = pl.cta_end[c];
+            cta_cols[4 * c + 2] = pl.cta_own0[c];
+            cta_cols[4 * c + 3] = pl.cta_own1[c];
+        }
+    }
     return ADMM_OK;
 }
 
@@ -630,7 +691,8 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
         ints.insert(ints.end(), x.begin(), x.end());
         return at;
     };
-    const size_t o_row = put(ro), o_col = put(co), o_cta = put(pl.cta_col), o_jlo = put(pl.cta_jlo),
+    const size_t o_row = put(ro), o_col = put(co), o_cta = put(pl.cta_beg), o_end = put(pl.cta_end),
+                 o_own0 = put(pl.cta_own0), o_own1 = put(pl.cta_own1), o_jlo = put(pl.cta_jlo),
                  o_nj = put(pl.cta_nj), o_jl = put(pl.j_cta_lo), o_jh = put(pl.j_cta_hi),
                  o_sl = put(pl.solve_lo), o_kp = put(h->kinv_pitch);
     ok = ok && dalloc(&h->ints_d, ints.size()) == cudaSuccess;
@@ -638,6 +700,9 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     h->row_off_d = h->ints_d + o_row;
     h->col_off_d = h->ints_d + o_col;
     h->cta_col_d = h->ints_d + o_cta;
+    h->cta_end_d = h->ints_d + o_end;
+    h->cta_own0_d = h->ints_d + o_own0;
+    h->cta_own1_d = h->ints_d + o_own1;
     h->cta_jlo_d = h->ints_d + o_jlo;
     h->cta_nj_d = h->ints_d + o_nj;
     h->j_cta_lo_d = h->ints_d + o_jl;
@@ -684,7 +749,8 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     if (code) return bail(code);
     code = encode_tensor_map(h);
     if (code) return bail(code);
-    SETUP_CK(admm::prepare_iterate(pl.chunks, pl.smem));
+    // opt into the device maximum: several handles share one kernel instance
+    SETUP_CK(admm::prepare_iterate(pl.chunks, h->smem_optin));
     int per_sm = 0;
     admm::max_coresident_iterate(pl.chunks, pl.smem, &per_sm);
     if (per_sm * h->num_sms < pl.P)
@@ -868,6 +934,19 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
             CK(h, cudaMemset(h->hist, 0, static_cast<size_t>(value) * 5 * sizeof(double)));
             return ADMM_OK;
         }
+        case ADMM_OPT_TRACE_ITERS: {
+            if (value < 0 || value > (1 << 20)) return fail(h, ADMM_EINVAL, "trace length out of range");
+            CK(h, cudaDeviceSynchronize());
+            if (h->trace) cudaFree(h->trace);
+            h->trace = nullptr;
+            h->trace_iters = 0;
+            if (value > 0) {
+                CK(h, dalloc(&h->trace, static_cast<size_t>(value) * 16));
+                CK(h, cudaMemset(h->trace, 0, static_cast<size_t>(value) * 16 * sizeof(long long)));
+                h->trace_iters = static_cast<int>(value);
+            }
+            return ADMM_OK;
+        }
         case ADMM_OPT_BARRIER_EXTRA:
             if (value < 0 || value > 1024) return fail(h, ADMM_EINVAL, "barrier extra out of range");
             h->bar_extra = static_cast<int>(value);
@@ -875,6 +954,23 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
         default:
             return fail(h, ADMM_EINVAL, "unknown option %d", option);
     }
+}
+
+int admm_get_trace(admm_t* h, int64_t* out, int32_t cap, int32_t* count, void* stream) {
+    if (!h || !out || !count || cap < 0) return h ? fail(h, ADMM_EINVAL, "bad arguments") : ADMM_EINVAL;
+    *count = 0;
+    if (!h->trace) return fail(h, ADMM_EINVAL, "tracing is off (ADMM_OPT_TRACE_ITERS)");
+    CK(h, cudaStreamSynchronize(as_stream(stream)));
+    const int n = std::min(cap, h->trace_iters);
+    std::vector<long long> buf(static_cast<size_t>(h->trace_iters) * 16);
+    CK(h, cudaMemcpy(buf.data(), h->trace, buf.size() * sizeof(long long), cudaMemcpyDeviceToHost));
+    for (int sel = 0; sel < 2; ++sel)
+        for (int it = 0; it < n; ++it)
+            for (int q = 0; q < 8; ++q)
+                out[(static_cast<size_t>(sel) * n + it) * 8 + q] =
+                    buf[(static_cast<size_t>(sel) * h->trace_iters + it) * 8 + q];
+    *count = n;
+    return ADMM_OK;
 }
 
 int admm_status(admm_t* h, void* stream) {

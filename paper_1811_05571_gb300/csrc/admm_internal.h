@@ -27,7 +27,7 @@ struct Plan {
     int chunks = 0;       // per-lane 32-pair chunks (template width)
     int nsub = 0;         // TMA boxes per slab row
     int wbox = 0;         // TMA box width (columns, even, <= 256)
-    int R = 0;            // rows per stage
+    int R = 0;            // rows per stage (fixed by the chunk count)
     int nstages = 0;
     int stage_bytes = 0;  // bytes landed per stage (all boxes)
     int stage_stride = 0; // ring slot stride (128-byte multiple)
@@ -37,8 +37,17 @@ struct Plan {
     int kpmax = 0;        // padded pitch of the tallest factor
     // shared-memory layout (byte offsets into dynamic smem)
     int off_ring = 0, off_full = 0, off_empty = 0, off_ws = 0, off_rs = 0, off_red = 0,
-        off_usum = 0, off_misc = 0, smem = 0;
-    std::vector<int> cta_col;   // P+1 slab starts
+        off_sigma = 0, off_misc = 0, smem = 0;
+    bool aligned = false; // slabs aligned to column blocks (one block per slab)
+    int red_lanes = 32;   // lanes summing the partials of one (block, row) in phase B
+    bool ws_all = false;  // the whole w (m x njs) fits in shared memory
+    int ws_rows = 0;      // rows of the shared w staging buffer
+    bool sigma_global = false;  // H_i^H w_i sums kept in the u buffer (wide slabs, many row blocks)
+    bool red_single = false;    // one cross-warp reduction buffer instead of two
+    std::vector<int> cta_beg;   // P slab starts (even)
+    std::vector<int> cta_end;   // P slab ends (even)
+    std::vector<int> cta_own0;  // P first owned column
+    std::vector<int> cta_own1;  // P one past the last owned column
     std::vector<int> cta_jlo;   // P
     std::vector<int> cta_nj;    // P
     std::vector<int> j_cta_lo;  // N
@@ -58,12 +67,16 @@ struct IterArgs {
     int m, n, ld, M, N, P;
     int R, nstages, stage_bytes, stage_stride, sub_bytes, nsub, wbox;
     int mimax, kpmax;
-    int off_ring, off_full, off_empty, off_ws, off_rs, off_red, off_usum, off_misc;
+    int off_ring, off_full, off_empty, off_ws, off_rs, off_red, off_sigma, off_misc;
+    int red_lanes, ws_all, ws_rows, sigma_global, red_single;
     float rho, kappa, inv_M;
     double rho_d;
     const int* row_off;
     const int* col_off;
-    const int* cta_col;
+    const int* cta_col;   // slab starts
+    const int* cta_end;   // slab ends
+    const int* cta_own0;
+    const int* cta_own1;
     const int* cta_jlo;
     const int* cta_nj;
     const int* j_cta_lo;
@@ -94,7 +107,12 @@ struct IterArgs {
     double eps_abs, eps_rel;
     long long timeout_ns;
     int bar_extra;
+    long long* trace;     // optional phase timestamps (2 CTAs x trace_iters x 8)
+    int trace_iters;
 };
+
+// Rows of H per pipeline stage of the kernel instance with `chunks` chunks.
+int rows_per_stage(int chunks);
 
 // Launch the persistent cooperative iteration kernel for `a.iters` iterations.
 cudaError_t launch_iterate(const CUtensorMap& tmap, const IterArgs& a, int chunks, int smem,

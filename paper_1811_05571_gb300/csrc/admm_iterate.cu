@@ -8,7 +8,7 @@
 //      ghat_b = gt_b - rho w_b
 //   D  u_b = z_b + H_b^H w_b                           (second pass over H),
 //      v_j = S_kappa(mean_i u_j^i + mean_i s_j^i), s_j^i += u_j^i - v_j,
-//      FP64 partial squared residual norms.
+//      squared residual norms (FP32 per thread, FP64 across threads and CTAs).
 // A-D is the paper's u-step (Eq. x_solution, x_solution_columns,
 // x_solution_rows_columns) rewritten with the inversion lemma: with
 // w = K^{-1}(gt - H z),  (H^H H + rho I)^{-1}(H^H gt + rho z) = z + H^H w
@@ -16,13 +16,17 @@
 // (g_rows_columns) costs no extra pass over H.
 //
 // Work layout: CTA c owns the column slab [cta_col[c], cta_col[c+1]) of H and
-// of every state vector for the whole launch.  A producer warp streams that
-// slab row band by row band into a shared-memory ring with 2-D TMA tile
-// loads (mbarrier completion); eight consumer warps each cover whole slab rows
-// (16-byte complex pairs per lane).  Pass A walks rows upwards, pass D
-// downwards, so the rows the previous pass read last are still in L2.  Only
-// the m-length products cross CTAs, through three grid barriers per
-// iteration whose waits are bounded by %globaltimer.
+// the columns [cta_own0[c], cta_own1[c]) of every state vector for the whole
+// launch.  Slabs are aligned to column blocks whenever there are no more
+// column blocks than CTAs, so a slab meets one block; at an odd block
+// boundary the 16-byte pair holding it is read by both neighbours and each
+// masks the column it does not own.  A producer warp streams the slab row
+// band by row band into a shared-memory ring with 2-D TMA tile loads
+// (mbarrier completion); eight consumer warps each cover whole slab rows
+// (16-byte complex pairs per lane) with paired FP32 FMAs.  Pass A walks rows
+// upwards, pass D downwards, so the rows the previous pass read last are still
+// in L2.  Only the m-length products cross CTAs, through three grid barriers
+// per iteration whose waits are bounded by %globaltimer.
 #include "admm_internal.h"
 #include "ptx.cuh"
 
@@ -47,14 +51,19 @@ __device__ __forceinline__ float4 operator-(float4 a, float4 b) {
 __device__ __forceinline__ float4 operator+(float4 a, float4 b) {
     return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w);
 }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float4 scale4(float4 a, float s) {
     return make_float4(a.x * s, a.y * s, a.z * s, a.w * s);
 }
 __device__ __forceinline__ float4 lds128(const unsigned char* p) {
     return *reinterpret_cast<const float4*>(p);
 }
-__device__ __forceinline__ double norm2(float2 a) {
-    return static_cast<double>(a.x) * a.x + static_cast<double>(a.y) * a.y;
+__device__ __forceinline__ float2 lo2(float4 v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(float4 v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float sq(float2 a) { return a.x * a.x + a.y * a.y; }
+__device__ __forceinline__ float2 shfl2(float2 v, int o) {
+    return make_float2(__shfl_xor_sync(0xffffffffu, v.x, o), __shfl_xor_sync(0xffffffffu, v.y, o));
 }
 
 // Complex soft-threshold S_kappa(a) of Eq. (softhresholding): a - kappa a/|a|
@@ -66,6 +75,30 @@ __device__ __forceinline__ float2 soft_threshold(float2 a, float kappa) {
         return make_float2(a.x * sc, a.y * sc);
     }
     return make_float2(0.0f, 0.0f);
+}
+
+// Sum of x[(lane >> 2) & 7] over the 32 lanes, left in every lane whose
+// (lane >> 2) selects that value: 18 shuffles for eight values.
+__device__ __forceinline__ float2 butterfly8(const float2 (&x)[8], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4;
+    float2 y[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 keep = b4 ? x[q + 4] : x[q];
+        const float2 send = b4 ? x[q] : x[q + 4];
+        y[q] = keep + shfl2(send, 16);
+    }
+    float2 z[2];
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const float2 keep = b3 ? y[q + 2] : y[q];
+        const float2 send = b3 ? y[q] : y[q + 2];
+        z[q] = keep + shfl2(send, 8);
+    }
+    float2 w = (b2 ? z[1] : z[0]) + shfl2(b2 ? z[0] : z[1], 4);
+    w = w + shfl2(w, 2);
+    w = w + shfl2(w, 1);
+    return w;
 }
 
 // Sense-reversing grid barrier over the consumer warps of every CTA.  The
@@ -91,7 +124,7 @@ __device__ bool grid_barrier(const IterArgs& a, Misc* misc) {
                     raise_status(a.status, ADMM_ETIMEOUT);
                     break;
                 }
-                __nanosleep(64);
+                __nanosleep(32);
             }
         }
         __threadfence();
@@ -157,8 +190,19 @@ __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* f
 // consumer warps
 // ---------------------------------------------------------------------------
 
+// rows of H per pipeline stage for a slab of CH 32-pair chunks (about 32 KB)
+template <int CH>
+struct RowsOf {
+    static constexpr int value = CH >= 8 ? 8 : 64 / CH;
+};
+
 template <int CH>
 struct Consumer {
+    static constexpr int kR = RowsOf<CH>::value;  // rows per stage
+    static constexpr int kRPW = kR / kConsumerWarps;  // rows per warp per stage
+    static constexpr int kWin = 8 / kRPW;             // stages per 8-row reduction window
+    static constexpr bool kPrefetch = CH <= 4;        // keep v and the next s_i in registers
+
     const IterArgs& a;
     unsigned char* smem;
     Misc* misc;
@@ -166,9 +210,10 @@ struct Consumer {
     uint64_t* empty;
     const unsigned char* ring;
     int tid, warp, lane, cta;
-    int c_beg, npairs, jlo, nj;
+    int c_beg, npairs, jlo, nj, own0, own1, npmax;
     uint32_t valid;       // bit k: pair lane + 32k lies in this slab
-    uint64_t jl;          // 4 bits per chunk: jl of column 0 (bits 0-1), column 1 (bits 2-3)
+    uint32_t owned;       // bit 2k+h: column h of pair lane + 32k is owned by this CTA
+    uint64_t jl;          // 4 bits per chunk: block of column 0 (bits 0-1), column 1 (bits 2-3)
     int soff[CH];         // byte offset of pair lane + 32k inside a stage, row 0
     int stage;            // stages consumed
 
@@ -180,11 +225,15 @@ struct Consumer {
         lane = tid & 31;
         cta = blockIdx.x;
         c_beg = a.cta_col[cta];
-        npairs = (a.cta_col[cta + 1] - c_beg) >> 1;
+        npairs = (a.cta_end[cta] - c_beg) >> 1;
         jlo = a.cta_jlo[cta];
         nj = a.cta_nj[cta];
+        own0 = a.cta_own0[cta];
+        own1 = a.cta_own1[cta];
+        npmax = a.wbox * a.nsub / 2;
         stage = 0;
         valid = 0;
+        owned = 0;
         jl = 0;
         const int ppb = a.wbox >> 1;
 #pragma unroll
@@ -197,9 +246,10 @@ struct Consumer {
                 const int c0 = c_beg + 2 * p;
                 uint64_t bits = 0;
                 for (int h = 0; h < 2; ++h) {
+                    if (c0 + h >= own0 && c0 + h < own1) owned |= 1u << (2 * k + h);
                     int j = jlo;
                     while (j + 1 < a.N && a.col_off[j + 1] <= c0 + h) ++j;
-                    bits |= static_cast<uint64_t>(j - jlo) << (2 * h);
+                    bits |= static_cast<uint64_t>(min(max(j - jlo, 0), 3)) << (2 * h);
                 }
                 jl |= bits << (4 * k);
             }
@@ -207,10 +257,18 @@ struct Consumer {
     }
 
     __device__ __forceinline__ bool is_valid(int k) const { return (valid >> k) & 1u; }
+    __device__ __forceinline__ bool is_owned(int k, int h) const { return (owned >> (2 * k + h)) & 1u; }
     __device__ __forceinline__ int jl_of(int k, int h) const {
         return static_cast<int>((jl >> (4 * k + 2 * h)) & 3u);
     }
     __device__ __forceinline__ int col_of(int k) const { return c_beg + 2 * (lane + 32 * k); }
+
+    __device__ __forceinline__ void stamp(int it, int q) {
+        if (a.trace && it < a.trace_iters && tid == 0 && (cta == 0 || cta == a.P - 1)) {
+            const int sel = cta == 0 ? 0 : 1;
+            a.trace[(static_cast<size_t>(sel) * a.trace_iters + it) * 8 + q] = global_timer_ns();
+        }
+    }
 
     // wait for the next stage; after a local failure, waits are skipped so that
     // every warp still reaches the same named barriers
@@ -229,87 +287,136 @@ struct Consumer {
         ++stage;
     }
 
-    // ---- pass A: partial products of H_b z_b per (row, column block) ------
-    template <bool MULTI>
-    __device__ void pass_rows_up() {
+    // z_i for the lane's pairs, zero in columns this CTA does not own
+    __device__ __forceinline__ float4 z_of(int k, float4 vv, float4 ss) const {
+        float4 z = vv - ss;
+        if (!is_owned(k, 0)) z.x = z.y = 0.f;
+        if (!is_owned(k, 1)) z.z = z.w = 0.f;
+        return z;
+    }
+
+    // ---- pass A (one column block per slab) --------------------------------
+    __device__ void pass_up_single() {
+        const int rowpitch = a.wbox * 8;
+        float4 vreg[kPrefetch ? CH : 1], snext[kPrefetch ? CH : 1];
+        if (kPrefetch) {
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                const int c = col_of(k);
+                vreg[k] = is_valid(k) ? *reinterpret_cast<const float4*>(a.v + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+                snext[k] = is_valid(k) ? *reinterpret_cast<const float4*>(a.s + c) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+        }
+        for (int i = 0; i < a.M; ++i) {
+            const int r0 = a.row_off[i], r1 = a.row_off[i + 1];
+            // (z.re, z.re) and (z.im, z.im) for both columns of every pair
+            float2 zr0[CH], zi0[CH], zr1[CH], zi1[CH];
+#pragma unroll
+            for (int k = 0; k < CH; ++k) {
+                float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (is_valid(k)) {
+                    if (kPrefetch) {
+                        z = z_of(k, vreg[k], snext[k]);
+                    } else {
+                        const int c = col_of(k);
+                        z = z_of(k, *reinterpret_cast<const float4*>(a.v + c),
+                                 *reinterpret_cast<const float4*>(a.s + static_cast<size_t>(i) * a.ld + c));
+                    }
+                }
+                zr0[k] = make_float2(z.x, z.x);
+                zi0[k] = make_float2(z.y, z.y);
+                zr1[k] = make_float2(z.z, z.z);
+                zi1[k] = make_float2(z.w, z.w);
+            }
+            if (kPrefetch && i + 1 < a.M) {
+#pragma unroll
+                for (int k = 0; k < CH; ++k)
+                    if (is_valid(k))
+                        snext[k] = *reinterpret_cast<const float4*>(
+                            a.s + static_cast<size_t>(i + 1) * a.ld + col_of(k));
+            }
+            const int nb = (r1 - r0 + kR - 1) / kR;
+            for (int b0 = 0; b0 < nb; b0 += kWin) {
+                float2 accA[8], accB[8];
+#pragma unroll
+                for (int v = 0; v < 8; ++v) accA[v] = accB[v] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int wi = 0; wi < kWin; ++wi) {
+                    if (b0 + wi < nb) {
+                        int slot;
+                        const unsigned char* buf = acquire_stage(slot);
+#pragma unroll
+                        for (int q = 0; q < kRPW; ++q) {
+                            const int v = wi * kRPW + q;
+                            const unsigned char* rowp = buf + (warp + kConsumerWarps * q) * rowpitch;
+#pragma unroll
+                            for (int k = 0; k < CH; ++k) {
+                                if (is_valid(k)) {
+                                    const float4 h = lds128(rowp + soff[k]);
+                                    accA[v] = fma2(lo2(h), zr0[k], accA[v]);
+                                    accB[v] = fma2(lo2(h), zi0[k], accB[v]);
+                                    accA[v] = fma2(hi2(h), zr1[k], accA[v]);
+                                    accB[v] = fma2(hi2(h), zi1[k], accB[v]);
+                                }
+                            }
+                        }
+                        release_stage(slot);
+                    }
+                }
+                // h z = (sum h.re z.re - h.im z.im, sum h.im z.re + h.re z.im)
+                float2 val[8];
+#pragma unroll
+                for (int v = 0; v < 8; ++v)
+                    val[v] = make_float2(accA[v].x - accB[v].y, accA[v].y + accB[v].x);
+                const float2 sum = butterfly8(val, lane);
+                const int v = lane >> 2;
+                const int wi = v / kRPW, q = v - wi * kRPW;
+                const int row = r0 + (b0 + wi) * kR + warp + kConsumerWarps * q;
+                if ((lane & 3) == 0 && b0 + wi < nb && row < r1)
+                    stcg2(a.part + (static_cast<size_t>(jlo) * a.m + row) * a.P + cta, sum);
+            }
+        }
+    }
+
+    // ---- pass A (slab meeting several column blocks) -------------------------
+    __device__ void pass_up_multi() {
         const int rowpitch = a.wbox * 8;
         for (int i = 0; i < a.M; ++i) {
             const int r0 = a.row_off[i], r1 = a.row_off[i + 1];
             float4 z[CH];
 #pragma unroll
             for (int k = 0; k < CH; ++k) {
+                z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
                 if (is_valid(k)) {
                     const int c = col_of(k);
-                    const float4 vv = *reinterpret_cast<const float4*>(a.v + c);
-                    const float4 ss =
-                        *reinterpret_cast<const float4*>(a.s + static_cast<size_t>(i) * a.ld + c);
-                    z[k] = vv - ss;
-                } else {
-                    z[k] = make_float4(0.f, 0.f, 0.f, 0.f);
+                    z[k] = z_of(k, *reinterpret_cast<const float4*>(a.v + c),
+                                *reinterpret_cast<const float4*>(a.s + static_cast<size_t>(i) * a.ld + c));
                 }
             }
-            const int nb = (r1 - r0 + a.R - 1) / a.R;
+            const int nb = (r1 - r0 + kR - 1) / kR;
             for (int b = 0; b < nb; ++b) {
-                const int y = r0 + b * a.R;
+                const int y = r0 + b * kR;
                 int slot;
                 const unsigned char* buf = acquire_stage(slot);
-                for (int t = warp; t < a.R; t += 2 * kConsumerWarps) {
-                    const int ra = t, rb = t + kConsumerWarps;
-                    const bool in_b = rb < a.R;
-                    const bool oka = y + ra < r1, okb = in_b && (y + rb < r1);
-                    if (!MULTI) {
-                        float2 sa = make_float2(0.f, 0.f), sbv = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int q = 0; q < kRPW; ++q) {
+                    const int row = y + warp + kConsumerWarps * q;
+                    const unsigned char* rowp = buf + (warp + kConsumerWarps * q) * rowpitch;
+                    for (int jj = 0; jj < nj; ++jj) {
+                        float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int k = 0; k < CH; ++k) {
                             if (is_valid(k)) {
-                                const float4 ha = lds128(buf + soff[k] + ra * rowpitch);
-                                cfma(sa, make_float2(ha.x, ha.y), make_float2(z[k].x, z[k].y));
-                                cfma(sa, make_float2(ha.z, ha.w), make_float2(z[k].z, z[k].w));
-                                if (in_b) {
-                                    const float4 hb = lds128(buf + soff[k] + rb * rowpitch);
-                                    cfma(sbv, make_float2(hb.x, hb.y), make_float2(z[k].x, z[k].y));
-                                    cfma(sbv, make_float2(hb.z, hb.w), make_float2(z[k].z, z[k].w));
-                                }
+                                const float2 z0 = jl_of(k, 0) == jj ? lo2(z[k]) : make_float2(0.f, 0.f);
+                                const float2 z1 = jl_of(k, 1) == jj ? hi2(z[k]) : make_float2(0.f, 0.f);
+                                const float4 h = lds128(rowp + soff[k]);
+                                cfma(acc, lo2(h), z0);
+                                cfma(acc, hi2(h), z1);
                             }
                         }
-                        sa = warp_sum(sa);
-                        sbv = warp_sum(sbv);
-                        if (lane == 0) {
-                            const size_t base = static_cast<size_t>(jlo) * a.m;
-                            if (oka)
-                                stcg2(a.part + (base + y + ra) * a.P + cta, sa);
-                            if (okb)
-                                stcg2(a.part + (base + y + rb) * a.P + cta, sbv);
-                        }
-                    } else {
-                        for (int jj = 0; jj < nj; ++jj) {
-                            float2 sa = make_float2(0.f, 0.f), sbv = make_float2(0.f, 0.f);
-#pragma unroll
-                            for (int k = 0; k < CH; ++k) {
-                                if (is_valid(k)) {
-                                    const bool m0 = jl_of(k, 0) == jj, m1 = jl_of(k, 1) == jj;
-                                    const float2 z0 = m0 ? make_float2(z[k].x, z[k].y)
-                                                         : make_float2(0.f, 0.f);
-                                    const float2 z1 = m1 ? make_float2(z[k].z, z[k].w)
-                                                         : make_float2(0.f, 0.f);
-                                    const float4 ha = lds128(buf + soff[k] + ra * rowpitch);
-                                    cfma(sa, make_float2(ha.x, ha.y), z0);
-                                    cfma(sa, make_float2(ha.z, ha.w), z1);
-                                    if (in_b) {
-                                        const float4 hb = lds128(buf + soff[k] + rb * rowpitch);
-                                        cfma(sbv, make_float2(hb.x, hb.y), z0);
-                                        cfma(sbv, make_float2(hb.z, hb.w), z1);
-                                    }
-                                }
-                            }
-                            sa = warp_sum(sa);
-                            sbv = warp_sum(sbv);
-                            if (lane == 0) {
-                                const size_t base = static_cast<size_t>(jlo + jj) * a.m;
-                                if (oka) stcg2(a.part + (base + y + ra) * a.P + cta, sa);
-                                if (okb) stcg2(a.part + (base + y + rb) * a.P + cta, sbv);
-                            }
-                        }
+                        acc = warp_sum(acc);
+                        if (lane == 0 && row < r1)
+                            stcg2(a.part + (static_cast<size_t>(jlo + jj) * a.m + row) * a.P + cta, acc);
                     }
                 }
                 release_stage(slot);
@@ -351,23 +458,27 @@ struct Consumer {
     }
 
     // ---- phase B: r = gt - sum of partials; gt = g_i - sum_{q != j} ghat ----
+    // Groups of red_lanes lanes sum the partials of one (column block, row).
     __device__ void reduce_partials(int it) {
         if (it > 0 && cta == 0 && warp == 0) finalize(it - 1);
-        const int nw = a.P * kConsumerWarps;
+        const int L = a.red_lanes;
+        const int groups = 32 / L;
+        const int g = lane / L, gl = lane - (lane / L) * L;
         const int total = a.N * a.m;
-        for (int idx = cta * kConsumerWarps + warp; idx < total; idx += nw) {
-            const int j = idx / a.m;
-            const int row = idx - j * a.m;
-            const int lo = a.j_cta_lo[j], hi = a.j_cta_hi[j];
-            const float2* pp = a.part + static_cast<size_t>(idx) * a.P;
+        const int stride = a.P * kConsumerWarps * groups;
+        for (int base = (cta * kConsumerWarps + warp) * groups; base < total; base += stride) {
+            const int idx = base + g;
             float2 acc = make_float2(0.f, 0.f);
-            for (int c = lo + lane; c <= hi; c += 32) {
-                const float2 x = ldcg2(pp + c);
-                acc.x += x.x;
-                acc.y += x.y;
+            int j = 0, row = 0;
+            if (idx < total) {
+                j = idx / a.m;
+                row = idx - j * a.m;
+                const int lo = a.j_cta_lo[j], hi = a.j_cta_hi[j];
+                const float2* pp = a.part + static_cast<size_t>(idx) * a.P;
+                for (int c = lo + gl; c <= hi; c += L) acc = acc + ldcg2(pp + c);
             }
-            acc = warp_sum(acc);
-            if (lane == 0) {
+            for (int o = L >> 1; o >= 1; o >>= 1) acc = acc + shfl2(acc, o);
+            if (idx < total && gl == 0) {
                 float2 gtl = __ldg(a.g + row);
                 for (int q = 0; q < a.N; ++q) {
                     if (q == j) continue;
@@ -382,6 +493,7 @@ struct Consumer {
     }
 
     // ---- phase C: w_b = K_b^{-1} r_b, ghat_b = gt_b - rho w_b ----------------
+    // Two factor rows per warp, sixteen 16-byte loads in flight per lane.
     __device__ void apply_factors() {
         float2* rS = reinterpret_cast<float2*>(smem + a.off_rs);
         int idx = a.solve_lo[cta];
@@ -403,171 +515,220 @@ struct Consumer {
             csync();
             const float4* r4 = reinterpret_cast<const float4*>(rS);
             const int kp2 = kp >> 1;
-            for (int q = idx + warp; q < seg_end; q += kConsumerWarps) {
-                const int rl = q - j * a.m - r0;
-                const float4* Kr = reinterpret_cast<const float4*>(K + static_cast<size_t>(rl) * kp);
-                float2 acc0 = make_float2(0.f, 0.f), acc1 = make_float2(0.f, 0.f);
-                int t = lane;
-                for (; t + 32 < kp2; t += 64) {
-                    const float4 k0 = __ldg(Kr + t), k1 = __ldg(Kr + t + 32);
-                    const float4 x0 = r4[t], x1 = r4[t + 32];
-                    cfma(acc0, make_float2(k0.x, k0.y), make_float2(x0.x, x0.y));
-                    cfma(acc0, make_float2(k0.z, k0.w), make_float2(x0.z, x0.w));
-                    cfma(acc1, make_float2(k1.x, k1.y), make_float2(x1.x, x1.y));
-                    cfma(acc1, make_float2(k1.z, k1.w), make_float2(x1.z, x1.w));
+            for (int q = idx + warp; q < seg_end; q += 2 * kConsumerWarps) {
+                const int qb = q + kConsumerWarps;
+                const bool has_b = qb < seg_end;
+                const int rla = q - j * a.m - r0;
+                const int rlb = has_b ? qb - j * a.m - r0 : rla;
+                const float4* Ka = reinterpret_cast<const float4*>(K + static_cast<size_t>(rla) * kp);
+                const float4* Kb = reinterpret_cast<const float4*>(K + static_cast<size_t>(rlb) * kp);
+                float2 aa = make_float2(0.f, 0.f), ab = make_float2(0.f, 0.f);
+                for (int t0 = 0; t0 < kp2; t0 += 256) {
+                    float4 ka[8], kb[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int t = t0 + lane + 32 * u;
+                        ka[u] = t < kp2 ? __ldg(Ka + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        kb[u] = (has_b && t < kp2) ? __ldg(Kb + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int t = t0 + lane + 32 * u;
+                        if (t < kp2) {
+                            const float4 x = r4[t];
+                            cfma(aa, lo2(ka[u]), lo2(x));
+                            cfma(aa, hi2(ka[u]), hi2(x));
+                            cfma(ab, lo2(kb[u]), lo2(x));
+                            cfma(ab, hi2(kb[u]), hi2(x));
+                        }
+                    }
                 }
-                if (t < kp2) {
-                    const float4 k0 = __ldg(Kr + t);
-                    const float4 x0 = r4[t];
-                    cfma(acc0, make_float2(k0.x, k0.y), make_float2(x0.x, x0.y));
-                    cfma(acc0, make_float2(k0.z, k0.w), make_float2(x0.z, x0.w));
-                }
-                float2 acc = make_float2(acc0.x + acc1.x, acc0.y + acc1.y);
-                acc = warp_sum(acc);
+                aa = warp_sum(aa);
+                ab = warp_sum(ab);
                 if (lane == 0) {
-                    stcg2(a.w + q, acc);
-                    const float2 gtl = ldcg2(a.gt + q);
-                    stcg2(a.ghat + q, make_float2(gtl.x - a.rho * acc.x, gtl.y - a.rho * acc.y));
+                    stcg2(a.w + q, aa);
+                    const float2 ga = ldcg2(a.gt + q);
+                    stcg2(a.ghat + q, make_float2(ga.x - a.rho * aa.x, ga.y - a.rho * aa.y));
+                    if (has_b) {
+                        stcg2(a.w + qb, ab);
+                        const float2 gb = ldcg2(a.gt + qb);
+                        stcg2(a.ghat + qb, make_float2(gb.x - a.rho * ab.x, gb.y - a.rho * ab.y));
+                    }
                 }
             }
             idx = seg_end;
         }
     }
 
-    // ---- pass D: u = z + H^H w, then averaging, shrinkage, dual update ------
-    template <bool MULTI>
-    __device__ void pass_rows_down_and_update() {
-        const int rowpitch = a.wbox * 8;
-        float4* usum = reinterpret_cast<float4*>(smem + a.off_usum);
+    // ---- pass D: sigma_i = H_i^H w_i per slab column --------------------------
+    __device__ void stage_w(int r0, int rows, int row_base_in_ws) {
         float2* wS = reinterpret_cast<float2*>(smem + a.off_ws);
+        const int wpitch = a.ws_rows;
+        for (int jj = 0; jj < nj; ++jj)
+            for (int k = tid; k < rows; k += kConsumerThreads)
+                wS[jj * wpitch + row_base_in_ws + k] =
+                    ldcg2(a.w + static_cast<size_t>(jlo + jj) * a.m + r0 + k);
+    }
+
+    template <bool MULTI>
+    __device__ void pass_down() {
+        const int rowpitch = a.wbox * 8;
+        const float2* wS = reinterpret_cast<const float2*>(smem + a.off_ws);
         float4* red = reinterpret_cast<float4*>(smem + a.off_red);
-        const int npmax = a.wbox * a.nsub / 2;
-        for (int p = tid; p < npairs; p += kConsumerThreads) usum[p] = make_float4(0.f, 0.f, 0.f, 0.f);
+        float4* sigma = reinterpret_cast<float4*>(smem + a.off_sigma);
+        const int wpitch = a.ws_rows;
+        if (a.ws_all) {
+            stage_w(0, a.m, 0);
+            csync();
+        }
         for (int bi = 0; bi < a.M; ++bi) {
             const int i = a.M - 1 - bi;
             const int r0 = a.row_off[i], r1 = a.row_off[i + 1], mi = r1 - r0;
-            for (int jj = 0; jj < nj; ++jj)
-                for (int k = tid; k < mi; k += kConsumerThreads)
-                    wS[jj * a.mimax + k] =
-                        ldcg2(a.w + static_cast<size_t>(jlo + jj) * a.m + r0 + k);
-            csync();
-            float4 acc[CH];
+            const int wbase = a.ws_all ? r0 : 0;   // row r of block i sits at wS[r - r0 + wbase]
+            if (!a.ws_all) {
+                stage_w(r0, mi, 0);
+                csync();
+            }
+            // per pair: conj(h) w as (h.re w.re, h.im w.re) and (h.re w.im, h.im w.im)
+            float2 aA0[CH], aB0[CH], aA1[CH], aB1[CH];
 #pragma unroll
-            for (int k = 0; k < CH; ++k) acc[k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            const int nb = (mi + a.R - 1) / a.R;
+            for (int k = 0; k < CH; ++k) aA0[k] = aB0[k] = aA1[k] = aB1[k] = make_float2(0.f, 0.f);
+            const int nb = (mi + kR - 1) / kR;
             for (int b = nb - 1; b >= 0; --b) {
-                const int y = r0 + b * a.R;
+                const int y = r0 + b * kR;
                 int slot;
                 const unsigned char* buf = acquire_stage(slot);
-                for (int t = warp; t < a.R; t += 2 * kConsumerWarps) {
-                    const int ra = t, rb = t + kConsumerWarps;
-                    const bool in_b = rb < a.R;
-                    const bool oka = y + ra < r1, okb = in_b && (y + rb < r1);
+#pragma unroll
+                for (int q = 0; q < kRPW; ++q) {
+                    const int rl = warp + kConsumerWarps * q;
+                    const bool ok = y + rl < r1;
+                    const unsigned char* rowp = buf + rl * rowpitch;
                     if (!MULTI) {
-                        const float2 wa = oka ? wS[y + ra - r0] : make_float2(0.f, 0.f);
-                        const float2 wb = okb ? wS[y + rb - r0] : make_float2(0.f, 0.f);
+                        const float2 wv = ok ? wS[y + rl - r0 + wbase] : make_float2(0.f, 0.f);
+                        const float2 wre = make_float2(wv.x, wv.x), wim = make_float2(wv.y, wv.y);
 #pragma unroll
                         for (int k = 0; k < CH; ++k) {
                             if (is_valid(k)) {
-                                const float4 ha = lds128(buf + soff[k] + ra * rowpitch);
-                                float2 c0 = make_float2(acc[k].x, acc[k].y);
-                                float2 c1 = make_float2(acc[k].z, acc[k].w);
-                                cfma_conj(c0, make_float2(ha.x, ha.y), wa);
-                                cfma_conj(c1, make_float2(ha.z, ha.w), wa);
-                                if (in_b) {
-                                    const float4 hb = lds128(buf + soff[k] + rb * rowpitch);
-                                    cfma_conj(c0, make_float2(hb.x, hb.y), wb);
-                                    cfma_conj(c1, make_float2(hb.z, hb.w), wb);
-                                }
-                                acc[k] = make_float4(c0.x, c0.y, c1.x, c1.y);
+                                const float4 h = lds128(rowp + soff[k]);
+                                aA0[k] = fma2(lo2(h), wre, aA0[k]);
+                                aB0[k] = fma2(lo2(h), wim, aB0[k]);
+                                aA1[k] = fma2(hi2(h), wre, aA1[k]);
+                                aB1[k] = fma2(hi2(h), wim, aB1[k]);
                             }
                         }
                     } else {
-                        float2 wa[kMaxBlocksPerSlab], wb[kMaxBlocksPerSlab];
+                        float2 wv[kMaxBlocksPerSlab];
 #pragma unroll
-                        for (int jj = 0; jj < kMaxBlocksPerSlab; ++jj) {
-                            const bool use = jj < nj;
-                            wa[jj] = (use && oka) ? wS[jj * a.mimax + y + ra - r0] : make_float2(0.f, 0.f);
-                            wb[jj] = (use && okb) ? wS[jj * a.mimax + y + rb - r0] : make_float2(0.f, 0.f);
-                        }
+                        for (int jj = 0; jj < kMaxBlocksPerSlab; ++jj)
+                            wv[jj] = (ok && jj < nj) ? wS[jj * wpitch + y + rl - r0 + wbase]
+                                                     : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int k = 0; k < CH; ++k) {
                             if (is_valid(k)) {
-                                const int j0 = jl_of(k, 0), j1 = jl_of(k, 1);
-                                const float4 ha = lds128(buf + soff[k] + ra * rowpitch);
-                                float2 c0 = make_float2(acc[k].x, acc[k].y);
-                                float2 c1 = make_float2(acc[k].z, acc[k].w);
-                                cfma_conj(c0, make_float2(ha.x, ha.y), wa[j0]);
-                                cfma_conj(c1, make_float2(ha.z, ha.w), wa[j1]);
-                                if (in_b) {
-                                    const float4 hb = lds128(buf + soff[k] + rb * rowpitch);
-                                    cfma_conj(c0, make_float2(hb.x, hb.y), wb[j0]);
-                                    cfma_conj(c1, make_float2(hb.z, hb.w), wb[j1]);
-                                }
-                                acc[k] = make_float4(c0.x, c0.y, c1.x, c1.y);
+                                const float4 h = lds128(rowp + soff[k]);
+                                const float2 w0 = wv[jl_of(k, 0)], w1 = wv[jl_of(k, 1)];
+                                aA0[k] = fma2(lo2(h), make_float2(w0.x, w0.x), aA0[k]);
+                                aB0[k] = fma2(lo2(h), make_float2(w0.y, w0.y), aB0[k]);
+                                aA1[k] = fma2(hi2(h), make_float2(w1.x, w1.x), aA1[k]);
+                                aB1[k] = fma2(hi2(h), make_float2(w1.y, w1.y), aB1[k]);
                             }
                         }
                     }
                 }
                 release_stage(slot);
             }
-            // cross-warp sum of the replica's products, then u_i = z_i + H_i^H w_i
+            // conj(h) w = (h.re w.re + h.im w.im, h.re w.im - h.im w.re); sum over warps
+            float4* rb = red + static_cast<size_t>(a.red_single ? 0 : (bi & 1)) * kConsumerWarps * npmax;
+            if (a.red_single) csync();   // the previous replica's sums have been read
 #pragma unroll
             for (int k = 0; k < CH; ++k)
-                if (is_valid(k)) red[warp * npmax + lane + 32 * k] = acc[k];
+                if (is_valid(k))
+                    rb[warp * npmax + lane + 32 * k] =
+                        make_float4(aA0[k].x + aB0[k].y, aB0[k].x - aA0[k].y,
+                                    aA1[k].x + aB1[k].y, aB1[k].x - aA1[k].y);
             csync();
             for (int p = tid; p < npairs; p += kConsumerThreads) {
-                float4 sum = red[p];
+                float4 s = rb[p];
 #pragma unroll
-                for (int wq = 1; wq < kConsumerWarps; ++wq) sum = sum + red[wq * npmax + p];
-                const int c = c_beg + 2 * p;
-                const float4 vv = *reinterpret_cast<const float4*>(a.v + c);
-                const float4 ss =
-                    *reinterpret_cast<const float4*>(a.s + static_cast<size_t>(i) * a.ld + c);
-                const float4 uu = (vv - ss) + sum;
-                *reinterpret_cast<float4*>(a.u + static_cast<size_t>(i) * a.ld + c) = uu;
-                usum[p] = usum[p] + uu;
+                for (int wq = 1; wq < kConsumerWarps; ++wq) s = s + rb[wq * npmax + p];
+                if (a.sigma_global) {
+                    // an edge pair's other column belongs to the neighbouring CTA
+                    const int c = c_beg + 2 * p;
+                    const bool o0 = c >= own0 && c < own1, o1 = c + 1 >= own0 && c + 1 < own1;
+                    float2* up = reinterpret_cast<float2*>(a.u + static_cast<size_t>(i) * a.ld + c);
+                    if (o0 && o1) {
+                        *reinterpret_cast<float4*>(up) = s;
+                    } else {
+                        if (o0) up[0] = lo2(s);
+                        if (o1) up[1] = hi2(s);
+                    }
+                } else
+                    sigma[static_cast<size_t>(i) * npmax + p] = s;
             }
         }
-        // v = S_kappa(mean u + mean s), s += u - v, FP64 residual partials
-        double rp = 0.0, rdv = 0.0, u2 = 0.0, v2 = 0.0, s2 = 0.0;
+        csync();
+    }
+
+    // H_i^H w_i of pair p (same thread wrote it in pass_down)
+    __device__ __forceinline__ float4 sigma_of(int i, int p) const {
+        if (a.sigma_global)
+            return *reinterpret_cast<const float4*>(a.u + static_cast<size_t>(i) * a.ld + c_beg + 2 * p);
+        return reinterpret_cast<const float4*>(smem + a.off_sigma)[static_cast<size_t>(i) * npmax + p];
+    }
+
+    // ---- epilogue: u_i = z_i + sigma_i, v = S(mean u + mean s), s += u - v ----
+    __device__ void update_state() {
+        float rp = 0.f, rdv = 0.f, u2 = 0.f, v2 = 0.f, s2 = 0.f;
         for (int p = tid; p < npairs; p += kConsumerThreads) {
             const int c = c_beg + 2 * p;
-            const float4 ub = scale4(usum[p], a.inv_M);
-            float4 sb = make_float4(0.f, 0.f, 0.f, 0.f);
-            for (int i = 0; i < a.M; ++i)
-                sb = sb + *reinterpret_cast<const float4*>(a.s + static_cast<size_t>(i) * a.ld + c);
-            sb = scale4(sb, a.inv_M);
-            const float4 av = ub + sb;
-            const float2 vn0 = soft_threshold(make_float2(av.x, av.y), a.kappa);
-            const float2 vn1 = soft_threshold(make_float2(av.z, av.w), a.kappa);
+            const bool o0 = c >= own0 && c < own1, o1 = c + 1 >= own0 && c + 1 < own1;
+            const float4 vv = *reinterpret_cast<const float4*>(a.v + c);
+            float4 us = make_float4(0.f, 0.f, 0.f, 0.f), sb = us;
+            for (int i = 0; i < a.M; ++i) {
+                const float4 ss = *reinterpret_cast<const float4*>(a.s + static_cast<size_t>(i) * a.ld + c);
+                us = us + ((vv - ss) + sigma_of(i, p));
+                sb = sb + ss;
+            }
+            const float4 av = scale4(us + sb, a.inv_M);
+            const float2 vn0 = soft_threshold(lo2(av), a.kappa);
+            const float2 vn1 = soft_threshold(hi2(av), a.kappa);
             const float4 vn = make_float4(vn0.x, vn0.y, vn1.x, vn1.y);
-            const float4 vo = *reinterpret_cast<const float4*>(a.v + c);
-            rdv += norm2(make_float2(vn.x - vo.x, vn.y - vo.y)) + norm2(make_float2(vn.z - vo.z, vn.w - vo.w));
-            v2 += norm2(vn0) + norm2(vn1);
+            const float m0 = o0 ? 1.f : 0.f, m1 = o1 ? 1.f : 0.f;
+            rdv += m0 * sq(make_float2(vn.x - vv.x, vn.y - vv.y)) + m1 * sq(make_float2(vn.z - vv.z, vn.w - vv.w));
+            v2 += m0 * sq(vn0) + m1 * sq(vn1);
             for (int i = 0; i < a.M; ++i) {
                 float4* sp = reinterpret_cast<float4*>(a.s + static_cast<size_t>(i) * a.ld + c);
+                float4* up = reinterpret_cast<float4*>(a.u + static_cast<size_t>(i) * a.ld + c);
                 const float4 ss = *sp;
-                const float4 uu = *reinterpret_cast<const float4*>(a.u + static_cast<size_t>(i) * a.ld + c);
+                const float4 uu = (vv - ss) + sigma_of(i, p);
                 const float4 sn = (ss + uu) - vn;
-                *sp = sn;
-                rp += norm2(make_float2(uu.x - vn.x, uu.y - vn.y)) + norm2(make_float2(uu.z - vn.z, uu.w - vn.w));
-                u2 += norm2(make_float2(uu.x, uu.y)) + norm2(make_float2(uu.z, uu.w));
-                s2 += norm2(make_float2(sn.x, sn.y)) + norm2(make_float2(sn.z, sn.w));
+                rp += m0 * sq(make_float2(uu.x - vn.x, uu.y - vn.y)) + m1 * sq(make_float2(uu.z - vn.z, uu.w - vn.w));
+                u2 += m0 * sq(lo2(uu)) + m1 * sq(hi2(uu));
+                s2 += m0 * sq(lo2(sn)) + m1 * sq(hi2(sn));
+                if (o0 && o1) {
+                    *sp = sn;
+                    *up = uu;
+                } else {
+                    float2* sp2 = reinterpret_cast<float2*>(sp);
+                    float2* up2 = reinterpret_cast<float2*>(up);
+                    if (o0) { sp2[0] = lo2(sn); up2[0] = lo2(uu); }
+                    if (o1) { sp2[1] = hi2(sn); up2[1] = hi2(uu); }
+                }
             }
-            *reinterpret_cast<float4*>(a.v + c) = vn;
+            if (o0 && o1) {
+                *reinterpret_cast<float4*>(a.v + c) = vn;
+            } else {
+                float2* vp = reinterpret_cast<float2*>(a.v + c);
+                if (o0) vp[0] = vn0;
+                if (o1) vp[1] = vn1;
+            }
         }
-        rp = warp_sum_d(rp);
-        rdv = warp_sum_d(rdv);
-        u2 = warp_sum_d(u2);
-        v2 = warp_sum_d(v2);
-        s2 = warp_sum_d(s2);
+        double d[5] = {rp, rdv, u2, v2, s2};
+#pragma unroll
+        for (int q = 0; q < 5; ++q) d[q] = warp_sum_d(d[q]);
         if (lane == 0) {
-            misc->red[warp][0] = rp;
-            misc->red[warp][1] = rdv;
-            misc->red[warp][2] = u2;
-            misc->red[warp][3] = v2;
-            misc->red[warp][4] = s2;
+#pragma unroll
+            for (int q = 0; q < 5; ++q) misc->red[warp][q] = d[q];
         }
         csync();
         if (tid < 5) {
@@ -602,18 +763,27 @@ struct Consumer {
         int completed = 0;
         bool ok = true, stopped = false;
         for (int it = 0; it < a.iters; ++it) {
-            if (multi) pass_rows_up<true>(); else pass_rows_up<false>();
+            stamp(it, 0);
+            if (multi) pass_up_multi(); else pass_up_single();
+            stamp(it, 1);
             if (!(ok = grid_barrier(a, misc))) break;
+            stamp(it, 2);
             reduce_partials(it);
+            stamp(it, 3);
             if (!(ok = grid_barrier(a, misc))) break;
+            stamp(it, 4);
             if (a.check_stop && it > 0 && __ldcg(a.stop_flag) != 0) {
                 stopped = true;
                 completed = it;
                 break;
             }
             apply_factors();
+            stamp(it, 5);
             if (!(ok = grid_barrier(a, misc))) break;
-            if (multi) pass_rows_down_and_update<true>(); else pass_rows_down_and_update<false>();
+            stamp(it, 6);
+            if (multi) pass_down<true>(); else pass_down<false>();
+            update_state();
+            stamp(it, 7);
             completed = it + 1;
         }
         if (ok && !stopped) {
@@ -673,6 +843,17 @@ void* pick(int chunks) {
 }
 
 }  // namespace
+
+int rows_per_stage(int chunks) {
+    switch (chunks) {
+        case 1: return RowsOf<1>::value;
+        case 2: return RowsOf<2>::value;
+        case 4: return RowsOf<4>::value;
+        case 8: return RowsOf<8>::value;
+        case 16: return RowsOf<16>::value;
+        default: return 0;
+    }
+}
 
 cudaError_t prepare_iterate(int chunks, int smem) {
     void* fn = pick(chunks);

@@ -103,6 +103,9 @@ class Solver:
     def set_option(self, option: int, value: int) -> None:
         B.admm_set_option(self.h, int(option), int(value))
 
+    def trace(self, cap: int):
+        return B.admm_get_trace(self.h, int(cap), self.stream)
+
     def status(self) -> int:
         return B.admm_status(self.h, self.stream)
 

@@ -57,21 +57,41 @@ def test_partition_rejects_bad_arguments(cuda_lib):
 
 PLAN_CASES = [(256, 4096, 4, 1), (1440, 32768, 8, 1), (1440, 32768, 1, 8), (1440, 32768, 4, 4),
               (100, 1000, 3, 3), (37, 517, 3, 5), (300, 3001, 7, 2), (12, 32, 1, 2),
-              (2048, 16384, 8, 1), (8192, 131072, 16, 1), (16, 64, 4, 4)]
+              (2048, 16384, 8, 1), (8192, 131072, 16, 1), (16, 64, 4, 4), (96, 2048, 2, 16),
+              (300, 3003, 3, 4), (200, 6001, 5, 4), (64, 20000, 1, 200)]
 
 
 @pytest.mark.parametrize("m,n,M,N", PLAN_CASES)
 def test_plan_slabs_cover_columns_and_fit_limits(cuda_lib, m, n, M, N):
     import paper_1811_05571_gb300 as P
-    plan, cols = P.admm_plan(m, n, M, N, num_sms=152, smem_limit=232448)
+    plan, slabs = P.admm_plan(m, n, M, N, num_sms=152, smem_limit=232448)
     ld = plan["ld"]
     assert ld >= n and ld % 32 == 0
-    assert cols[0] == 0 and cols[-1] == ld and len(cols) == plan["ctas"] + 1
-    widths = np.diff(cols)
-    assert np.all(widths > 0) and np.all(widths % 2 == 0)       # 16-byte pairs, TMA x aligned
-    assert widths.max() - widths.min() <= 2                      # balanced
-    assert widths.max() == plan["slab_cols"]
-    assert plan["ctas"] <= 152
+    assert len(slabs) == plan["ctas"] <= 152
+    beg = np.array([s[0] for s in slabs]); end = np.array([s[1] for s in slabs])
+    own0 = np.array([s[2] for s in slabs]); own1 = np.array([s[3] for s in slabs])
+    assert np.all(beg % 2 == 0) and np.all(end % 2 == 0) and np.all(end > beg)   # TMA x aligned
+    assert beg[0] == 0 and end[-1] == ld
+    # consecutive slabs abut or share the one pair holding an odd block boundary
+    assert np.all((beg[1:] == end[:-1]) | (beg[1:] == end[:-1] - 2))
+    assert (end - beg).max() == plan["slab_cols"]
+    # every column (padding included) is owned by exactly one CTA, inside its slab
+    assert np.all(own0 >= beg) and np.all(own1 <= end) and np.all(own1 > own0)
+    assert own0[0] == 0 and own1[-1] == ld and np.all(own0[1:] == own1[:-1])
+    assert np.all(own0 - beg <= 1) and np.all(end - own1 <= 1)
+    col_off = [a for a, _ in A.balanced_blocks(n, N)] + [n]
+    if N <= plan["ctas"]:
+        assert plan["max_blocks_per_slab"] == 1
+        # owned columns of a CTA never cross a column-block boundary
+        for o0, o1 in zip(own0, own1):
+            j = np.searchsorted(col_off, o0, side="right") - 1
+            hi = col_off[j + 1] if j + 1 < N else ld
+            assert o1 <= hi
+        # slab widths are balanced within a column block
+        for j in range(N):
+            lo, hi = col_off[j], (col_off[j + 1] if j + 1 < N else ld)
+            w = [e - b for b, e, o0, o1 in slabs if o0 >= lo and o1 <= hi]
+            assert w and max(w) - min(w) <= 2
     assert plan["box_cols"] % 2 == 0 and plan["box_cols"] <= 256
     assert plan["box_cols"] * plan["boxes_per_row"] >= plan["slab_cols"]
     assert plan["slab_cols"] // 2 <= 32 * plan["chunks"]
@@ -79,14 +99,6 @@ def test_plan_slabs_cover_columns_and_fit_limits(cuda_lib, m, n, M, N):
     assert 2 <= plan["stages"] <= 8
     assert plan["smem_bytes"] <= 232448
     assert 1 <= plan["max_blocks_per_slab"] <= 4
-    # every slab touches the blocks its columns fall in
-    col_off = [a for a, _ in A.balanced_blocks(n, N)] + [n]
-    touched = []
-    for c0, c1 in zip(cols[:-1], cols[1:]):
-        lo = np.searchsorted(col_off, c0, side="right") - 1
-        hi = min(np.searchsorted(col_off, c1 - 1, side="right") - 1, N - 1)
-        touched.append(hi - min(lo, N - 1) + 1)
-    assert max(touched) == plan["max_blocks_per_slab"]
 
 
 def test_plan_rejects_too_narrow_column_blocks(cuda_lib):

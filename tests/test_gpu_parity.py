@@ -74,9 +74,11 @@ def compare_all(s, ref, M, N):
     assert ru <= TOL, f"u relative error {ru:.3e}"
     k, vv, ss, gh = s.state()
     assert k == ref.iters
+    # the scaled duals accumulate u - v differences, so their FP32 error scales
+    # with ||u||, not with ||s|| (which can be much smaller, e.g. lambda = 0)
     ss = ss.numpy().astype(np.complex128)
-    rs = np.linalg.norm(ss - ref.s) / max(np.linalg.norm(ref.s), 1e-30)
-    assert rs <= 10 * TOL, f"s relative error {rs:.3e}"
+    rs = np.linalg.norm(ss - ref.s) / max(np.linalg.norm(ref.s), np.linalg.norm(ref.u), 1e-30)
+    assert rs <= 10 * TOL, f"s error {rs:.3e} (relative to max(||s||, ||u||))"
     if N > 1:
         gh = gh.numpy().astype(np.complex128)
         rg = np.linalg.norm(gh - ref.ghat) / max(np.linalg.norm(ref.ghat), 1e-30)
@@ -281,3 +283,32 @@ def test_barrier_timeout_is_reported_and_reset_recovers():
     assert s.status() == 0
     ref = oracle_run(p, 2, 1, 30)
     compare_all(s, ref, 2, 1)
+
+
+def test_phase_trace_is_monotonic_and_covers_every_iteration():
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(128, 4096, 8, seed=16)
+    s = gpu_run(p, 4, 1, 0)
+    s.set_option(P.ADMM_OPT_TRACE_ITERS, 5)
+    s.iterate(5)
+    tr = s.trace(5)
+    assert tr.shape == (2, 5, 8)
+    for cta in range(2):
+        flat = tr[cta].reshape(-1)
+        assert np.all(flat > 0) and np.all(np.diff(flat) >= 0)
+    s.set_option(P.ADMM_OPT_TRACE_ITERS, 0)
+    s.iterate(2)
+    assert s.status() == 0
+
+
+def test_several_handles_with_different_plans_coexist():
+    """Handles whose plans need different shared memory launch the same kernel
+    instance in any order."""
+    p = synth.gaussian_problem(256, 8192, 8, seed=17)
+    rho = _rho_cols(p, 4)
+    a = gpu_run(p, 8, 1, 0, rho=rho)
+    b = gpu_run(p, 1, 4, 0, rho=rho)
+    c = gpu_run(p, 4, 4, 0, rho=rho)
+    for s in (a, b, c, a, c, b):
+        s.iterate(3)
+        assert s.status() == 0
