@@ -16,6 +16,6 @@ from ._binding import (  # noqa: F401
     admm_abi_version, admm_strerror, admm_partition, admm_plan, admm_setup, admm_iterate,
     admm_solve, admm_get_v, admm_get_u, admm_get_residuals, admm_set_g, admm_set_lambda,
     admm_set_rho, admm_reset, admm_get_state, admm_set_state, admm_get_info, admm_set_option,
-    admm_get_trace, admm_status, admm_destroy,
+    admm_get_trace, admm_status, admm_destroy, admm_solve_small_noalloc,
 )
 from .solver import Solver  # noqa: F401

@@ -82,6 +82,8 @@ SIGNATURES = {
                                  ctypes.POINTER(c_int32), c_void_p]),
     "admm_status": (c_int32, [c_void_p, c_void_p]),
     "admm_destroy": (None, [c_void_p]),
+    "admm_solve_small_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32,
+                                           c_double, c_double, c_int32, c_void_p, c_void_p]),
 }
 
 _LIB = None
@@ -266,3 +268,10 @@ def admm_status(h: int, stream=None) -> int:
 def admm_destroy(h: int) -> None:
     if h:
         load().admm_destroy(h)
+
+
+def admm_solve_small_noalloc(H, g, m: int, n: int, row_blocks: int, col_blocks: int, lam: float,
+                             rho: float, iters: int, v_out, stream=None) -> None:
+    """Allocation-free solve of a small problem into the caller's v_out (see include/admm.h)."""
+    _check(load().admm_solve_small_noalloc(_ptr(H), _ptr(g), m, n, row_blocks, col_blocks, lam, rho,
+                                           iters, _ptr(v_out), _stream(stream)))

@@ -110,6 +110,8 @@ void free_all(admm_t* h) {
 
 namespace admm {
 
+void set_handle_free_error(const char* msg) { g_setup_error = msg ? msg : ""; }
+
 void balanced_offsets(int64_t total, int parts, std::vector<int>& off) {
     off.assign(parts + 1, 0);
     const int64_t base = total / parts, extra = total % parts;

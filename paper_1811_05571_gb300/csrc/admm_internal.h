@@ -62,6 +62,9 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
 
 void balanced_offsets(int64_t total, int parts, std::vector<int>& off);
 
+// Message returned by admm_last_error(NULL) (calls that have no handle).
+void set_handle_free_error(const char* msg);
+
 // Arguments of the persistent iteration kernel (passed by value).
 struct IterArgs {
     int m, n, ld, M, N, P;
