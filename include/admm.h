@@ -72,6 +72,11 @@ extern "C" {
                                      call ends with ADMM_ETIMEOUT (0 = off, the default) */
 #define ADMM_OPT_TRACE_ITERS   4  /* record %globaltimer phase stamps of the first `value`
                                      iterations of each launch (0 = off, the default) */
+#define ADMM_OPT_L2_KEEP_BYTES 5  /* bytes of H at the end of each pass over H that are loaded
+                                     with the L2 evict_last policy, so the next pass (which
+                                     walks the rows in the opposite order) finds them in L2;
+                                     the rest is loaded evict_first (default 80 MiB; 0 = no
+                                     L2 policy hints) */
 
 typedef struct admm_problem admm_t;
 
@@ -238,8 +243,8 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value);
  * and the last CTA, and for each of the first min(cap, trace length)
  * iterations, 8 %globaltimer stamps in nanoseconds: iteration start, first
  * pass over H done, first grid barrier passed, partial sums reduced, second
- * barrier passed, factors applied, third barrier passed, second pass and
- * state update done.  `out` holds 2 * cap * 8 int64 (CTA 0 first); *count
+ * barrier passed, factors applied, third barrier passed, second pass over H
+ * and state update done.  `out` holds 2 * cap * 8 int64 (CTA 0 first); *count
  * receives the iterations written per CTA.  Synchronises `stream`. */
 int admm_get_trace(admm_t* h, int64_t* out, int32_t cap, int32_t* count, void* stream);
 

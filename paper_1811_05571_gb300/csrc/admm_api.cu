@@ -34,7 +34,7 @@ struct admm_problem {
     Plan plan;
     // device memory owned by the handle
     float2 *H = nullptr, *g = nullptr, *v = nullptr, *s = nullptr, *u = nullptr;
-    float2 *ghat = nullptr, *gt = nullptr, *r = nullptr, *w = nullptr, *part = nullptr;
+    float2 *ghat = nullptr, *gt = nullptr, *r = nullptr, *w = nullptr, *part = nullptr;  // ghat: 2 x N x m
     float2* kinv = nullptr;
     long long* kinv_off_d = nullptr;
     int* ints_d = nullptr;  // all int tables in one allocation
@@ -58,6 +58,8 @@ struct admm_problem {
     long long* trace = nullptr;  // phase timestamps, 2 x trace_iters x 8
     int trace_iters = 0;
     int64_t k = 0;       // iterations completed (host mirror)
+    int pending = 0;     // the last launch's final residual record has not been summed yet
+    int64_t l2_keep_bytes = 80LL << 20;  // H bytes per pass marked L2 evict_last
     int broken = 0;      // sticky error that blocks further iterations
     double gram_ms = 0.0, factor_ms = 0.0;
     std::string err;
@@ -251,13 +253,13 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     pl.ws_rows = pl.ws_all ? static_cast<int>(m) : pl.mimax;
     // shared memory: fixed regions, then the deepest ring that fits
     const int ws = pl.njs * pl.ws_rows * 8;
-    const int rs = pl.kpmax * 8;
+    const int rs = pl.kpmax * 8;   // r_b, and the same again for gt_b
     pl.red_single = 2 * kConsumerWarps * npitch * 16 > 64 * 1024;
     pl.sigma_global = static_cast<int64_t>(M) * npitch * 16 > 32 * 1024;
     const int red = (pl.red_single ? 1 : 2) * kConsumerWarps * npitch * 16;
     const int sigma = pl.sigma_global ? 0 : M * npitch * 16;
     const int misc = 1024;
-    const int fixed = round_up(ws, 128) + round_up(rs, 128) + round_up(red, 128) +
+    const int fixed = round_up(ws, 128) + 2 * round_up(rs, 128) + round_up(red, 128) +
                       round_up(sigma, 128) + misc + 256 + 1024;
     pl.R = rows_per_stage(pl.chunks);
     pl.sub_bytes = pl.R * pl.wbox * 8;
@@ -280,6 +282,8 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     pl.off_ws = off;
     off += round_up(ws, 128);
     pl.off_rs = off;
+    off += round_up(rs, 128);
+    pl.off_gs = off;
     off += round_up(rs, 128);
     pl.off_red = off;
     off += round_up(red, 128);
@@ -429,7 +433,7 @@ int zero_state(admm_t* h, cudaStream_t st) {
     CK(h, cudaMemsetAsync(h->v, 0, ld * sizeof(float2), st));
     CK(h, cudaMemsetAsync(h->s, 0, ld * h->M * sizeof(float2), st));
     CK(h, cudaMemsetAsync(h->u, 0, ld * h->M * sizeof(float2), st));
-    CK(h, cudaMemsetAsync(h->ghat, 0, static_cast<size_t>(h->N) * h->m * sizeof(float2), st));
+    CK(h, cudaMemsetAsync(h->ghat, 0, 2 * static_cast<size_t>(h->N) * h->m * sizeof(float2), st));
     CK(h, cudaMemsetAsync(h->bar, 0, 2 * sizeof(unsigned), st));
     CK(h, cudaMemsetAsync(h->status, 0, sizeof(int), st));
     CK(h, cudaMemsetAsync(h->stop_flag, 0, sizeof(int), st));
@@ -437,7 +441,15 @@ int zero_state(admm_t* h, cudaStream_t st) {
     CK(h, cudaMemsetAsync(h->hist, 0, static_cast<size_t>(h->hist_cap) * 5 * sizeof(double), st));
     h->k = 0;
     h->broken = 0;
+    h->pending = 0;
     return ADMM_OK;
+}
+
+// stages per pass whose H rows stay in L2 for the reversed next pass
+int keep_stages(const admm_t* h) {
+    const Plan& pl = h->plan;
+    const int64_t per_stage = static_cast<int64_t>(pl.R) * pl.ld * static_cast<int64_t>(sizeof(float2));
+    return static_cast<int>(std::max<int64_t>(0, h->l2_keep_bytes / std::max<int64_t>(per_stage, 1)));
 }
 
 int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_rel,
@@ -465,6 +477,7 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.off_empty = pl.off_empty;
     a.off_ws = pl.off_ws;
     a.off_rs = pl.off_rs;
+    a.off_gs = pl.off_gs;
     a.off_red = pl.off_red;
     a.off_sigma = pl.off_sigma;
     a.off_misc = pl.off_misc;
@@ -516,14 +529,35 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.bar_extra = h->bar_extra;
     a.trace = h->trace;
     a.trace_iters = h->trace_iters;
+    a.keep_stages = keep_stages(h);
+    a.pending_prev = h->pending && h->k > 0 ? 1 : 0;
     cudaError_t e = admm::launch_iterate(h->tmap, a, pl.chunks, pl.smem, st);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the iteration kernel");
     h->k += iters;
+    h->pending = 1;   // this launch's last record is summed by the next launch or a sync call
     return ADMM_OK;
 }
 
 int device_status(admm_t* h, cudaStream_t st) {
     CK(h, cudaStreamSynchronize(st));
+    long long kd0 = 0;
+    CK(h, cudaMemcpy(&kd0, h->k_done, sizeof(long long), cudaMemcpyDeviceToHost));
+    if (h->pending && kd0 > 0) {
+        // sum the last launch's final residual record (its kernel ends without a grid barrier)
+        admm::IterArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.M = h->M;
+        a.n = static_cast<int>(h->n);
+        a.P = h->plan.P;
+        a.rho_d = h->rho;
+        a.res_part = h->res_part;
+        a.hist = h->hist;
+        a.hist_cap = h->hist_cap;
+        a.status = h->status;
+        CK(h, admm::launch_finalize(a, kd0 - 1, st));
+        CK(h, cudaStreamSynchronize(st));
+    }
+    h->pending = 0;
     int code = 0;
     long long kd = 0;
     CK(h, cudaMemcpy(&code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
@@ -677,7 +711,7 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     const size_t Nm = static_cast<size_t>(col_blocks) * m;
     bool ok = dalloc(&h->H, ld * m) == cudaSuccess && dalloc(&h->g, m) == cudaSuccess &&
               dalloc(&h->v, ld) == cudaSuccess && dalloc(&h->s, ld * row_blocks) == cudaSuccess &&
-              dalloc(&h->u, ld * row_blocks) == cudaSuccess && dalloc(&h->ghat, Nm) == cudaSuccess &&
+              dalloc(&h->u, ld * row_blocks) == cudaSuccess && dalloc(&h->ghat, 2 * Nm) == cudaSuccess &&
               dalloc(&h->gt, Nm) == cudaSuccess && dalloc(&h->r, Nm) == cudaSuccess &&
               dalloc(&h->w, Nm) == cudaSuccess && dalloc(&h->part, Nm * pl.P) == cudaSuccess &&
               dalloc(&h->kinv, kel) == cudaSuccess &&
@@ -711,7 +745,7 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     h->j_cta_hi_d = h->ints_d + o_jh;
     h->solve_lo_d = h->ints_d + o_sl;
     h->kinv_pitch_d = h->ints_d + o_kp;
-    h->state_bytes = static_cast<int64_t>((ld * (1 + 2 * row_blocks) + 4 * Nm + Nm * pl.P) * sizeof(float2));
+    h->state_bytes = static_cast<int64_t>((ld * (1 + 2 * row_blocks) + 5 * Nm + Nm * pl.P) * sizeof(float2));
 
 #define SETUP_CK(call)                                             \
     do {                                                           \
@@ -783,6 +817,13 @@ int admm_solve(admm_t* h, int32_t max_iter, double eps_abs, double eps_rel, int3
     cudaStream_t st = as_stream(stream);
     int code = run_kernel(h, max_iter, 1, eps_abs, eps_rel, st);
     if (code) return code;
+    {
+        // a solve that stopped early already summed the record of its last iteration
+        CK(h, cudaStreamSynchronize(st));
+        long long kd = 0;
+        CK(h, cudaMemcpy(&kd, h->k_done, sizeof(long long), cudaMemcpyDeviceToHost));
+        if (kd - k0 < max_iter) h->pending = 0;
+    }
     code = device_status(h, st);
     if (iters_done) *iters_done = static_cast<int32_t>(h->k - k0);
     return code;
@@ -867,8 +908,8 @@ int admm_get_state(admm_t* h, int64_t* k, void* v, void* s, void* ghat, void* st
         CK(h, cudaMemcpy2DAsync(s, h->n * sizeof(float2), h->s, h->plan.ld * sizeof(float2),
                                 h->n * sizeof(float2), h->M, cudaMemcpyDefault, st));
     if (ghat)
-        CK(h, cudaMemcpyAsync(ghat, h->ghat, static_cast<size_t>(h->N) * h->m * sizeof(float2),
-                              cudaMemcpyDefault, st));
+        CK(h, cudaMemcpyAsync(ghat, h->ghat + static_cast<size_t>(h->k & 1) * h->N * h->m,
+                              static_cast<size_t>(h->N) * h->m * sizeof(float2), cudaMemcpyDefault, st));
     CK(h, cudaStreamSynchronize(st));
     return code;
 }
@@ -881,14 +922,16 @@ int admm_set_state(admm_t* h, int64_t k, const void* v, const void* s, const voi
     CK(h, cudaMemcpyAsync(h->v, v, h->n * sizeof(float2), cudaMemcpyDefault, st));
     CK(h, cudaMemcpy2DAsync(h->s, h->plan.ld * sizeof(float2), s, h->n * sizeof(float2),
                             h->n * sizeof(float2), h->M, cudaMemcpyDefault, st));
+    float2* cur = h->ghat + static_cast<size_t>(k & 1) * h->N * h->m;
     if (ghat)
-        CK(h, cudaMemcpyAsync(h->ghat, ghat, static_cast<size_t>(h->N) * h->m * sizeof(float2),
+        CK(h, cudaMemcpyAsync(cur, ghat, static_cast<size_t>(h->N) * h->m * sizeof(float2),
                               cudaMemcpyDefault, st));
     else
-        CK(h, cudaMemsetAsync(h->ghat, 0, static_cast<size_t>(h->N) * h->m * sizeof(float2), st));
+        CK(h, cudaMemsetAsync(cur, 0, static_cast<size_t>(h->N) * h->m * sizeof(float2), st));
     CK(h, cudaMemcpyAsync(h->k_done, &k, sizeof(long long), cudaMemcpyHostToDevice, st));
     CK(h, cudaStreamSynchronize(st));
     h->k = k;
+    h->pending = 0;   // the restored state has no residual record of its own
     return ADMM_OK;
 }
 
@@ -949,6 +992,10 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
             }
             return ADMM_OK;
         }
+        case ADMM_OPT_L2_KEEP_BYTES:
+            if (value < 0) return fail(h, ADMM_EINVAL, "L2 keep bytes must be >= 0");
+            h->l2_keep_bytes = value;
+            return ADMM_OK;
         case ADMM_OPT_BARRIER_EXTRA:
             if (value < 0 || value > 1024) return fail(h, ADMM_EINVAL, "barrier extra out of range");
             h->bar_extra = static_cast<int>(value);

@@ -36,7 +36,7 @@ struct Plan {
     int mimax = 0;        // tallest row block
     int kpmax = 0;        // padded pitch of the tallest factor
     // shared-memory layout (byte offsets into dynamic smem)
-    int off_ring = 0, off_full = 0, off_empty = 0, off_ws = 0, off_rs = 0, off_red = 0,
+    int off_ring = 0, off_full = 0, off_empty = 0, off_ws = 0, off_rs = 0, off_gs = 0, off_red = 0,
         off_sigma = 0, off_misc = 0, smem = 0;
     bool aligned = false; // slabs aligned to column blocks (one block per slab)
     int red_lanes = 32;   // lanes summing the partials of one (block, row) in phase B
@@ -70,7 +70,7 @@ struct IterArgs {
     int m, n, ld, M, N, P;
     int R, nstages, stage_bytes, stage_stride, sub_bytes, nsub, wbox;
     int mimax, kpmax;
-    int off_ring, off_full, off_empty, off_ws, off_rs, off_red, off_sigma, off_misc;
+    int off_ring, off_full, off_empty, off_ws, off_rs, off_gs, off_red, off_sigma, off_misc;
     int red_lanes, ws_all, ws_rows, sigma_global, red_single;
     float rho, kappa, inv_M;
     double rho_d;
@@ -89,9 +89,9 @@ struct IterArgs {
     float2* s;
     float2* u;
     const float2* g;
-    float2* ghat;
-    float2* gt;
-    float2* r;
+    float2* ghat;         // two N x m buffers; iteration k reads buffer k & 1, writes the other
+    float2* gt;           // N x m estimated-data-corrected g of the current iteration
+    float2* r;            // N x m residuals r_b
     float2* w;
     float2* part;
     const float2* kinv;
@@ -112,7 +112,12 @@ struct IterArgs {
     int bar_extra;
     long long* trace;     // optional phase timestamps (2 CTAs x trace_iters x 8)
     int trace_iters;
+    int keep_stages;      // last stages of each pass loaded L2 evict_last (0 = no L2 hints)
+    int pending_prev;     // the previous launch's last residual record is still to be summed
 };
+
+// Sum the per-CTA residual partials of iteration kabs into the history ring.
+cudaError_t launch_finalize(const IterArgs& a, long long kabs, cudaStream_t stream);
 
 // Rows of H per pipeline stage of the kernel instance with `chunks` chunks.
 int rows_per_stage(int chunks);

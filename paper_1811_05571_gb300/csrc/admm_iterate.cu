@@ -154,15 +154,22 @@ __device__ bool producer_wait(uint64_t* bar, uint32_t parity, const IterArgs& a,
 __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* full,
                          uint64_t* empty, Misc* misc, unsigned char* ring, int c_beg) {
     prefetch_tensormap(tmap);
+    // The last keep_stages stages of every pass are marked evict_last: the next
+    // pass walks the rows in the opposite order and finds them in L2.  All
+    // other stages are streamed evict_first so they do not displace them.
+    const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
+    int per_pass = 0;
+    for (int i = 0; i < a.M; ++i) per_pass += (a.row_off[i + 1] - a.row_off[i] + a.R - 1) / a.R;
     int stage = 0;
     bool ok = true;
     for (int it = 0; it < a.iters && ok; ++it) {
         for (int pass = 0; pass < 2 && ok; ++pass) {
+            int pos = 0;
             for (int bi = 0; bi < a.M && ok; ++bi) {
                 const int i = pass == 0 ? bi : a.M - 1 - bi;
                 const int r0 = a.row_off[i], r1 = a.row_off[i + 1];
                 const int nb = (r1 - r0 + a.R - 1) / a.R;
-                for (int bb = 0; bb < nb; ++bb) {
+                for (int bb = 0; bb < nb; ++bb, ++pos) {
                     const int b = pass == 0 ? bb : nb - 1 - bb;
                     const int y = r0 + b * a.R;
                     const int slot = stage % a.nstages;
@@ -173,9 +180,15 @@ __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* f
                     }
                     mbar_arrive_expect_tx(&full[slot], static_cast<uint32_t>(a.stage_bytes));
                     unsigned char* dst = ring + static_cast<size_t>(slot) * a.stage_stride;
-                    for (int sb = 0; sb < a.nsub; ++sb)
-                        tma_load_2d(dst + static_cast<size_t>(sb) * a.sub_bytes, tmap,
-                                    c_beg + sb * a.wbox, y, &full[slot]);
+                    const uint64_t pol = pos >= per_pass - a.keep_stages ? pol_last : pol_first;
+                    for (int sb = 0; sb < a.nsub; ++sb) {
+                        if (a.keep_stages > 0)
+                            tma_load_2d_hint(dst + static_cast<size_t>(sb) * a.sub_bytes, tmap,
+                                             c_beg + sb * a.wbox, y, &full[slot], pol);
+                        else
+                            tma_load_2d(dst + static_cast<size_t>(sb) * a.sub_bytes, tmap,
+                                        c_beg + sb * a.wbox, y, &full[slot]);
+                    }
                     ++stage;
                     *reinterpret_cast<volatile int*>(&misc->issued) = stage;
                 }
@@ -184,6 +197,39 @@ __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* f
     }
     __threadfence_block();
     *reinterpret_cast<volatile int*>(&misc->producer_done) = 1;
+}
+
+// Record of iteration kabs (absolute index): FP64 sums of the per-CTA residual
+// partials, written to the history ring; optional stopping test.  One warp.
+__device__ void finalize_record(const IterArgs& a, long long kabs, int lane, bool check) {
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int c = lane; c < a.P; c += 32) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) acc[q] += __ldcg(a.res_part + static_cast<size_t>(c) * 8 + q);
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) acc[q] = warp_sum_d(acc[q]);
+    if (lane == 0) {
+        const double Md = static_cast<double>(a.M);
+        double rec[5];
+        rec[0] = acc[0];
+        rec[1] = a.rho_d * a.rho_d * Md * acc[1];
+        rec[2] = acc[2];
+        rec[3] = Md * acc[3];
+        rec[4] = acc[4];
+        double* dst = a.hist + static_cast<size_t>(kabs % a.hist_cap) * 5;
+#pragma unroll
+        for (int q = 0; q < 5; ++q) dst[q] = rec[q];
+        const bool bad = !isfinite(rec[0] + rec[1] + rec[2] + rec[3] + rec[4]);
+        if (bad) raise_status(a.status, ADMM_EDIVERGED);
+        if (check) {
+            const double p = static_cast<double>(a.M) * static_cast<double>(a.n);
+            const double eps_pri = sqrt(p) * a.eps_abs + a.eps_rel * fmax(sqrt(rec[2]), sqrt(rec[3]));
+            const double eps_dual = sqrt(p) * a.eps_abs + a.eps_rel * a.rho_d * sqrt(rec[4]);
+            const int stop = (!bad && sqrt(rec[0]) <= eps_pri && sqrt(rec[1]) <= eps_dual) ? 1 : 0;
+            __stcg(a.stop_flag, stop);
+        }
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -247,9 +293,11 @@ struct Consumer {
                 uint64_t bits = 0;
                 for (int h = 0; h < 2; ++h) {
                     if (c0 + h >= own0 && c0 + h < own1) owned |= 1u << (2 * k + h);
-                    int j = jlo;
-                    while (j + 1 < a.N && a.col_off[j + 1] <= c0 + h) ++j;
-                    bits |= static_cast<uint64_t>(min(max(j - jlo, 0), 3)) << (2 * h);
+                    if (nj > 1) {
+                        int j = jlo;
+                        while (j + 1 < a.N && a.col_off[j + 1] <= c0 + h) ++j;
+                        bits |= static_cast<uint64_t>(min(max(j - jlo, 0), 3)) << (2 * h);
+                    }
                 }
                 jl |= bits << (4 * k);
             }
@@ -424,43 +472,16 @@ struct Consumer {
         }
     }
 
-    // ---- record of iteration k: FP64 sums over the CTAs, stopping test ------
-    __device__ void finalize(int k) {
-        double acc[5] = {0, 0, 0, 0, 0};
-        for (int c = lane; c < a.P; c += 32) {
-#pragma unroll
-            for (int q = 0; q < 5; ++q) acc[q] += __ldcg(a.res_part + static_cast<size_t>(c) * 8 + q);
-        }
-#pragma unroll
-        for (int q = 0; q < 5; ++q) acc[q] = warp_sum_d(acc[q]);
-        if (lane == 0) {
-            const double Md = static_cast<double>(a.M);
-            double rec[5];
-            rec[0] = acc[0];
-            rec[1] = a.rho_d * a.rho_d * Md * acc[1];
-            rec[2] = acc[2];
-            rec[3] = Md * acc[3];
-            rec[4] = acc[4];
-            double* dst = a.hist + static_cast<size_t>((a.k0 + k) % a.hist_cap) * 5;
-#pragma unroll
-            for (int q = 0; q < 5; ++q) dst[q] = rec[q];
-            const bool bad = !isfinite(rec[0] + rec[1] + rec[2] + rec[3] + rec[4]);
-            if (bad) raise_status(a.status, ADMM_EDIVERGED);
-            if (a.check_stop) {
-                const double p = static_cast<double>(a.M) * static_cast<double>(a.n);
-                const double eps_pri =
-                    sqrt(p) * a.eps_abs + a.eps_rel * fmax(sqrt(rec[2]), sqrt(rec[3]));
-                const double eps_dual = sqrt(p) * a.eps_abs + a.eps_rel * a.rho_d * sqrt(rec[4]);
-                const int stop = (!bad && sqrt(rec[0]) <= eps_pri && sqrt(rec[1]) <= eps_dual) ? 1 : 0;
-                __stcg(a.stop_flag, stop);
-            }
-        }
-    }
-
     // ---- phase B: r = gt - sum of partials; gt = g_i - sum_{q != j} ghat ----
     // Groups of red_lanes lanes sum the partials of one (column block, row).
+    // The last CTA also sums the residual record of the previous iteration.
     __device__ void reduce_partials(int it) {
-        if (it > 0 && cta == 0 && warp == 0) finalize(it - 1);
+        if (cta == a.P - 1 && warp == 0) {
+            if (it > 0) finalize_record(a, a.k0 + it - 1, lane, a.check_stop != 0);
+            else if (a.pending_prev) finalize_record(a, a.k0 - 1, lane, false);
+        }
+        const size_t Nm = static_cast<size_t>(a.N) * a.m;
+        const float2* ghat_cur = a.ghat + ((a.k0 + it) & 1) * Nm;
         const int L = a.red_lanes;
         const int groups = 32 / L;
         const int g = lane / L, gl = lane - (lane / L) * L;
@@ -468,21 +489,27 @@ struct Consumer {
         const int stride = a.P * kConsumerWarps * groups;
         for (int base = (cta * kConsumerWarps + warp) * groups; base < total; base += stride) {
             const int idx = base + g;
-            float2 acc = make_float2(0.f, 0.f);
+            float2 acc = make_float2(0.f, 0.f), acc2 = acc;
             int j = 0, row = 0;
             if (idx < total) {
                 j = idx / a.m;
                 row = idx - j * a.m;
                 const int lo = a.j_cta_lo[j], hi = a.j_cta_hi[j];
                 const float2* pp = a.part + static_cast<size_t>(idx) * a.P;
-                for (int c = lo + gl; c <= hi; c += L) acc = acc + ldcg2(pp + c);
+                int c = lo + gl;
+                for (; c + L <= hi; c += 2 * L) {
+                    acc = acc + ldcg2(pp + c);
+                    acc2 = acc2 + ldcg2(pp + c + L);
+                }
+                if (c <= hi) acc = acc + ldcg2(pp + c);
             }
+            acc = acc + acc2;
             for (int o = L >> 1; o >= 1; o >>= 1) acc = acc + shfl2(acc, o);
             if (idx < total && gl == 0) {
                 float2 gtl = __ldg(a.g + row);
                 for (int q = 0; q < a.N; ++q) {
                     if (q == j) continue;
-                    const float2 gh = ldcg2(a.ghat + static_cast<size_t>(q) * a.m + row);
+                    const float2 gh = ldcg2(ghat_cur + static_cast<size_t>(q) * a.m + row);
                     gtl.x -= gh.x;
                     gtl.y -= gh.y;
                 }
@@ -492,10 +519,14 @@ struct Consumer {
         }
     }
 
-    // ---- phase C: w_b = K_b^{-1} r_b, ghat_b = gt_b - rho w_b ----------------
-    // Two factor rows per warp, sixteen 16-byte loads in flight per lane.
-    __device__ void apply_factors() {
+    // ---- phase C: w_b = K_b^{-1} r_b, ghat_b = gt_b - rho w_b into the next
+    // estimated-data buffer.  Two factor rows per warp, sixteen 16-byte loads
+    // in flight per lane, factors streamed L2 evict_first.
+    __device__ void apply_factors(int it) {
         float2* rS = reinterpret_cast<float2*>(smem + a.off_rs);
+        const size_t Nm = static_cast<size_t>(a.N) * a.m;
+        float2* ghat_nxt = a.ghat + ((a.k0 + it + 1) & 1) * Nm;
+        const uint64_t pol = policy_evict_first();
         int idx = a.solve_lo[cta];
         const int end = a.solve_lo[cta + 1];
         while (idx < end) {
@@ -510,8 +541,7 @@ struct Consumer {
             const float2* K = a.kinv + a.kinv_off[b];
             csync();
             for (int k = tid; k < kp; k += kConsumerThreads)
-                rS[k] = k < mi ? ldcg2(a.r + static_cast<size_t>(j) * a.m + r0 + k)
-                               : make_float2(0.f, 0.f);
+                rS[k] = k < mi ? ldcg2(a.r + static_cast<size_t>(j) * a.m + r0 + k) : make_float2(0.f, 0.f);
             csync();
             const float4* r4 = reinterpret_cast<const float4*>(rS);
             const int kp2 = kp >> 1;
@@ -528,8 +558,8 @@ struct Consumer {
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int t = t0 + lane + 32 * u;
-                        ka[u] = t < kp2 ? __ldg(Ka + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-                        kb[u] = (has_b && t < kp2) ? __ldg(Kb + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        ka[u] = t < kp2 ? ldg_hint(Ka + t, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
+                        kb[u] = (has_b && t < kp2) ? ldg_hint(Kb + t, pol) : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -548,11 +578,11 @@ struct Consumer {
                 if (lane == 0) {
                     stcg2(a.w + q, aa);
                     const float2 ga = ldcg2(a.gt + q);
-                    stcg2(a.ghat + q, make_float2(ga.x - a.rho * aa.x, ga.y - a.rho * aa.y));
+                    stcg2(ghat_nxt + q, make_float2(ga.x - a.rho * aa.x, ga.y - a.rho * aa.y));
                     if (has_b) {
                         stcg2(a.w + qb, ab);
                         const float2 gb = ldcg2(a.gt + qb);
-                        stcg2(a.ghat + qb, make_float2(gb.x - a.rho * ab.x, gb.y - a.rho * ab.y));
+                        stcg2(ghat_nxt + qb, make_float2(gb.x - a.rho * ab.x, gb.y - a.rho * ab.y));
                     }
                 }
             }
@@ -761,34 +791,27 @@ struct Consumer {
     __device__ void run() {
         const bool multi = nj > 1;
         int completed = 0;
-        bool ok = true, stopped = false;
         for (int it = 0; it < a.iters; ++it) {
             stamp(it, 0);
             if (multi) pass_up_multi(); else pass_up_single();
             stamp(it, 1);
-            if (!(ok = grid_barrier(a, misc))) break;
+            if (!grid_barrier(a, misc)) break;
             stamp(it, 2);
             reduce_partials(it);
             stamp(it, 3);
-            if (!(ok = grid_barrier(a, misc))) break;
+            if (!grid_barrier(a, misc)) break;
             stamp(it, 4);
-            if (a.check_stop && it > 0 && __ldcg(a.stop_flag) != 0) {
-                stopped = true;
-                completed = it;
-                break;
-            }
-            apply_factors();
+            apply_factors(it);
             stamp(it, 5);
-            if (!(ok = grid_barrier(a, misc))) break;
+            if (!grid_barrier(a, misc)) break;
             stamp(it, 6);
+            // the record of iteration it-1 was tested in phase B; stopping here
+            // leaves v, s and the current estimated data of iteration it-1
+            if (a.check_stop && it > 0 && __ldcg(a.stop_flag) != 0) break;
             if (multi) pass_down<true>(); else pass_down<false>();
             update_state();
             stamp(it, 7);
             completed = it + 1;
-        }
-        if (ok && !stopped) {
-            ok = grid_barrier(a, misc);
-            if (ok && cta == 0 && warp == 0) finalize(a.iters - 1);
         }
         if (cta == 0 && tid == 0) a.k_done[0] = a.k0 + completed;
         drain();
@@ -824,6 +847,10 @@ __global__ void __launch_bounds__(kIterThreads, 1)
     }
     Consumer<CH> c(a, smem, misc, full, empty, ring);
     c.run();
+}
+
+__global__ void __launch_bounds__(32) finalize_kernel(const __grid_constant__ IterArgs a, long long kabs) {
+    finalize_record(a, kabs, threadIdx.x & 31, false);
 }
 
 template <int CH>
@@ -869,6 +896,11 @@ int max_coresident_iterate(int chunks, int smem, int* per_sm) {
         return 0;
     if (per_sm) *per_sm = blocks;
     return blocks;
+}
+
+cudaError_t launch_finalize(const IterArgs& a, long long kabs, cudaStream_t stream) {
+    finalize_kernel<<<1, 32, 0, stream>>>(a, kabs);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_iterate(const CUtensorMap& tmap, const IterArgs& a, int chunks, int smem,

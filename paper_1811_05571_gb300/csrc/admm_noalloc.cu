@@ -132,7 +132,7 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
     const size_t x_v = cv.take(ld * sizeof(float2));
     const size_t x_s = cv.take(ld * M * sizeof(float2));
     const size_t x_u = cv.take(ld * M * sizeof(float2));
-    const size_t x_ghat = cv.take(Nm * sizeof(float2));
+    const size_t x_ghat = cv.take(2 * Nm * sizeof(float2));
     const size_t x_gt = cv.take(Nm * sizeof(float2));
     const size_t x_r = cv.take(Nm * sizeof(float2));
     const size_t x_w = cv.take(Nm * sizeof(float2));
@@ -234,6 +234,7 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
         a.off_empty = pl.off_empty;
         a.off_ws = pl.off_ws;
         a.off_rs = pl.off_rs;
+        a.off_gs = pl.off_gs;
         a.off_red = pl.off_red;
         a.off_sigma = pl.off_sigma;
         a.off_misc = pl.off_misc;
@@ -279,6 +280,8 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
         a.hist_cap = 1;
         a.iters = iters;
         a.timeout_ns = 5000000000LL;
+        a.keep_stages = static_cast<int>((80LL << 20) / (static_cast<long long>(pl.R) * pl.ld * 8));
+        a.pending_prev = 0;
         NA_CK(admm::launch_iterate(tmap, a, pl.chunks, pl.smem, st));
     }
     NA_CK(cudaMemcpyAsync(v_out, v, static_cast<size_t>(n) * sizeof(float2), cudaMemcpyDeviceToDevice, st));
