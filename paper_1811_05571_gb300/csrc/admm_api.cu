@@ -232,8 +232,18 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
         }
         most = std::max(most, pl.j_cta_hi[j] - pl.j_cta_lo[j] + 1);
     }
-    pl.red_lanes = 1;
-    while (pl.red_lanes < 32 && pl.red_lanes * 4 < most) pl.red_lanes *= 2;
+    // phase B lane groups: the widest group that still covers every (block, row)
+    // in one round over all warps, but no narrower than 16 partials per lane
+    {
+        const int64_t items = static_cast<int64_t>(N) * m;
+        const int64_t warps = static_cast<int64_t>(pl.P) * kConsumerWarps;
+        int need_groups = 1;
+        while (need_groups < 32 && static_cast<int64_t>(need_groups) * warps < items) need_groups *= 2;
+        const int l_round = 32 / need_groups;
+        int l_regs = 1;
+        while (l_regs < 32 && l_regs * 16 < most) l_regs *= 2;
+        pl.red_lanes = std::max(l_regs, l_round);
+    }
     pl.npmax = pl.wmax / 2;
     const int need = (pl.npmax + 31) / 32;
     int ch = 1;

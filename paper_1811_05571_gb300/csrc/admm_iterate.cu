@@ -117,14 +117,17 @@ __device__ bool grid_barrier(const IterArgs& a, Misc* misc) {
             __threadfence();
             st_release_gpu(gen, g0 + 1u);
         } else {
+            // tight spin (the CTA's other warps wait in bar.sync); the clock
+            // and the status word are checked every 64 polls
             const long long t0 = global_timer_ns();
-            while (ld_acquire_gpu(gen) == g0) {
-                if (ld_volatile(a.status) != 0) break;
-                if (global_timer_ns() - t0 > a.timeout_ns) {
-                    raise_status(a.status, ADMM_ETIMEOUT);
-                    break;
+            for (unsigned polls = 1; ld_acquire_gpu(gen) == g0; ++polls) {
+                if ((polls & 63u) == 0) {
+                    if (ld_volatile(a.status) != 0) break;
+                    if (global_timer_ns() - t0 > a.timeout_ns) {
+                        raise_status(a.status, ADMM_ETIMEOUT);
+                        break;
+                    }
                 }
-                __nanosleep(32);
             }
         }
         __threadfence();
@@ -489,21 +492,25 @@ struct Consumer {
         const int stride = a.P * kConsumerWarps * groups;
         for (int base = (cta * kConsumerWarps + warp) * groups; base < total; base += stride) {
             const int idx = base + g;
-            float2 acc = make_float2(0.f, 0.f), acc2 = acc;
+            float2 acc = make_float2(0.f, 0.f);
             int j = 0, row = 0;
             if (idx < total) {
                 j = idx / a.m;
                 row = idx - j * a.m;
                 const int lo = a.j_cta_lo[j], hi = a.j_cta_hi[j];
                 const float2* pp = a.part + static_cast<size_t>(idx) * a.P;
-                int c = lo + gl;
-                for (; c + L <= hi; c += 2 * L) {
-                    acc = acc + ldcg2(pp + c);
-                    acc2 = acc2 + ldcg2(pp + c + L);
+                // up to 16 loads per lane issued before any is summed
+                for (int c0 = lo + gl; c0 <= hi; c0 += 16 * L) {
+                    float2 x[16];
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) {
+                        const int c = c0 + u * L;
+                        x[u] = c <= hi ? ldcg2(pp + c) : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 16; ++u) acc = acc + x[u];
                 }
-                if (c <= hi) acc = acc + ldcg2(pp + c);
             }
-            acc = acc + acc2;
             for (int o = L >> 1; o >= 1; o >>= 1) acc = acc + shfl2(acc, o);
             if (idx < total && gl == 0) {
                 float2 gtl = __ldg(a.g + row);
@@ -753,12 +760,16 @@ struct Consumer {
                 if (o1) vp[1] = vn1;
             }
         }
-        double d[5] = {rp, rdv, u2, v2, s2};
+        // FP32 within a warp (a few hundred positive terms), FP64 from the warp sums on
+        float d[5] = {rp, rdv, u2, v2, s2};
 #pragma unroll
-        for (int q = 0; q < 5; ++q) d[q] = warp_sum_d(d[q]);
+        for (int q = 0; q < 5; ++q) {
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+        }
         if (lane == 0) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) misc->red[warp][q] = d[q];
+            for (int q = 0; q < 5; ++q) misc->red[warp][q] = static_cast<double>(d[q]);
         }
         csync();
         if (tid < 5) {
