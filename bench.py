@@ -53,6 +53,9 @@ def parse_args(argv=None):
     ap.add_argument("--trace", type=int, default=0,
                     help="after the timed region, run this many traced iterations per split and "
                          "report the median time of each phase")
+    ap.add_argument("--l2-keep-mb", type=float, default=None,
+                    help="MiB of H per pass kept in L2 for the reversed next pass "
+                         "(ADMM_OPT_L2_KEEP_BYTES; default: the library's)")
     ap.add_argument("--cpu-sample-worker", action="store_true", help=argparse.SUPPRESS)
     return ap.parse_args(argv)
 
@@ -261,6 +264,9 @@ def run_ours(args) -> None:
             solvers.append(pkg.Solver(H_d, g_d, M, N, p.lam, p.rho, stream=stream))
     del H_d
     torch.cuda.synchronize()
+    if args.l2_keep_mb is not None:
+        for s in solvers:
+            s.set_option(pkg.ADMM_OPT_L2_KEEP_BYTES, int(args.l2_keep_mb * (1 << 20)))
     infos = [s.info() for s in solvers]
 
     def barrier():
@@ -373,6 +379,7 @@ def run_ours(args) -> None:
         "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS,
                    "splits": [f"{M}x{N}" for M, N in SPLITS],
                    "parallelism": "replicas" if world > 1 else "single GPU",
+                   "l2_keep_mb": args.l2_keep_mb,
                    "lambda": p.lam, "rho": p.rho,
                    "l2": "inputs larger than L2 (H 377 MB per split vs 129 MB L2), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",

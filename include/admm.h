@@ -72,11 +72,11 @@ extern "C" {
                                      call ends with ADMM_ETIMEOUT (0 = off, the default) */
 #define ADMM_OPT_TRACE_ITERS   4  /* record %globaltimer phase stamps of the first `value`
                                      iterations of each launch (0 = off, the default) */
-#define ADMM_OPT_L2_KEEP_BYTES 5  /* bytes of H at the end of each pass over H that are loaded
-                                     with the L2 evict_last policy, so the next pass (which
-                                     walks the rows in the opposite order) finds them in L2;
-                                     the rest is loaded evict_first (default 80 MiB; 0 = no
-                                     L2 policy hints) */
+#define ADMM_OPT_L2_KEEP_BYTES 5  /* bytes of H at the end of each pass over H that keep the
+                                     normal L2 priority, so the next pass (which walks the
+                                     rows in the opposite order) finds them in L2; the rest
+                                     of H and the factors are loaded evict_first (default
+                                     52 MiB; 0 = no L2 policy hints) */
 
 typedef struct admm_problem admm_t;
 

@@ -59,7 +59,7 @@ struct admm_problem {
     int trace_iters = 0;
     int64_t k = 0;       // iterations completed (host mirror)
     int pending = 0;     // the last launch's final residual record has not been summed yet
-    int64_t l2_keep_bytes = 80LL << 20;  // H bytes per pass marked L2 evict_last
+    int64_t l2_keep_bytes = 52LL << 20;  // H bytes per pass kept for the reversed next pass
     int broken = 0;      // sticky error that blocks further iterations
     double gram_ms = 0.0, factor_ms = 0.0;
     std::string err;

@@ -157,10 +157,11 @@ __device__ bool producer_wait(uint64_t* bar, uint32_t parity, const IterArgs& a,
 __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* full,
                          uint64_t* empty, Misc* misc, unsigned char* ring, int c_beg) {
     prefetch_tensormap(tmap);
-    // The last keep_stages stages of every pass are marked evict_last: the next
-    // pass walks the rows in the opposite order and finds them in L2.  All
-    // other stages are streamed evict_first so they do not displace them.
-    const uint64_t pol_first = policy_evict_first(), pol_last = policy_evict_last();
+    // The last keep_stages stages of every pass keep the normal L2 priority:
+    // the next pass walks the rows in the opposite order and finds them in
+    // L2.  All other stages are streamed evict_first so they do not displace
+    // them, and once read the kept lines age out like any other line.
+    const uint64_t pol_first = policy_evict_first();
     int per_pass = 0;
     for (int i = 0; i < a.M; ++i) per_pass += (a.row_off[i + 1] - a.row_off[i] + a.R - 1) / a.R;
     int stage = 0;
@@ -183,14 +184,14 @@ __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* f
                     }
                     mbar_arrive_expect_tx(&full[slot], static_cast<uint32_t>(a.stage_bytes));
                     unsigned char* dst = ring + static_cast<size_t>(slot) * a.stage_stride;
-                    const uint64_t pol = pos >= per_pass - a.keep_stages ? pol_last : pol_first;
+                    const bool keep = a.keep_stages <= 0 || pos >= per_pass - a.keep_stages;
                     for (int sb = 0; sb < a.nsub; ++sb) {
-                        if (a.keep_stages > 0)
-                            tma_load_2d_hint(dst + static_cast<size_t>(sb) * a.sub_bytes, tmap,
-                                             c_beg + sb * a.wbox, y, &full[slot], pol);
-                        else
+                        if (keep)
                             tma_load_2d(dst + static_cast<size_t>(sb) * a.sub_bytes, tmap,
                                         c_beg + sb * a.wbox, y, &full[slot]);
+                        else
+                            tma_load_2d_hint(dst + static_cast<size_t>(sb) * a.sub_bytes, tmap,
+                                             c_beg + sb * a.wbox, y, &full[slot], pol_first);
                     }
                     ++stage;
                     *reinterpret_cast<volatile int*>(&misc->issued) = stage;

@@ -280,7 +280,7 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
         a.hist_cap = 1;
         a.iters = iters;
         a.timeout_ns = 5000000000LL;
-        a.keep_stages = static_cast<int>((80LL << 20) / (static_cast<long long>(pl.R) * pl.ld * 8));
+        a.keep_stages = static_cast<int>((52LL << 20) / (static_cast<long long>(pl.R) * pl.ld * 8));
         a.pending_prev = 0;
         NA_CK(admm::launch_iterate(tmap, a, pl.chunks, pl.smem, st));
     }
