@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define ADMM_ABI_VERSION 1
+#define ADMM_ABI_VERSION 2
 
 /* status codes */
 #define ADMM_OK            0  /* success */
@@ -77,6 +77,19 @@ extern "C" {
                                      rows in the opposite order) finds them in L2; the rest
                                      of H and the factors are loaded evict_first (default
                                      52 MiB; 0 = no L2 policy hints) */
+#define ADMM_OPT_H_FP16        6  /* 1: stream an FP16 copy of H (half the bytes per pass);
+                                     0: stream the complex64 H (the default).  The first 1
+                                     builds the copy: every 64-row group g of H gets the scale
+                                     c_g = 2^(q-14), where max over the group of max(|Re|,|Im|)
+                                     is f 2^q with f in [0.5, 1), and H16 = fp16_rn(H / c_g)
+                                     (round to nearest even; |H / c_g| < 2^14).  The cached
+                                     factors of that mode are those of the matrix H16 c_g
+                                     encodes, so an FP16 run is exact ADMM on that matrix.
+                                     The iteration state is shared: switching back to 0
+                                     continues from the FP16 iterate on the complex64 H
+                                     (polish iterations).  The copy takes m * ld * 4 bytes
+                                     more device memory and is kept until admm_destroy;
+                                     admm_set_rho refactors both.  Synchronises the device. */
 
 typedef struct admm_problem admm_t;
 
@@ -98,6 +111,9 @@ typedef struct admm_info {
     int64_t state_bytes;      /* bytes of v, s, u, estimated data and scratch */
     double setup_gram_ms;     /* device time of the Gram products */
     double setup_factor_ms;   /* device time of the FP64 Cholesky and inverse */
+    int32_t h_fp16;           /* 1 while the iterations stream the FP16 copy of H */
+    int32_t h16_ready;        /* 1 once the FP16 copy and its factors exist */
+    int64_t h16_bytes;        /* bytes of H streamed by one pass in FP16 (m * n * 4), 0 if none */
 } admm_info_t;
 
 /* Launch plan of the iteration kernel, computed on the host (admm_plan). */

@@ -21,3 +21,4 @@ from .admm_fp64 import (  # noqa: F401
     comm_elements,
     lemma_applies,
 )
+from . import quantize  # noqa: F401,E402

@@ -20,7 +20,8 @@ ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ENOTPD = 0, 1, 2, 3, 4
 ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED = 5, 6, 7, 8
 ADMM_C64, ADMM_C128 = 0, 1
 ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS = 1, 2, 3, 4
-ADMM_OPT_L2_KEEP_BYTES = 5
+ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16 = 5, 6
+ABI_VERSION = 2
 
 
 class AdmmInfo(ctypes.Structure):
@@ -31,7 +32,8 @@ class AdmmInfo(ctypes.Structure):
                 ("stages", c_int32), ("slab_cols", c_int32), ("smem_bytes", c_int32),
                 ("num_sms", c_int32), ("h_bytes", c_int64), ("factor_bytes", c_int64),
                 ("state_bytes", c_int64), ("setup_gram_ms", c_double),
-                ("setup_factor_ms", c_double)]
+                ("setup_factor_ms", c_double), ("h_fp16", c_int32), ("h16_ready", c_int32),
+                ("h16_bytes", c_int64)]
 
     def as_dict(self) -> dict:
         return {name.rstrip("_"): getattr(self, name) for name, _ in self._fields_}

@@ -48,6 +48,14 @@ struct admm_problem {
     int* status = nullptr;
     int* stop_flag = nullptr;
     CUtensorMap tmap;
+    // FP16 copy of H (ADMM_OPT_H_FP16): one complex element in 4 bytes, a
+    // power-of-two scale per 64-row group, and the factors of the matrix it encodes
+    void* H16 = nullptr;
+    float* scales = nullptr;
+    unsigned* gmax = nullptr;
+    float2* kinv16 = nullptr;
+    CUtensorMap tmap16;
+    int use_f16 = 0;     // the iteration kernel streams H16
     std::vector<long long> kinv_off;
     std::vector<int> kinv_pitch;
     int64_t kinv_elems = 0;
@@ -99,7 +107,7 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(admm_t* h) {
     void* ptrs[] = {h->H, h->g, h->v, h->s, h->u, h->ghat, h->gt, h->r, h->w, h->part, h->kinv,
                     h->kinv_off_d, h->ints_d, h->res_part, h->hist, h->k_done, h->bar, h->status,
-                    h->stop_flag, h->trace};
+                    h->stop_flag, h->trace, h->H16, h->scales, h->gmax, h->kinv16};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -256,6 +264,15 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     pl.nsub = (pl.wmax + 255) / 256;
     pl.wbox = round_up((pl.wmax + pl.nsub - 1) / pl.nsub, 2);
     const int npitch = pl.wbox * pl.nsub / 2;   // pair pitch of the per-pair buffers
+    pl.npitch = npitch;
+    // FP16 stream: the box starts at the slab start rounded down to 4 columns
+    // (16 bytes of 4-byte elements), so it covers up to 2 columns more
+    pl.nsub16 = (pl.wmax + 2 + 255) / 256;
+    pl.wbox16 = round_up((pl.wmax + 2 + pl.nsub16 - 1) / pl.nsub16, 4);
+    if (pl.wbox16 > 256) {
+        ++pl.nsub16;
+        pl.wbox16 = round_up((pl.wmax + 2 + pl.nsub16 - 1) / pl.nsub16, 4);
+    }
     pl.mimax = 0;
     for (int i = 0; i < M; ++i) pl.mimax = std::max(pl.mimax, row_off[i + 1] - row_off[i]);
     pl.kpmax = round_up(pl.mimax, 4);
@@ -272,9 +289,10 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     const int fixed = round_up(ws, 128) + 2 * round_up(rs, 128) + round_up(red, 128) +
                       round_up(sigma, 128) + misc + 256 + 1024;
     pl.R = rows_per_stage(pl.chunks);
+    pl.R16 = rows_per_stage(pl.chunks, true);
     pl.sub_bytes = pl.R * pl.wbox * 8;
     pl.stage_bytes = pl.sub_bytes * pl.nsub;
-    pl.stage_stride = round_up(pl.stage_bytes, 128);
+    pl.stage_stride = round_up(std::max(pl.stage_bytes, pl.R16 * pl.wbox16 * 4 * pl.nsub16), 128);
     pl.nstages = std::min(8, (smem_limit - fixed) / pl.stage_stride);
     if (pl.nstages < 2) {
         *why = "shared memory too small for two pipeline stages";
@@ -355,7 +373,7 @@ int copy_vector_in(admm_t* h, float2* dst, const void* src, int64_t count, int d
     return ADMM_OK;
 }
 
-int build_factors(admm_t* h, cudaStream_t st) {
+int build_factors(admm_t* h, cudaStream_t st, const float2* H, float2* kinv, bool timed) {
     const Plan& pl = h->plan;
     const int T = (pl.mimax + admm::kTile - 1) / admm::kTile;
     const size_t S = static_cast<size_t>(T) * admm::kTile;
@@ -374,10 +392,10 @@ int build_factors(admm_t* h, cudaStream_t st) {
     f.T = T;
     f.row_off = h->row_off_d;
     f.col_off = h->col_off_d;
-    f.H = h->H;
+    f.H = H;
     f.A = A;
     f.W = W;
-    f.kinv = h->kinv;
+    f.kinv = kinv;
     f.kinv_off = h->kinv_off_d;
     f.kinv_pitch = h->kinv_pitch_d;
     f.rho = h->rho;
@@ -386,7 +404,7 @@ int build_factors(admm_t* h, cudaStream_t st) {
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     cudaEventCreate(&e2);
-    cudaError_t err = cudaMemsetAsync(h->kinv, 0, h->kinv_elems * sizeof(float2), st);
+    cudaError_t err = cudaMemsetAsync(kinv, 0, h->kinv_elems * sizeof(float2), st);
     if (err == cudaSuccess) err = cudaMemsetAsync(h->status, 0, sizeof(int), st);
     if (err == cudaSuccess) err = cudaEventRecord(e0, st);
     if (err == cudaSuccess) err = admm::launch_gram(f, st);
@@ -405,14 +423,31 @@ int build_factors(admm_t* h, cudaStream_t st) {
     cudaFree(A);
     cudaFree(W);
     if (err != cudaSuccess) return cuda_fail(h, err, "factor kernels");
-    h->gram_ms = t01;
-    h->factor_ms = t12;
+    if (timed) {
+        h->gram_ms = t01;
+        h->factor_ms = t12;
+    }
     int st_code = 0;
     CK(h, cudaMemcpy(&st_code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st_code == ADMM_ENOTPD)
         return fail(h, ADMM_ENOTPD, "a block rho I + H_b H_b^H is not positive definite in FP64");
     if (st_code != 0) return fail(h, st_code, "factor kernels raised status %d", st_code);
     return ADMM_OK;
+}
+
+// factors of the matrix the FP16 copy encodes (dequantised into a scratch copy)
+int build_factors_f16(admm_t* h, cudaStream_t st) {
+    const size_t elems = static_cast<size_t>(h->plan.ld) * h->m;
+    float2* Hdeq = nullptr;
+    if (dalloc(&Hdeq, elems) != cudaSuccess)
+        return fail(h, ADMM_ENOMEM, "cannot allocate %.1f MB to dequantise the FP16 copy of H", elems * 8 / 1e6);
+    cudaError_t e = admm::launch_dequantize_f16(h->H16, h->m, h->plan.ld, h->scales, Hdeq, st);
+    int code = ADMM_OK;
+    if (e != cudaSuccess) code = cuda_fail(h, e, "dequantise H");
+    else code = build_factors(h, st, Hdeq, h->kinv16, false);
+    cudaStreamSynchronize(st);
+    cudaFree(Hdeq);
+    return code;
 }
 
 int encode_tensor_map(admm_t* h) {
@@ -427,14 +462,58 @@ int encode_tensor_map(admm_t* h) {
         encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     const Plan& pl = h->plan;
-    cuuint64_t dims[2] = {static_cast<cuuint64_t>(pl.ld), static_cast<cuuint64_t>(h->m)};
-    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pl.ld) * sizeof(float2)};
-    cuuint32_t box[2] = {static_cast<cuuint32_t>(pl.wbox), static_cast<cuuint32_t>(pl.R)};
-    cuuint32_t estr[2] = {1, 1};
-    CUresult r = encode(&h->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, h->H, dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(h, ADMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    // complex64 H: one 8-byte element per complex entry; FP16 H: one 4-byte element
+    const bool f16 = h->H16 != nullptr;
+    for (int f = 0; f < (f16 ? 2 : 1); ++f) {
+        const size_t eb = f ? 4 : 8;
+        cuuint64_t dims[2] = {static_cast<cuuint64_t>(pl.ld), static_cast<cuuint64_t>(h->m)};
+        cuuint64_t strides[1] = {static_cast<cuuint64_t>(pl.ld) * eb};
+        cuuint32_t box[2] = {static_cast<cuuint32_t>(f ? pl.wbox16 : pl.wbox),
+                             static_cast<cuuint32_t>(f ? pl.R16 : pl.R)};
+        cuuint32_t estr[2] = {1, 1};
+        CUresult r = encode(f ? &h->tmap16 : &h->tmap,
+                            f ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                            f ? h->H16 : static_cast<void*>(h->H), dims, strides, box, estr,
+                            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) return fail(h, ADMM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    }
+    return ADMM_OK;
+}
+
+// quantise H to the FP16 copy and factor the matrix it encodes (once per handle)
+int enable_f16(admm_t* h) {
+    if (h->H16) return ADMM_OK;
+    const Plan& pl = h->plan;
+    const size_t elems = static_cast<size_t>(pl.ld) * h->m;
+    const int64_t groups = (h->m + 63) / 64;
+    if (cudaMalloc(&h->H16, elems * 4) != cudaSuccess || dalloc(&h->scales, groups) != cudaSuccess ||
+        dalloc(&h->gmax, groups) != cudaSuccess || dalloc(&h->kinv16, h->kinv_elems) != cudaSuccess) {
+        void* ptrs[] = {h->H16, h->scales, h->gmax, h->kinv16};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        h->H16 = nullptr;
+        h->scales = nullptr;
+        h->gmax = nullptr;
+        h->kinv16 = nullptr;
+        return fail(h, ADMM_ENOMEM, "cannot allocate %.1f MB for the FP16 copy of H", elems * 4 / 1e6);
+    }
+    cudaStream_t st = nullptr;
+    CK(h, cudaDeviceSynchronize());
+    CK(h, admm::launch_quantize_f16(h->H, h->m, pl.ld, h->gmax, h->H16, h->scales, nullptr, st));
+    int code = build_factors_f16(h, st);
+    if (code == ADMM_OK) code = encode_tensor_map(h);
+    if (code) {
+        void* ptrs[] = {h->H16, h->scales, h->gmax, h->kinv16};
+        for (void* p : ptrs)
+            if (p) cudaFree(p);
+        h->H16 = nullptr;
+        h->scales = nullptr;
+        h->gmax = nullptr;
+        h->kinv16 = nullptr;
+        return code;
+    }
+    CK(h, cudaDeviceSynchronize());
     return ADMM_OK;
 }
 
@@ -458,7 +537,8 @@ int zero_state(admm_t* h, cudaStream_t st) {
 // stages per pass whose H rows stay in L2 for the reversed next pass
 int keep_stages(const admm_t* h) {
     const Plan& pl = h->plan;
-    const int64_t per_stage = static_cast<int64_t>(pl.R) * pl.ld * static_cast<int64_t>(sizeof(float2));
+    const int64_t per_stage = h->use_f16 ? static_cast<int64_t>(pl.R16) * pl.ld * 4
+                                         : static_cast<int64_t>(pl.R) * pl.ld * 8;
     return static_cast<int>(std::max<int64_t>(0, h->l2_keep_bytes / std::max<int64_t>(per_stage, 1)));
 }
 
@@ -473,13 +553,16 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.M = h->M;
     a.N = h->N;
     a.P = pl.P;
-    a.R = pl.R;
+    const bool f16 = h->use_f16 != 0;
+    a.R = f16 ? pl.R16 : pl.R;
     a.nstages = pl.nstages;
-    a.stage_bytes = pl.stage_bytes;
     a.stage_stride = pl.stage_stride;
-    a.sub_bytes = pl.sub_bytes;
-    a.nsub = pl.nsub;
-    a.wbox = pl.wbox;
+    a.nsub = f16 ? pl.nsub16 : pl.nsub;
+    a.wbox = f16 ? pl.wbox16 : pl.wbox;
+    a.elem_bytes = f16 ? 4 : 8;
+    a.sub_bytes = a.R * a.wbox * a.elem_bytes;
+    a.stage_bytes = a.sub_bytes * a.nsub;
+    a.npitch = pl.npitch;
     a.mimax = pl.mimax;
     a.kpmax = pl.kpmax;
     a.off_ring = pl.off_ring;
@@ -520,7 +603,8 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.r = h->r;
     a.w = h->w;
     a.part = h->part;
-    a.kinv = h->kinv;
+    a.kinv = f16 ? h->kinv16 : h->kinv;
+    a.scales = f16 ? h->scales : nullptr;
     a.kinv_off = h->kinv_off_d;
     a.kinv_pitch = h->kinv_pitch_d;
     a.res_part = h->res_part;
@@ -541,7 +625,7 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.trace_iters = h->trace_iters;
     a.keep_stages = keep_stages(h);
     a.pending_prev = h->pending && h->k > 0 ? 1 : 0;
-    cudaError_t e = admm::launch_iterate(h->tmap, a, pl.chunks, pl.smem, st);
+    cudaError_t e = admm::launch_iterate(f16 ? h->tmap16 : h->tmap, a, pl.chunks, pl.smem, st, f16);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the iteration kernel");
     h->k += iters;
     h->pending = 1;   // this launch's last record is summed by the next launch or a sync call
@@ -791,7 +875,7 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     SETUP_CK(cudaStreamSynchronize(st));
     SETUP_CK(cudaMemcpy(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) return bail(fail(h, ADMM_ENONFINITE, "H or g holds NaN or Inf"));
-    code = build_factors(h, st);
+    code = build_factors(h, st, h->H, h->kinv, true);
     if (code) return bail(code);
     code = encode_tensor_map(h);
     if (code) return bail(code);
@@ -888,9 +972,12 @@ int admm_set_rho(admm_t* h, double rho, void* stream) {
     cudaStream_t st = as_stream(stream);
     const double old = h->rho;
     h->rho = rho;
-    int code = build_factors(h, st);
+    int code = build_factors(h, st, h->H, h->kinv, true);
+    if (code == ADMM_OK && h->H16) code = build_factors_f16(h, st);
     if (code) {
         h->rho = old;
+        build_factors(h, st, h->H, h->kinv, true);
+        if (h->H16) build_factors_f16(h, st);
         return code;
     }
     CK(h, admm::launch_scale(h->s, static_cast<int64_t>(h->plan.ld) * h->M, static_cast<float>(old / rho), st));
@@ -958,7 +1045,7 @@ int admm_get_info(const admm_t* h, admm_info_t* info) {
     info->kappa = h->lambda / (h->M * h->rho);
     info->iterations = h->k;
     info->ctas = pl.P;
-    info->rows_per_stage = pl.R;
+    info->rows_per_stage = h->use_f16 ? pl.R16 : pl.R;
     info->stages = pl.nstages;
     info->slab_cols = pl.wmax;
     info->smem_bytes = pl.smem;
@@ -968,6 +1055,9 @@ int admm_get_info(const admm_t* h, admm_info_t* info) {
     info->state_bytes = h->state_bytes;
     info->setup_gram_ms = h->gram_ms;
     info->setup_factor_ms = h->factor_ms;
+    info->h_fp16 = h->use_f16;
+    info->h16_ready = h->H16 ? 1 : 0;
+    info->h16_bytes = h->H16 ? h->m * h->n * 4 : 0;
     return ADMM_OK;
 }
 
@@ -1006,6 +1096,15 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
             if (value < 0) return fail(h, ADMM_EINVAL, "L2 keep bytes must be >= 0");
             h->l2_keep_bytes = value;
             return ADMM_OK;
+        case ADMM_OPT_H_FP16: {
+            if (value != 0 && value != 1) return fail(h, ADMM_EINVAL, "ADMM_OPT_H_FP16 takes 0 or 1");
+            if (value == 1) {
+                const int code = enable_f16(h);
+                if (code) return code;
+            }
+            h->use_f16 = static_cast<int>(value);
+            return ADMM_OK;
+        }
         case ADMM_OPT_BARRIER_EXTRA:
             if (value < 0 || value > 1024) return fail(h, ADMM_EINVAL, "barrier extra out of range");
             h->bar_extra = static_cast<int>(value);

@@ -42,6 +42,10 @@ struct Plan {
     int red_lanes = 32;   // lanes summing the partials of one (block, row) in phase B
     bool ws_all = false;  // the whole w (m x njs) fits in shared memory
     int ws_rows = 0;      // rows of the shared w staging buffer
+    int R16 = 0;          // FP16 stream: rows per stage
+    int wbox16 = 0;       // FP16 stream: TMA box width (columns, multiple of 4)
+    int nsub16 = 0;       // FP16 stream: boxes per slab row
+    int npitch = 0;       // pair pitch of the per-pair shared buffers
     bool sigma_global = false;  // H_i^H w_i sums kept in the u buffer (wide slabs, many row blocks)
     bool red_single = false;    // one cross-warp reduction buffer instead of two
     std::vector<int> cta_beg;   // P slab starts (even)
@@ -69,6 +73,8 @@ void set_handle_free_error(const char* msg);
 struct IterArgs {
     int m, n, ld, M, N, P;
     int R, nstages, stage_bytes, stage_stride, sub_bytes, nsub, wbox;
+    int elem_bytes;       // bytes of one complex element of the streamed H (8 complex64, 4 FP16)
+    int npitch;           // pair pitch of the per-pair shared buffers (red, sigma)
     int mimax, kpmax;
     int off_ring, off_full, off_empty, off_ws, off_rs, off_gs, off_red, off_sigma, off_misc;
     int red_lanes, ws_all, ws_rows, sigma_global, red_single;
@@ -110,21 +116,24 @@ struct IterArgs {
     double eps_abs, eps_rel;
     long long timeout_ns;
     int bar_extra;
+    const float* scales;  // FP16 stream: one scale per 64-row group (null for complex64 H)
     long long* trace;     // optional phase timestamps (2 CTAs x trace_iters x 8)
     int trace_iters;
-    int keep_stages;      // last stages of each pass loaded L2 evict_last (0 = no L2 hints)
+    int keep_stages;      // last stages of each pass keep the normal L2 priority (0 = no L2 hints)
     int pending_prev;     // the previous launch's last residual record is still to be summed
 };
 
 // Sum the per-CTA residual partials of iteration kabs into the history ring.
 cudaError_t launch_finalize(const IterArgs& a, long long kabs, cudaStream_t stream);
 
-// Rows of H per pipeline stage of the kernel instance with `chunks` chunks.
-int rows_per_stage(int chunks);
+// Rows of H per pipeline stage of the kernel instance with `chunks` chunks
+// (complex64 or FP16 storage).
+int rows_per_stage(int chunks, bool f16 = false);
 
 // Launch the persistent cooperative iteration kernel for `a.iters` iterations.
+// `f16` selects the instance that streams FP16 H (4-byte complex elements).
 cudaError_t launch_iterate(const CUtensorMap& tmap, const IterArgs& a, int chunks, int smem,
-                           cudaStream_t stream);
+                           cudaStream_t stream, bool f16 = false);
 // Opt the kernel instances into `smem` bytes of dynamic shared memory.
 cudaError_t prepare_iterate(int chunks, int smem);
 int max_coresident_iterate(int chunks, int smem, int* per_sm);
@@ -155,5 +164,11 @@ cudaError_t launch_pack_c128(const double2* src, int64_t m, int64_t n, float2* d
                              cudaStream_t s);
 cudaError_t launch_finite_check(const float2* x, int64_t count, int* flag, cudaStream_t s);
 cudaError_t launch_scale(float2* x, int64_t count, float alpha, cudaStream_t s);
+// FP16 copy of H with one power-of-two scale per 64-row group (and, when Hdeq
+// is not null, the dequantised matrix in FP32); gmax_bits holds ceil(m/64) words.
+cudaError_t launch_quantize_f16(const float2* H, int64_t m, int64_t ld, unsigned* gmax_bits,
+                                void* H16, float* scales, float2* Hdeq, cudaStream_t s);
+cudaError_t launch_dequantize_f16(const void* H16, int64_t m, int64_t ld, const float* scales,
+                                  float2* Hdeq, cudaStream_t s);
 
 }  // namespace admm

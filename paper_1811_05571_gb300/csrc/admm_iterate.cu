@@ -27,6 +27,8 @@
 // upwards, pass D downwards, so the rows the previous pass read last are still
 // in L2.  Only the m-length products cross CTAs, through three grid barriers
 // per iteration whose waits are bounded by %globaltimer.
+#include <cuda_fp16.h>
+
 #include "admm_internal.h"
 #include "ptx.cuh"
 
@@ -155,8 +157,10 @@ __device__ bool producer_wait(uint64_t* bar, uint32_t parity, const IterArgs& a,
 }
 
 __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* full,
-                         uint64_t* empty, Misc* misc, unsigned char* ring, int c_beg) {
+                         uint64_t* empty, Misc* misc, unsigned char* ring, int c_beg_slab) {
     prefetch_tensormap(tmap);
+    // 4-byte elements: start at a multiple of 4 columns (x * 4 bytes a multiple of 16)
+    const int c_beg = a.elem_bytes == 4 ? (c_beg_slab & ~3) : c_beg_slab;
     // The last keep_stages stages of every pass keep the normal L2 priority:
     // the next pass walks the rows in the opposite order and finds them in
     // L2.  All other stages are streamed evict_first so they do not displace
@@ -240,15 +244,18 @@ __device__ void finalize_record(const IterArgs& a, long long kabs, int lane, boo
 // consumer warps
 // ---------------------------------------------------------------------------
 
-// rows of H per pipeline stage for a slab of CH 32-pair chunks (about 32 KB)
-template <int CH>
+// rows of H per pipeline stage for a slab of CH 32-pair chunks (about 32 KB of
+// complex64; FP16 stages take twice the rows, up to 64, to keep the bytes in
+// flight per SM)
+template <int CH, bool F16>
 struct RowsOf {
-    static constexpr int value = CH >= 8 ? 8 : 64 / CH;
+    static constexpr int base = CH >= 8 ? 8 : 64 / CH;
+    static constexpr int value = F16 ? (2 * base < 64 ? 2 * base : 64) : base;
 };
 
-template <int CH>
+template <int CH, bool F16>
 struct Consumer {
-    static constexpr int kR = RowsOf<CH>::value;  // rows per stage
+    static constexpr int kR = RowsOf<CH, F16>::value;  // rows per stage
     static constexpr int kRPW = kR / kConsumerWarps;  // rows per warp per stage
     static constexpr int kWin = 8 / kRPW;             // stages per 8-row reduction window
     static constexpr bool kPrefetch = CH <= 4;        // keep v and the next s_i in registers
@@ -280,17 +287,19 @@ struct Consumer {
         nj = a.cta_nj[cta];
         own0 = a.cta_own0[cta];
         own1 = a.cta_own1[cta];
-        npmax = a.wbox * a.nsub / 2;
+        npmax = a.npitch;
         stage = 0;
         valid = 0;
         owned = 0;
         jl = 0;
-        const int ppb = a.wbox >> 1;
+        // columns of the stage box start at the slab start (FP16: rounded down to 4)
+        const int shift = F16 ? (c_beg & 3) : 0;
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
             const int p = lane + 32 * k;
-            const int sb = p / ppb;
-            soff[k] = sb * a.sub_bytes + (p - sb * ppb) * 16;
+            const int rel = 2 * p + shift;
+            const int sb = rel / a.wbox;
+            soff[k] = sb * a.sub_bytes + (rel - sb * a.wbox) * (F16 ? 4 : 8);
             if (p < npairs) {
                 valid |= 1u << k;
                 const int c0 = c_beg + 2 * p;
@@ -314,6 +323,20 @@ struct Consumer {
         return static_cast<int>((jl >> (4 * k + 2 * h)) & 3u);
     }
     __device__ __forceinline__ int col_of(int k) const { return c_beg + 2 * (lane + 32 * k); }
+
+    // one 16-byte complex pair of H (FP16 storage: 8 bytes, converted to FP32)
+    __device__ __forceinline__ float4 load_pair(const unsigned char* rowp, int k) const {
+        if (F16) {
+            const uint2 raw = *reinterpret_cast<const uint2*>(rowp + soff[k]);
+            const float2 c0 = __half22float2(*reinterpret_cast<const __half2*>(&raw.x));
+            const float2 c1 = __half22float2(*reinterpret_cast<const __half2*>(&raw.y));
+            return make_float4(c0.x, c0.y, c1.x, c1.y);
+        }
+        return lds128(rowp + soff[k]);
+    }
+    __device__ __forceinline__ float row_scale(int row) const {
+        return F16 ? __ldg(a.scales + (row >> 6)) : 1.0f;
+    }
 
     __device__ __forceinline__ void stamp(int it, int q) {
         if (a.trace && it < a.trace_iters && tid == 0 && (cta == 0 || cta == a.P - 1)) {
@@ -349,7 +372,7 @@ struct Consumer {
 
     // ---- pass A (one column block per slab) --------------------------------
     __device__ void pass_up_single() {
-        const int rowpitch = a.wbox * 8;
+        const int rowpitch = a.wbox * (F16 ? 4 : 8);
         float4 vreg[kPrefetch ? CH : 1], snext[kPrefetch ? CH : 1];
         if (kPrefetch) {
 #pragma unroll
@@ -404,7 +427,7 @@ struct Consumer {
 #pragma unroll
                             for (int k = 0; k < CH; ++k) {
                                 if (is_valid(k)) {
-                                    const float4 h = lds128(rowp + soff[k]);
+                                    const float4 h = load_pair(rowp, k);
                                     accA[v] = fma2(lo2(h), zr0[k], accA[v]);
                                     accB[v] = fma2(lo2(h), zi0[k], accB[v]);
                                     accA[v] = fma2(hi2(h), zr1[k], accA[v]);
@@ -420,10 +443,14 @@ struct Consumer {
 #pragma unroll
                 for (int v = 0; v < 8; ++v)
                     val[v] = make_float2(accA[v].x - accB[v].y, accA[v].y + accB[v].x);
-                const float2 sum = butterfly8(val, lane);
+                float2 sum = butterfly8(val, lane);
                 const int v = lane >> 2;
                 const int wi = v / kRPW, q = v - wi * kRPW;
                 const int row = r0 + (b0 + wi) * kR + warp + kConsumerWarps * q;
+                if (F16) {
+                    const float sc = row_scale(min(row, a.m - 1));
+                    sum = make_float2(sum.x * sc, sum.y * sc);
+                }
                 if ((lane & 3) == 0 && b0 + wi < nb && row < r1)
                     stcg2(a.part + (static_cast<size_t>(jlo) * a.m + row) * a.P + cta, sum);
             }
@@ -432,7 +459,7 @@ struct Consumer {
 
     // ---- pass A (slab meeting several column blocks) -------------------------
     __device__ void pass_up_multi() {
-        const int rowpitch = a.wbox * 8;
+        const int rowpitch = a.wbox * (F16 ? 4 : 8);
         for (int i = 0; i < a.M; ++i) {
             const int r0 = a.row_off[i], r1 = a.row_off[i + 1];
             float4 z[CH];
@@ -461,12 +488,16 @@ struct Consumer {
                             if (is_valid(k)) {
                                 const float2 z0 = jl_of(k, 0) == jj ? lo2(z[k]) : make_float2(0.f, 0.f);
                                 const float2 z1 = jl_of(k, 1) == jj ? hi2(z[k]) : make_float2(0.f, 0.f);
-                                const float4 h = lds128(rowp + soff[k]);
+                                const float4 h = load_pair(rowp, k);
                                 cfma(acc, lo2(h), z0);
                                 cfma(acc, hi2(h), z1);
                             }
                         }
                         acc = warp_sum(acc);
+                        if (F16) {
+                            const float sc = row_scale(min(row, a.m - 1));
+                            acc = make_float2(acc.x * sc, acc.y * sc);
+                        }
                         if (lane == 0 && row < r1)
                             stcg2(a.part + (static_cast<size_t>(jlo + jj) * a.m + row) * a.P + cta, acc);
                     }
@@ -602,15 +633,21 @@ struct Consumer {
     __device__ void stage_w(int r0, int rows, int row_base_in_ws) {
         float2* wS = reinterpret_cast<float2*>(smem + a.off_ws);
         const int wpitch = a.ws_rows;
+        // FP16 stream: fold the row scale of H into w (H_i^H w = sum conj(h16) (scale w))
         for (int jj = 0; jj < nj; ++jj)
-            for (int k = tid; k < rows; k += kConsumerThreads)
-                wS[jj * wpitch + row_base_in_ws + k] =
-                    ldcg2(a.w + static_cast<size_t>(jlo + jj) * a.m + r0 + k);
+            for (int k = tid; k < rows; k += kConsumerThreads) {
+                float2 wv = ldcg2(a.w + static_cast<size_t>(jlo + jj) * a.m + r0 + k);
+                if (F16) {
+                    const float sc = row_scale(r0 + k);
+                    wv = make_float2(wv.x * sc, wv.y * sc);
+                }
+                wS[jj * wpitch + row_base_in_ws + k] = wv;
+            }
     }
 
     template <bool MULTI>
     __device__ void pass_down() {
-        const int rowpitch = a.wbox * 8;
+        const int rowpitch = a.wbox * (F16 ? 4 : 8);
         const float2* wS = reinterpret_cast<const float2*>(smem + a.off_ws);
         float4* red = reinterpret_cast<float4*>(smem + a.off_red);
         float4* sigma = reinterpret_cast<float4*>(smem + a.off_sigma);
@@ -647,7 +684,7 @@ struct Consumer {
 #pragma unroll
                         for (int k = 0; k < CH; ++k) {
                             if (is_valid(k)) {
-                                const float4 h = lds128(rowp + soff[k]);
+                                const float4 h = load_pair(rowp, k);
                                 aA0[k] = fma2(lo2(h), wre, aA0[k]);
                                 aB0[k] = fma2(lo2(h), wim, aB0[k]);
                                 aA1[k] = fma2(hi2(h), wre, aA1[k]);
@@ -663,7 +700,7 @@ struct Consumer {
 #pragma unroll
                         for (int k = 0; k < CH; ++k) {
                             if (is_valid(k)) {
-                                const float4 h = lds128(rowp + soff[k]);
+                                const float4 h = load_pair(rowp, k);
                                 const float2 w0 = wv[jl_of(k, 0)], w1 = wv[jl_of(k, 1)];
                                 aA0[k] = fma2(lo2(h), make_float2(w0.x, w0.x), aA0[k]);
                                 aB0[k] = fma2(lo2(h), make_float2(w0.y, w0.y), aB0[k]);
@@ -830,7 +867,7 @@ struct Consumer {
     }
 };
 
-template <int CH>
+template <int CH, bool F16>
 __global__ void __launch_bounds__(kIterThreads, 1)
     iterate_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ IterArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -857,7 +894,7 @@ __global__ void __launch_bounds__(kIterThreads, 1)
             producer(&tmap, a, full, empty, misc, ring, a.cta_col[blockIdx.x]);
         return;
     }
-    Consumer<CH> c(a, smem, misc, full, empty, ring);
+    Consumer<CH, F16> c(a, smem, misc, full, empty, ring);
     c.run();
 }
 
@@ -865,39 +902,46 @@ __global__ void __launch_bounds__(32) finalize_kernel(const __grid_constant__ It
     finalize_record(a, kabs, threadIdx.x & 31, false);
 }
 
-template <int CH>
+template <int CH, bool F16>
 void* kernel_fn() {
-    return reinterpret_cast<void*>(&iterate_kernel<CH>);
+    return reinterpret_cast<void*>(&iterate_kernel<CH, F16>);
 }
 
-void* pick(int chunks) {
+template <bool F16>
+void* pick_t(int chunks) {
     switch (chunks) {
-        case 1: return kernel_fn<1>();
-        case 2: return kernel_fn<2>();
-        case 4: return kernel_fn<4>();
-        case 8: return kernel_fn<8>();
-        case 16: return kernel_fn<16>();
+        case 1: return kernel_fn<1, F16>();
+        case 2: return kernel_fn<2, F16>();
+        case 4: return kernel_fn<4, F16>();
+        case 8: return kernel_fn<8, F16>();
+        case 16: return kernel_fn<16, F16>();
         default: return nullptr;
     }
 }
 
+void* pick(int chunks, bool f16 = false) { return f16 ? pick_t<true>(chunks) : pick_t<false>(chunks); }
+
 }  // namespace
 
-int rows_per_stage(int chunks) {
+int rows_per_stage(int chunks, bool f16) {
     switch (chunks) {
-        case 1: return RowsOf<1>::value;
-        case 2: return RowsOf<2>::value;
-        case 4: return RowsOf<4>::value;
-        case 8: return RowsOf<8>::value;
-        case 16: return RowsOf<16>::value;
+        case 1: return f16 ? RowsOf<1, true>::value : RowsOf<1, false>::value;
+        case 2: return f16 ? RowsOf<2, true>::value : RowsOf<2, false>::value;
+        case 4: return f16 ? RowsOf<4, true>::value : RowsOf<4, false>::value;
+        case 8: return f16 ? RowsOf<8, true>::value : RowsOf<8, false>::value;
+        case 16: return f16 ? RowsOf<16, true>::value : RowsOf<16, false>::value;
         default: return 0;
     }
 }
 
 cudaError_t prepare_iterate(int chunks, int smem) {
-    void* fn = pick(chunks);
-    if (!fn) return cudaErrorInvalidValue;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    for (int f = 0; f < 2; ++f) {
+        void* fn = pick(chunks, f == 1);
+        if (!fn) return cudaErrorInvalidValue;
+        const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
 }
 
 int max_coresident_iterate(int chunks, int smem, int* per_sm) {
@@ -915,9 +959,21 @@ cudaError_t launch_finalize(const IterArgs& a, long long kabs, cudaStream_t stre
     return cudaGetLastError();
 }
 
+// The mbarrier byte counts must equal what the TMA boxes deliver, and the ring
+// slots must hold them: a mismatch would leave copies in flight when the CTAs
+// exit, so the launch is refused instead.
+bool stage_geometry_ok(const IterArgs& a, int chunks, bool f16) {
+    const int eb = f16 ? 4 : 8;
+    return a.elem_bytes == eb && a.R == rows_per_stage(chunks, f16) && a.wbox >= 2 && a.wbox <= 256 &&
+           (a.wbox * eb) % 16 == 0 && a.nsub >= 1 && a.sub_bytes == a.R * a.wbox * eb &&
+           a.stage_bytes == a.sub_bytes * a.nsub && a.stage_bytes <= a.stage_stride &&
+           a.nstages >= 2 && a.nstages <= 8 && (!f16 || a.scales != nullptr);
+}
+
 cudaError_t launch_iterate(const CUtensorMap& tmap, const IterArgs& a, int chunks, int smem,
-                           cudaStream_t stream) {
-    void* fn = pick(chunks);
+                           cudaStream_t stream, bool f16) {
+    if (!stage_geometry_ok(a, chunks, f16)) return cudaErrorInvalidValue;
+    void* fn = pick(chunks, f16);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {const_cast<CUtensorMap*>(&tmap), const_cast<IterArgs*>(&a)};
     return cudaLaunchCooperativeKernel(fn, dim3(a.P), dim3(kIterThreads), args,

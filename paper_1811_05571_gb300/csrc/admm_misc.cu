@@ -1,5 +1,9 @@
 // Small device helpers of the setup path: complex128 -> complex64 packing into
 // the padded layout, a finite-value check, and in-place scaling.
+#include <algorithm>
+
+#include <cuda_fp16.h>
+
 #include "admm_internal.h"
 
 namespace admm {
@@ -34,6 +38,60 @@ __global__ void scale_kernel(float2* x, int64_t count, float alpha) {
     }
 }
 
+// max(|Re|, |Im|) of each 64-row group of H (as float bits: non-negative floats order like ints)
+__global__ void group_absmax_kernel(const float2* __restrict__ H, int64_t m, int64_t ld,
+                                    unsigned* __restrict__ gmax_bits) {
+    const int64_t groups = (m + 63) / 64;
+    for (int64_t g = blockIdx.y; g < groups; g += gridDim.y) {
+        const int64_t r0 = g * 64, r1 = min(m, r0 + 64);
+        float mx = 0.f;
+        for (int64_t r = r0; r < r1; ++r)
+            for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < ld;
+                 c += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+                const float2 v = H[r * ld + c];
+                mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+            }
+        for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(gmax_bits + g, __float_as_uint(mx));
+    }
+}
+
+// scale of a group: 2^(q - 14) where max = f 2^q, f in [0.5, 1) (so |H / scale| <= 2^14);
+// H16 = H / scale rounded to FP16; optionally the dequantised H16 * scale in FP32
+__global__ void quantize_kernel(const float2* __restrict__ H, int64_t m, int64_t ld,
+                                const unsigned* __restrict__ gmax_bits, __half2* __restrict__ H16,
+                                float* __restrict__ scales, float2* __restrict__ Hdeq) {
+    const int64_t total = m * ld;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = e / ld;
+        const float mx = __uint_as_float(gmax_bits[r >> 6]);
+        int q = 0;
+        frexpf(mx, &q);
+        const float scale = mx > 0.f ? ldexpf(1.0f, q - 14) : 1.0f;
+        if (e % ld == 0 && (r & 63) == 0) scales[r >> 6] = scale;
+        const float2 v = H[e];
+        const __half2 hv = __floats2half2_rn(v.x / scale, v.y / scale);
+        H16[e] = hv;
+        if (Hdeq) {
+            const float2 f = __half22float2(hv);
+            Hdeq[e] = make_float2(f.x * scale, f.y * scale);
+        }
+    }
+}
+
+// FP32 copy of the dequantised FP16 matrix (to rebuild its factors)
+__global__ void dequantize_kernel(const __half2* __restrict__ H16, int64_t m, int64_t ld,
+                                  const float* __restrict__ scales, float2* __restrict__ Hdeq) {
+    const int64_t total = m * ld;
+    for (int64_t e = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float scale = scales[(e / ld) >> 6];
+        const float2 f = __half22float2(H16[e]);
+        Hdeq[e] = make_float2(f.x * scale, f.y * scale);
+    }
+}
+
 int grid_for(int64_t count) {
     int64_t blocks = (count + 255) / 256;
     if (blocks > 4096) blocks = 4096;
@@ -51,6 +109,25 @@ cudaError_t launch_pack_c128(const double2* src, int64_t m, int64_t n, float2* d
 
 cudaError_t launch_finite_check(const float2* x, int64_t count, int* flag, cudaStream_t s) {
     finite_kernel<<<grid_for(count), 256, 0, s>>>(x, count, flag);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_quantize_f16(const float2* H, int64_t m, int64_t ld, unsigned* gmax_bits,
+                                void* H16, float* scales, float2* Hdeq, cudaStream_t s) {
+    const int64_t groups = (m + 63) / 64;
+    cudaError_t e = cudaMemsetAsync(gmax_bits, 0, groups * sizeof(unsigned), s);
+    if (e != cudaSuccess) return e;
+    const int chunks = static_cast<int>(std::min<int64_t>(64, (ld + 255) / 256));
+    const unsigned gy = static_cast<unsigned>(std::min<int64_t>(groups, 65535));
+    group_absmax_kernel<<<dim3(chunks, gy), 256, 0, s>>>(H, m, ld, gmax_bits);
+    quantize_kernel<<<grid_for(m * ld), 256, 0, s>>>(H, m, ld, gmax_bits, static_cast<__half2*>(H16),
+                                                    scales, Hdeq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dequantize_f16(const void* H16, int64_t m, int64_t ld, const float* scales,
+                                  float2* Hdeq, cudaStream_t s) {
+    dequantize_kernel<<<grid_for(m * ld), 256, 0, s>>>(static_cast<const __half2*>(H16), m, ld, scales, Hdeq);
     return cudaGetLastError();
 }
 

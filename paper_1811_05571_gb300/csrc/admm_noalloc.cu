@@ -227,6 +227,8 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
         a.sub_bytes = pl.sub_bytes;
         a.nsub = pl.nsub;
         a.wbox = pl.wbox;
+        a.elem_bytes = 8;
+        a.npitch = pl.npitch;
         a.mimax = pl.mimax;
         a.kpmax = pl.kpmax;
         a.off_ring = pl.off_ring;

@@ -58,15 +58,25 @@ class Solver:
         return B.admm_solve(self.h, int(max_iter), float(eps_abs), float(eps_rel), self.stream)
 
     # -- results -----------------------------------------------------------
+    def _order_after(self, out) -> None:
+        # the copy ran on the handle's stream: later work on torch's current
+        # stream (e.g. .cpu() of a device result) must wait for it
+        st = self.stream
+        if (st is not None and isinstance(st, self._torch.cuda.Stream)
+                and isinstance(out, self._torch.Tensor) and out.is_cuda):
+            self._torch.cuda.current_stream().wait_stream(st)
+
     def v(self, out=None):
         out = self._torch.empty(self.n, dtype=self._torch.complex64, device="cuda") if out is None else out
         B.admm_get_v(self.h, out, self.stream)
+        self._order_after(out)
         return out
 
     def u(self, out=None):
         out = (self._torch.empty((self.M, self.n), dtype=self._torch.complex64, device="cuda")
                if out is None else out)
         B.admm_get_u(self.h, out, self.stream)
+        self._order_after(out)
         return out
 
     def residuals(self, cap: int | None = None) -> np.ndarray:
@@ -102,6 +112,10 @@ class Solver:
 
     def set_option(self, option: int, value: int) -> None:
         B.admm_set_option(self.h, int(option), int(value))
+
+    def use_fp16(self, on: bool = True) -> None:
+        """Stream the FP16 copy of H (built on first use) or the complex64 H."""
+        B.admm_set_option(self.h, B.ADMM_OPT_H_FP16, 1 if on else 0)
 
     def trace(self, cap: int):
         return B.admm_get_trace(self.h, int(cap), self.stream)

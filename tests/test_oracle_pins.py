@@ -429,3 +429,42 @@ def test_stop_rule_and_residual_decay():
     assert np.sqrt(rec[0]) <= np.sqrt(nstack) * 1e-8 + 1e-6 * max(np.sqrt(rec[2]), np.sqrt(rec[3]))
     prev = r.hist[-2]
     assert not A.stop_test(prev, nstack, p.rho, 1e-8, 1e-6)
+
+
+# ----------------------------------------------------------------------------
+# the stored FP64 solution of the time-to-tolerance workload
+# ----------------------------------------------------------------------------
+
+def load_vstar():
+    """(header dict, v*) from tests/golden/vstar_gaussian_2048x16384_c8.txt."""
+    path = os.path.join(GOLDEN, "vstar_gaussian_2048x16384_c8.txt")
+    head, rows = {}, []
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#"):
+                parts = line[1:].split()
+                if parts and parts[0] in ("lambda", "rho", "iterations", "nonzeros"):
+                    head[parts[0]] = float(parts[1])
+                continue
+            k, re, im = line.split()
+            rows.append((int(k), float(re), float(im)))
+    v = np.zeros(16384, dtype=np.complex128)
+    for k, re, im in rows:
+        v[k] = re + 1j * im
+    return head, v
+
+
+def test_stored_solution_satisfies_the_lasso_optimality_conditions():
+    """v* minimises 1/2||Hv - g||^2 + lambda ||v||_1 (independent of ADMM):
+    with c = H^H (g - H v*), c_k = lambda v_k / |v_k| on the support and
+    |c_k| <= lambda elsewhere."""
+    head, v = load_vstar()
+    p = synth.gaussian_problem(2048, 16384, 128, seed=5)
+    assert head["lambda"] == p.lam and head["rho"] == p.rho
+    c = p.H.conj().T @ (p.g - p.H @ v)
+    sup = v != 0
+    assert sup.sum() == head["nonzeros"]
+    assert np.max(np.abs(c[sup] - p.lam * v[sup] / np.abs(v[sup]))) <= 1e-9 * p.lam
+    assert np.max(np.abs(c[~sup])) <= p.lam * (1 + 1e-9)
+    # the planted scene is recovered on its support
+    assert set(np.flatnonzero(p.u_true)) <= set(np.flatnonzero(v))
