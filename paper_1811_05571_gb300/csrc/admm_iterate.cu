@@ -168,7 +168,8 @@ __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* f
     const uint64_t pol_first = policy_evict_first();
     int per_pass = 0;
     for (int i = 0; i < a.M; ++i) per_pass += (a.row_off[i + 1] - a.row_off[i] + a.R - 1) / a.R;
-    int stage = 0;
+    int stage = 0, slot = 0;   // stages issued; ring slot of the next one
+    uint32_t pphase = 0;        // fill parity of that slot
     bool ok = true;
     for (int it = 0; it < a.iters && ok; ++it) {
         for (int pass = 0; pass < 2 && ok; ++pass) {
@@ -180,8 +181,7 @@ __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* f
                 for (int bb = 0; bb < nb; ++bb, ++pos) {
                     const int b = pass == 0 ? bb : nb - 1 - bb;
                     const int y = r0 + b * a.R;
-                    const int slot = stage % a.nstages;
-                    const uint32_t parity = ((stage / a.nstages) & 1) ^ 1;
+                    const uint32_t parity = pphase ^ 1u;
                     if (!producer_wait(&empty[slot], parity, a, misc)) {
                         ok = false;
                         break;
@@ -198,6 +198,10 @@ __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* f
                                              c_beg + sb * a.wbox, y, &full[slot], pol_first);
                     }
                     ++stage;
+                    if (++slot == a.nstages) {
+                        slot = 0;
+                        pphase ^= 1u;
+                    }
                     *reinterpret_cast<volatile int*>(&misc->issued) = stage;
                 }
             }
@@ -271,8 +275,10 @@ struct Consumer {
     uint32_t valid;       // bit k: pair lane + 32k lies in this slab
     uint32_t owned;       // bit 2k+h: column h of pair lane + 32k is owned by this CTA
     uint64_t jl;          // 4 bits per chunk: block of column 0 (bits 0-1), column 1 (bits 2-3)
-    int soff[CH];         // byte offset of pair lane + 32k inside a stage, row 0
-    int stage;            // stages consumed
+    int soff[CH];         // byte offset of pair lane + 32k inside a stage, row 0 (pairs outside
+                          // the slab read pair 0: finite data, multiplied by a zero z)
+    int slot;             // ring slot of the next stage
+    uint32_t phase;       // parity of that slot's current fill
 
     __device__ Consumer(const IterArgs& args, unsigned char* sm, Misc* mi, uint64_t* f,
                         uint64_t* e, const unsigned char* rg)
@@ -288,7 +294,8 @@ struct Consumer {
         own0 = a.cta_own0[cta];
         own1 = a.cta_own1[cta];
         npmax = a.npitch;
-        stage = 0;
+        slot = 0;
+        phase = 0;
         valid = 0;
         owned = 0;
         jl = 0;
@@ -297,7 +304,7 @@ struct Consumer {
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
             const int p = lane + 32 * k;
-            const int rel = 2 * p + shift;
+            const int rel = p < npairs ? 2 * p + shift : shift;
             const int sb = rel / a.wbox;
             soff[k] = sb * a.sub_bytes + (rel - sb * a.wbox) * (F16 ? 4 : 8);
             if (p < npairs) {
@@ -347,19 +354,20 @@ struct Consumer {
 
     // wait for the next stage; after a local failure, waits are skipped so that
     // every warp still reaches the same named barriers
-    __device__ __forceinline__ const unsigned char* acquire_stage(int& slot) {
-        slot = stage % a.nstages;
-        const uint32_t parity = (stage / a.nstages) & 1;
+    __device__ __forceinline__ const unsigned char* acquire_stage() {
         if (!*reinterpret_cast<volatile int*>(&misc->failed)) {
-            if (!mbar_wait_bounded(&full[slot], parity, a.status, a.timeout_ns))
+            if (!mbar_wait_bounded(&full[slot], phase, a.status, a.timeout_ns))
                 *reinterpret_cast<volatile int*>(&misc->failed) = 1;
         }
         return ring + static_cast<size_t>(slot) * a.stage_stride;
     }
-    __device__ __forceinline__ void release_stage(int slot) {
+    __device__ __forceinline__ void release_stage() {
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[slot]);
-        ++stage;
+        if (++slot == a.nstages) {
+            slot = 0;
+            phase ^= 1u;
+        }
     }
 
     // z_i for the lane's pairs, zero in columns this CTA does not own
@@ -418,24 +426,22 @@ struct Consumer {
 #pragma unroll
                 for (int wi = 0; wi < kWin; ++wi) {
                     if (b0 + wi < nb) {
-                        int slot;
-                        const unsigned char* buf = acquire_stage(slot);
+                        const unsigned char* buf = acquire_stage();
 #pragma unroll
                         for (int q = 0; q < kRPW; ++q) {
                             const int v = wi * kRPW + q;
                             const unsigned char* rowp = buf + (warp + kConsumerWarps * q) * rowpitch;
 #pragma unroll
                             for (int k = 0; k < CH; ++k) {
-                                if (is_valid(k)) {
-                                    const float4 h = load_pair(rowp, k);
-                                    accA[v] = fma2(lo2(h), zr0[k], accA[v]);
-                                    accB[v] = fma2(lo2(h), zi0[k], accB[v]);
-                                    accA[v] = fma2(hi2(h), zr1[k], accA[v]);
-                                    accB[v] = fma2(hi2(h), zi1[k], accB[v]);
-                                }
+                                // pairs outside the slab have z = 0
+                                const float4 h = load_pair(rowp, k);
+                                accA[v] = fma2(lo2(h), zr0[k], accA[v]);
+                                accB[v] = fma2(lo2(h), zi0[k], accB[v]);
+                                accA[v] = fma2(hi2(h), zr1[k], accA[v]);
+                                accB[v] = fma2(hi2(h), zi1[k], accB[v]);
                             }
                         }
-                        release_stage(slot);
+                        release_stage();
                     }
                 }
                 // h z = (sum h.re z.re - h.im z.im, sum h.im z.re + h.re z.im)
@@ -475,8 +481,7 @@ struct Consumer {
             const int nb = (r1 - r0 + kR - 1) / kR;
             for (int b = 0; b < nb; ++b) {
                 const int y = r0 + b * kR;
-                int slot;
-                const unsigned char* buf = acquire_stage(slot);
+                const unsigned char* buf = acquire_stage();
 #pragma unroll
                 for (int q = 0; q < kRPW; ++q) {
                     const int row = y + warp + kConsumerWarps * q;
@@ -485,13 +490,12 @@ struct Consumer {
                         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
                         for (int k = 0; k < CH; ++k) {
-                            if (is_valid(k)) {
-                                const float2 z0 = jl_of(k, 0) == jj ? lo2(z[k]) : make_float2(0.f, 0.f);
-                                const float2 z1 = jl_of(k, 1) == jj ? hi2(z[k]) : make_float2(0.f, 0.f);
-                                const float4 h = load_pair(rowp, k);
-                                cfma(acc, lo2(h), z0);
-                                cfma(acc, hi2(h), z1);
-                            }
+                            // pairs outside the slab have z = 0
+                            const float2 z0 = jl_of(k, 0) == jj ? lo2(z[k]) : make_float2(0.f, 0.f);
+                            const float2 z1 = jl_of(k, 1) == jj ? hi2(z[k]) : make_float2(0.f, 0.f);
+                            const float4 h = load_pair(rowp, k);
+                            cfma(acc, lo2(h), z0);
+                            cfma(acc, hi2(h), z1);
                         }
                         acc = warp_sum(acc);
                         if (F16) {
@@ -502,7 +506,7 @@ struct Consumer {
                             stcg2(a.part + (static_cast<size_t>(jlo + jj) * a.m + row) * a.P + cta, acc);
                     }
                 }
-                release_stage(slot);
+                release_stage();
             }
         }
     }
@@ -671,8 +675,7 @@ struct Consumer {
             const int nb = (mi + kR - 1) / kR;
             for (int b = nb - 1; b >= 0; --b) {
                 const int y = r0 + b * kR;
-                int slot;
-                const unsigned char* buf = acquire_stage(slot);
+                const unsigned char* buf = acquire_stage();
 #pragma unroll
                 for (int q = 0; q < kRPW; ++q) {
                     const int rl = warp + kConsumerWarps * q;
@@ -683,13 +686,12 @@ struct Consumer {
                         const float2 wre = make_float2(wv.x, wv.x), wim = make_float2(wv.y, wv.y);
 #pragma unroll
                         for (int k = 0; k < CH; ++k) {
-                            if (is_valid(k)) {
-                                const float4 h = load_pair(rowp, k);
-                                aA0[k] = fma2(lo2(h), wre, aA0[k]);
-                                aB0[k] = fma2(lo2(h), wim, aB0[k]);
-                                aA1[k] = fma2(hi2(h), wre, aA1[k]);
-                                aB1[k] = fma2(hi2(h), wim, aB1[k]);
-                            }
+                            // sums of pairs outside the slab are never stored
+                            const float4 h = load_pair(rowp, k);
+                            aA0[k] = fma2(lo2(h), wre, aA0[k]);
+                            aB0[k] = fma2(lo2(h), wim, aB0[k]);
+                            aA1[k] = fma2(hi2(h), wre, aA1[k]);
+                            aB1[k] = fma2(hi2(h), wim, aB1[k]);
                         }
                     } else {
                         float2 wv[kMaxBlocksPerSlab];
@@ -699,18 +701,16 @@ struct Consumer {
                                                      : make_float2(0.f, 0.f);
 #pragma unroll
                         for (int k = 0; k < CH; ++k) {
-                            if (is_valid(k)) {
-                                const float4 h = load_pair(rowp, k);
-                                const float2 w0 = wv[jl_of(k, 0)], w1 = wv[jl_of(k, 1)];
-                                aA0[k] = fma2(lo2(h), make_float2(w0.x, w0.x), aA0[k]);
-                                aB0[k] = fma2(lo2(h), make_float2(w0.y, w0.y), aB0[k]);
-                                aA1[k] = fma2(hi2(h), make_float2(w1.x, w1.x), aA1[k]);
-                                aB1[k] = fma2(hi2(h), make_float2(w1.y, w1.y), aB1[k]);
-                            }
+                            const float4 h = load_pair(rowp, k);
+                            const float2 w0 = wv[jl_of(k, 0)], w1 = wv[jl_of(k, 1)];
+                            aA0[k] = fma2(lo2(h), make_float2(w0.x, w0.x), aA0[k]);
+                            aB0[k] = fma2(lo2(h), make_float2(w0.y, w0.y), aB0[k]);
+                            aA1[k] = fma2(hi2(h), make_float2(w1.x, w1.x), aA1[k]);
+                            aB1[k] = fma2(hi2(h), make_float2(w1.y, w1.y), aB1[k]);
                         }
                     }
                 }
-                release_stage(slot);
+                release_stage();
             }
             // conj(h) w = (h.re w.re + h.im w.im, h.re w.im - h.im w.re); sum over warps
             float4* rb = red + static_cast<size_t>(a.red_single ? 0 : (bi & 1)) * kConsumerWarps * npmax;
