@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12,
                     help="iterations per split in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 8192x131072 mixed-precision workload")
     ap.add_argument("--no-time-to-tol", action="store_true",
                     help="skip the time-to-1e-4 comparison of FP16+polish against plain complex64")
     ap.add_argument("--trace", type=int, default=0,
@@ -351,6 +353,82 @@ def time_to_tolerance(pkg, stream, dev, barrier) -> dict:
     return out
 
 
+def mixed_precision_large(pkg, stream, dev, barrier, peaks) -> dict:
+    """The 8192 x 131072 workload (16 row blocks of 512 rows, consensus): per
+    iteration in complex64 and in FP16 H, and 300 iterations as 280 FP16 + 20
+    complex64 polish against 300 complex64, each timed with CUDA events on the
+    launching stream.  H (8.6 GB complex64) is far larger than L2."""
+    import torch
+    import synth
+    c = synth.CONFIG3
+    H, g, _, lam = synth.gaussian_problem_device(c["m"], c["n"], c["nnz"], c["seed"], device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        s = pkg.Solver(H, g, c["row_blocks"], 1, lam, c["rho"], stream=stream)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    del H, g
+    torch.cuda.empty_cache()
+    t0 = time.perf_counter()
+    s.use_fp16(True)
+    torch.cuda.synchronize()
+    setup16_s = time.perf_counter() - t0
+    out = {"workload": f"gaussian {c['m']}x{c['n']} CN(0,1/{c['m']}), {c['nnz']} nonzeros, 30 dB, "
+                       f"seed {c['seed']} (device generator), consensus {c['row_blocks']}x1, "
+                       f"lambda 0.05 max|H^H g|, rho 1",
+           "setup_ms": setup_s * 1e3, "fp16_setup_ms": setup16_s * 1e3}
+
+    def per_iter(fp16: bool, k: int = 20) -> float:
+        s.use_fp16(fp16)
+        for _ in range(3):
+            s.iterate(1)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(k):
+            s.iterate(1)
+        b.record(stream)
+        barrier()
+        return a.elapsed_time(b) / k * 1e3
+
+    info = s.info()
+    state = (2 * c["row_blocks"] + 2) * c["n"] * 8
+    for name, fp16, hb in (("c64", False, info["h_bytes"]), ("fp16_h", True, info["h16_bytes"])):
+        us = per_iter(fp16)
+        alg = 2 * hb + info["factor_bytes"] + state
+        out[name] = {"us_per_iter": us, "alg_bytes_per_iter": alg, "gbs": alg / us / 1e3,
+                     "frac": alg / us / 1e3 / peaks["hbm_gbs"]}
+
+    def schedule(k16: int, k32: int) -> float:
+        s.reset()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        if k16:
+            s.use_fp16(True)
+            s.iterate(k16)
+        s.use_fp16(False)
+        s.iterate(k32)
+        b.record(stream)
+        barrier()
+        return a.elapsed_time(b)
+
+    ms_chosen = schedule(c["fp16_iters"], c["polish_iters"])
+    rec_chosen = s.residuals(1)[0].tolist()
+    ms_plain = schedule(0, c["fp16_iters"] + c["polish_iters"])
+    rec_plain = s.residuals(1)[0].tolist()
+    if s.status() != 0:
+        raise RuntimeError("device status after the mixed-precision runs")
+    s.close()
+    out["schedule"] = {"chosen": {"fp16_iters": c["fp16_iters"], "polish_iters": c["polish_iters"],
+                                  "ms": ms_chosen, "final_rp2_rd2": rec_chosen[:2]},
+                       "plain": {"iters": c["fp16_iters"] + c["polish_iters"], "ms": ms_plain,
+                                 "final_rp2_rd2": rec_plain[:2]},
+                       "speedup": ms_plain / ms_chosen}
+    return out
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -478,6 +556,9 @@ def run_ours(args) -> None:
     ttt = None
     if not args.no_time_to_tol:
         ttt = time_to_tolerance(pkg, stream, dev, barrier)
+    large = None
+    if not args.no_large:
+        large = mixed_precision_large(pkg, stream, dev, barrier, peaks=load_peaks())
 
     phases = None
     if args.trace > 0:
@@ -523,6 +604,7 @@ def run_ours(args) -> None:
     if traffic is not None:
         for name in per_split:
             per_split[name]["dram_bytes_per_launch"] = traffic.get(name)
+            per_split[name]["fp16_h"]["dram_bytes_per_launch"] = traffic.get(name + "_fp16")
     value = world * len(SPLITS) * K / total_s
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
@@ -536,7 +618,8 @@ def run_ours(args) -> None:
                    "l2": "inputs larger than L2 (H 377 MB per split vs 129 MB L2), no flush"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": (sum(traffic.values()) / len(traffic)) if traffic else None,
+                     "traffic": (sum(traffic[f"{M}x{N}"] for M, N in SPLITS) / len(SPLITS))
+                                if traffic and all(f"{M}x{N}" in traffic for M, N in SPLITS) else None,
                      "peak_source": peaks["source"], "kernel": "admm::iterate_kernel"},
         "e2e": {"value": world * len(SPLITS) * K / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": len(SPLITS) * M_ROWS * 8,
@@ -549,6 +632,8 @@ def run_ours(args) -> None:
         line["cpu_baseline"] = cpu
     if ttt is not None:
         line["time_to_tol"] = ttt
+    if large is not None:
+        line["mixed_precision_large"] = large
     if phases is not None:
         line["phases"] = phases
     for s in solvers:

@@ -292,15 +292,19 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     pl.R16 = rows_per_stage(pl.chunks, true);
     pl.sub_bytes = pl.R * pl.wbox * 8;
     pl.stage_bytes = pl.sub_bytes * pl.nsub;
-    pl.stage_stride = round_up(std::max(pl.stage_bytes, pl.R16 * pl.wbox16 * 4 * pl.nsub16), 128);
+    // one ring region, cut into slots of either mode's stage size
+    pl.stage_stride = round_up(pl.stage_bytes, 128);
+    pl.stage_stride16 = round_up(pl.R16 * pl.wbox16 * 4 * pl.nsub16, 128);
     pl.nstages = std::min(8, (smem_limit - fixed) / pl.stage_stride);
-    if (pl.nstages < 2) {
+    pl.nstages16 = std::min(8, (smem_limit - fixed) / pl.stage_stride16);
+    if (pl.nstages < 2 || pl.nstages16 < 2) {
         *why = "shared memory too small for two pipeline stages";
         return ADMM_EUNSUPPORTED;
     }
+    pl.ring_bytes = std::max(pl.stage_stride * pl.nstages, pl.stage_stride16 * pl.nstages16);
     int off = 0;
     pl.off_ring = off;
-    off += pl.stage_stride * pl.nstages;
+    off += pl.ring_bytes;
     off = round_up(off, 128);
     pl.off_full = off;
     off += 8 * 8;
@@ -555,8 +559,8 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.P = pl.P;
     const bool f16 = h->use_f16 != 0;
     a.R = f16 ? pl.R16 : pl.R;
-    a.nstages = pl.nstages;
-    a.stage_stride = pl.stage_stride;
+    a.nstages = f16 ? pl.nstages16 : pl.nstages;
+    a.stage_stride = f16 ? pl.stage_stride16 : pl.stage_stride;
     a.nsub = f16 ? pl.nsub16 : pl.nsub;
     a.wbox = f16 ? pl.wbox16 : pl.wbox;
     a.elem_bytes = f16 ? 4 : 8;
@@ -1046,7 +1050,7 @@ int admm_get_info(const admm_t* h, admm_info_t* info) {
     info->iterations = h->k;
     info->ctas = pl.P;
     info->rows_per_stage = h->use_f16 ? pl.R16 : pl.R;
-    info->stages = pl.nstages;
+    info->stages = h->use_f16 ? pl.nstages16 : pl.nstages;
     info->slab_cols = pl.wmax;
     info->smem_bytes = pl.smem;
     info->num_sms = h->num_sms;

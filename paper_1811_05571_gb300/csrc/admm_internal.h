@@ -43,6 +43,9 @@ struct Plan {
     bool ws_all = false;  // the whole w (m x njs) fits in shared memory
     int ws_rows = 0;      // rows of the shared w staging buffer
     int R16 = 0;          // FP16 stream: rows per stage
+    int nstages16 = 0;    // FP16 stream: pipeline depth
+    int stage_stride16 = 0;  // FP16 stream: ring slot size
+    int ring_bytes = 0;   // shared memory of the ring (either mode's slots fit)
     int wbox16 = 0;       // FP16 stream: TMA box width (columns, multiple of 4)
     int nsub16 = 0;       // FP16 stream: boxes per slab row
     int npitch = 0;       // pair pitch of the per-pair shared buffers

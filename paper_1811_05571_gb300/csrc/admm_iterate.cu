@@ -249,8 +249,8 @@ __device__ void finalize_record(const IterArgs& a, long long kabs, int lane, boo
 // ---------------------------------------------------------------------------
 
 // rows of H per pipeline stage for a slab of CH 32-pair chunks (about 32 KB of
-// complex64; FP16 stages take twice the rows, up to 64, to keep the bytes in
-// flight per SM)
+// complex64; FP16 stages take twice the rows, up to 64, to keep the bytes per
+// stage: fewer, larger stages beat a deeper ring of small ones)
 template <int CH, bool F16>
 struct RowsOf {
     static constexpr int base = CH >= 8 ? 8 : 64 / CH;

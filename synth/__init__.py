@@ -19,4 +19,6 @@ from .workloads import (  # noqa: F401
     round_to_c64,
     CONFIG1,
     CONFIG2,
+    CONFIG3,
+    gaussian_problem_device,
 )

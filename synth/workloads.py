@@ -261,3 +261,30 @@ CONFIG1 = dict(kind="gaussian", m=256, n=4096, nnz=16, seed=0, row_blocks=4, col
                lam_frac=0.05, rho=1.0, iters=300)
 CONFIG2 = dict(kind="cra", m=1440, n=32768, splits=((8, 1), (1, 8), (4, 4)),
                matrix_seed=1, scene_seed=2, lam_frac=0.05, rho_col_blocks=8, iters=300)
+CONFIG3 = dict(kind="gaussian_device", m=8192, n=131072, nnz=400, seed=3, row_blocks=16,
+               col_blocks=1, lam_frac=0.05, rho=1.0, fp16_iters=280, polish_iters=20)
+
+
+def gaussian_problem_device(m: int, n: int, nnz: int, seed: int, snr_db: float = 30.0,
+                            lam_frac: float = 0.05, device="cuda"):
+    """Gaussian instance generated on the GPU (for sizes the host generator is
+    too slow for): H ~ CN(0, 1/m) complex64, ``nnz`` unit-magnitude entries of
+    uniform phase at distinct uniform indices, complex Gaussian noise scaled to
+    exactly ``snr_db``, lambda = lam_frac * max|H^H g| (complex64 products).
+
+    Draws come from one torch.Generator on ``device`` seeded with ``seed``, in
+    the order H, support, phases, w.  Returns (H, g, u_true, lam) with the
+    tensors on ``device``."""
+    import torch
+    gen = torch.Generator(device=device).manual_seed(int(seed))
+    H = torch.view_as_complex(torch.randn(m, n, 2, generator=gen, device=device).mul_((0.5 / m) ** 0.5))
+    u = torch.zeros(n, dtype=torch.complex64, device=device)
+    idx = torch.randperm(n, generator=gen, device=device)[:nnz]
+    phase = torch.rand(nnz, generator=gen, device=device) * (2.0 * np.pi)
+    u[idx] = torch.polar(torch.ones_like(phase), phase)
+    clean = H @ u
+    w = torch.view_as_complex(torch.randn(m, 2, generator=gen, device=device).contiguous())
+    w = w * (clean.norm() / w.norm() / 10.0 ** (snr_db / 20.0))
+    g = clean + w
+    lam = float(lam_frac * (H.conj().T @ g).abs().max())
+    return H, g, u, lam
