@@ -146,6 +146,17 @@ const char* admm_last_error(const admm_t* h);
  * ADMM_EINVAL unless 1 <= parts <= total and offsets != NULL. */
 int admm_partition(int64_t total, int32_t parts, int64_t* offsets);
 
+/* Elements of C^1 one node exchanges per iteration when the split runs on
+ * separate nodes (Section IV, Table I), for m measurements (N_m), n unknowns
+ * (N_p), M = row_blocks and N = col_blocks: out[0] = 2 n (row split: the
+ * replica out, the consensus image back), out[1] = N m (column split: the
+ * estimated data of every block), out[2] = N m / M + 2 n / N (both; may be
+ * fractional).  All three are written whatever the split, so callers can
+ * compare them (Section IV-B).  Host only, no GPU needed.  ADMM_EINVAL unless
+ * m, n >= 1, 1 <= row_blocks, 1 <= col_blocks and out != NULL.  This build
+ * runs every block on one GPU and exchanges nothing between nodes. */
+int admm_comm_elements(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks, double* out);
+
 /* Plan of the persistent iteration kernel for an m x n problem split into
  * row_blocks x col_blocks on a GPU with `num_sms` SMs and `smem_limit` bytes of
  * opt-in shared memory per block.  Host only, no GPU needed.  When
@@ -170,9 +181,14 @@ int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks,
  * (I + H_b H_b^H / rho)^{-1} of the inversion lemma, Eq. (inversion_lemma),
  * (inversion_lemma2) and (inversion_lemma3).  The iteration state starts at
  * v = s = u = 0 with zero estimated data.
- * Requires 1 <= row_blocks <= m, 1 <= col_blocks <= n,
- * row_blocks * col_blocks <= 256, and every block with fewer rows than
- * columns (the lemma branch); a tall block returns ADMM_EUNSUPPORTED.
+ * Requires 1 <= row_blocks <= m, 1 <= col_blocks <= n and
+ * row_blocks * col_blocks <= 256.  A block with at least as many rows as
+ * columns, where the paper inverts the n_b x n_b matrix H_b^H H_b + rho I
+ * directly (Section III-B), uses the same m_b x m_b factor: the identity
+ * (H_b^H H_b + rho I)^{-1} (H_b^H x + rho z) = z + H_b^H K_b^{-1} (x - H_b z)
+ * holds for every shape, so the result is the direct branch's; the cost is
+ * m_b^2 cached factor elements per block instead of n_b^2 (ADMM_ENOMEM or
+ * ADMM_EUNSUPPORTED when they do not fit).
  * Synchronises `stream`.  On success *out receives the handle; on failure
  * *out is NULL and admm_last_error(NULL) describes the error. */
 int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,

@@ -14,7 +14,7 @@ from ._binding import (  # noqa: F401
     ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS,
     ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ABI_VERSION,
     AdmmError, load, library_path,
-    admm_abi_version, admm_strerror, admm_partition, admm_plan, admm_setup, admm_iterate,
+    admm_abi_version, admm_strerror, admm_partition, admm_comm_elements, admm_plan, admm_setup, admm_iterate,
     admm_solve, admm_get_v, admm_get_u, admm_get_residuals, admm_set_g, admm_set_lambda,
     admm_set_rho, admm_reset, admm_get_state, admm_set_state, admm_get_info, admm_set_option,
     admm_get_trace, admm_status, admm_destroy, admm_solve_small_noalloc,

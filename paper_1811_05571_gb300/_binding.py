@@ -61,6 +61,7 @@ SIGNATURES = {
     "admm_strerror": (ctypes.c_char_p, [c_int32]),
     "admm_last_error": (ctypes.c_char_p, [c_void_p]),
     "admm_partition": (c_int32, [c_int64, c_int32, ctypes.POINTER(c_int64)]),
+    "admm_comm_elements": (c_int32, [c_int64, c_int64, c_int32, c_int32, ctypes.POINTER(c_double)]),
     "admm_plan": (c_int32, [c_int64, c_int64, c_int32, c_int32, c_int32, c_int32,
                             ctypes.POINTER(AdmmPlan), ctypes.POINTER(c_int32)]),
     "admm_setup": (c_int32, [ctypes.POINTER(c_void_p), c_void_p, c_void_p, c_int64, c_int64,
@@ -160,6 +161,12 @@ def admm_abi_version() -> int:
 
 def admm_strerror(status: int) -> str:
     return load().admm_strerror(status).decode()
+
+
+def admm_comm_elements(m: int, n: int, row_blocks: int, col_blocks: int) -> dict:
+    out = (c_double * 3)()
+    _check(load().admm_comm_elements(m, n, row_blocks, col_blocks, out))
+    return {"consensus": out[0], "sectioning": out[1], "cs": out[2]}
 
 
 def admm_partition(total: int, parts: int) -> list[int]:

@@ -711,6 +711,16 @@ int admm_partition(int64_t total, int32_t parts, int64_t* offsets) {
     return ADMM_OK;
 }
 
+int admm_comm_elements(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks, double* out) {
+    if (!out || m < 1 || n < 1 || row_blocks < 1 || col_blocks < 1) return ADMM_EINVAL;
+    const double Nm = static_cast<double>(m), Np = static_cast<double>(n);
+    const double M = row_blocks, N = col_blocks;
+    out[0] = 2 * Np;
+    out[1] = N * Nm;
+    out[2] = N * Nm / M + 2 * Np / N;
+    return ADMM_OK;
+}
+
 int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks, int32_t num_sms,
               int32_t smem_limit, admm_plan_t* out, int32_t* cta_cols) {
     if (!out) return ADMM_EINVAL;
@@ -755,13 +765,6 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     std::vector<int> ro, co;
     admm::balanced_offsets(m, row_blocks, ro);
     admm::balanced_offsets(n, col_blocks, co);
-    for (int i = 0; i < row_blocks; ++i)
-        for (int j = 0; j < col_blocks; ++j)
-            if (ro[i + 1] - ro[i] >= co[j + 1] - co[j])
-                return fail(nullptr, ADMM_EUNSUPPORTED,
-                            "block (%d,%d) has %d rows >= %d columns: the direct (non-lemma) u-step "
-                            "is not implemented on the GPU",
-                            i, j, ro[i + 1] - ro[i], co[j + 1] - co[j]);
 
     admm_t* h = new admm_t();
     h->m = m;

@@ -80,10 +80,6 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
     std::vector<int> ro, co;
     admm::balanced_offsets(m, row_blocks, ro);
     admm::balanced_offsets(n, col_blocks, co);
-    for (int i = 0; i < row_blocks; ++i)
-        for (int j = 0; j < col_blocks; ++j)
-            if (ro[i + 1] - ro[i] >= co[j + 1] - co[j])
-                return noalloc_fail(ADMM_EUNSUPPORTED, "every block needs fewer rows than columns");
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int dev = 0, sms = 0, smem_optin = 0;

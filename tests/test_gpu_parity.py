@@ -244,13 +244,23 @@ def test_complex128_and_host_inputs_match_complex64_device_inputs():
     assert torch.equal(a.v(), b.v())
 
 
-def test_tall_block_is_rejected():
-    import paper_1811_05571_gb300 as P
-    H = torch.zeros((64, 64), dtype=torch.complex64, device="cuda")
-    g = torch.zeros(64, dtype=torch.complex64, device="cuda")
-    with pytest.raises(P.AdmmError) as e:
-        P.Solver(H, g, 1, 2, 0.1, 1.0)
-    assert e.value.status == P.ADMM_EUNSUPPORTED
+@pytest.mark.parametrize("m,n,M,N,iters", [
+    (300, 1000, 1, 5, 120),     # sectioning, 300 x 200 blocks
+    (1200, 512, 2, 1, 120),     # overdetermined consensus, 600 x 512 blocks
+    (400, 600, 2, 4, 100),      # C&S, 200 x 150 blocks
+    (64, 64, 1, 1, 100),        # square: the direct branch at m_b = n_b
+])
+def test_tall_blocks_match_the_direct_branch(m, n, M, N, iters):
+    """Blocks with m_b >= n_b: the oracle inverts H_b^H H_b + rho I (the
+    direct branch); the GPU applies the same operator through K_b."""
+    rows = A.balanced_blocks(m, M)
+    cols = A.balanced_blocks(n, N)
+    assert all(not A.lemma_applies(r1 - r0, c1 - c0) for r0, r1 in rows for c0, c1 in cols)
+    p = synth.gaussian_problem(m, n, max(2, n // 32), seed=m + n + M + N)
+    rho = _rho_cols(p, N)
+    ref = oracle_run(p, M, N, iters, rho=rho)
+    s = gpu_run(p, M, N, iters, rho=rho)
+    compare_all(s, ref, M, N)
 
 
 def test_nonfinite_input_is_rejected():
