@@ -316,6 +316,77 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
                              int32_t row_blocks, int32_t col_blocks, double lambda, double rho,
                              int32_t iters, void* v_out, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Batched shared-H solver.  `batch` independent scenes g_b (b = 0..batch-1)
+ * with one sensing matrix H are iterated together under the same split: each
+ * scene runs exactly the iteration of admm_iterate (Sections III-A..C, with
+ * its own lambda_b), on the matrix the FP16 storage of H encodes
+ * (ADMM_OPT_H_FP16: one power-of-two scale per 64-row group).  The products
+ * H_ij z_j^i, K_ij^{-1} r_ij and H_ij^H w_ij of all scenes are GEMMs on the
+ * tensor cores (tcgen05.mma, FP16 operands, FP32 accumulation): every
+ * right-hand side is split into FP16 hi + lo parts after a power-of-two scale
+ * per scene and block, so the products carry about 22 significant bits, and
+ * the factors K^{-1} are split the same way.  The paper processes one scene;
+ * the batch is this library's extension for many scenes with one H.
+ * Vectors are scene-major complex64: G and Y batch x m, V and X batch x n.
+ * ------------------------------------------------------------------------- */
+typedef struct admm_batch admm_batch_t;
+
+typedef struct admm_batch_info {
+    int64_t m, n;
+    int32_t batch, row_blocks, col_blocks;
+    int32_t splits;           /* K splits of the forward product GEMM */
+    int64_t iterations;
+    double tensor_flops;      /* tensor-core FLOPs issued per iteration (tile padding included) */
+    double method_flops;      /* 8 real FLOPs per complex multiply-add of the method, all scenes */
+    double state_bytes;       /* bytes of state and packed operands moved per iteration */
+} admm_batch_info_t;
+
+/* Create a batched solver.  H (m x n, host or device, element type h_dtype)
+ * is copied; lambda holds `batch` weights (host memory).  Requires m and every
+ * block start to be multiples of 4 (16-byte TMA rows of the FP16 copy and of
+ * its transpose), 1 <= batch <= 4096, and the shape limits of admm_setup.
+ * The state starts at zero and G at zero (admm_batch_set_g).  Synchronises
+ * `stream`.  On failure *out is NULL and admm_batch_last_error(NULL) says why. */
+int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, int32_t row_blocks,
+                     int32_t col_blocks, int32_t batch, const double* lambda, double rho, int32_t h_dtype,
+                     void* stream);
+
+/* Copy the batch x m measurements (complex64, host or device).  Synchronises. */
+int admm_batch_set_g(admm_batch_t* h, const void* G, void* stream);
+
+/* Run `iters` iterations for every scene (one CUDA graph launch each; the
+ * graph is captured on the first call).  Asynchronous on `stream`. */
+int admm_batch_iterate(admm_batch_t* h, int32_t iters, void* stream);
+
+/* Copy the batch x n images v (complex64) into V (host or device). */
+int admm_batch_get_v(admm_batch_t* h, void* V, void* stream);
+
+/* ||r_p||^2 and ||r_d||^2 of the last iteration per scene (2 * batch doubles,
+ * host), as in admm_get_residuals; synchronises and returns the device status. */
+int admm_batch_get_residuals(admm_batch_t* h, double* out, void* stream);
+
+/* Zero the state (v, s, estimated data) and the iteration count.  Synchronises. */
+int admm_batch_reset(admm_batch_t* h, void* stream);
+
+/* Y_b = Hq X_b for every scene with the tensor-core forward product, where Hq
+ * is the matrix the FP16 storage encodes (the products of Eq. g_columns and of
+ * the u-step); X is batch x n, Y batch x m.  Synchronises. */
+int admm_batch_forward(admm_batch_t* h, const void* X, void* Y, void* stream);
+
+/* X_b = Hq^H Y_b for every scene (the adjoint product of the u-step).  Synchronises. */
+int admm_batch_adjoint(admm_batch_t* h, const void* Y, void* X, void* stream);
+
+/* Synchronise `stream` and return the sticky device status. */
+int admm_batch_status(admm_batch_t* h, void* stream);
+
+int admm_batch_get_info(const admm_batch_t* h, admm_batch_info_t* info);
+
+/* Last failure on `h` (or of the last failed admm_batch_setup when h is NULL). */
+const char* admm_batch_last_error(const admm_batch_t* h);
+
+void admm_batch_destroy(admm_batch_t* h);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,5 +18,9 @@ from ._binding import (  # noqa: F401
     admm_solve, admm_get_v, admm_get_u, admm_get_residuals, admm_set_g, admm_set_lambda,
     admm_set_rho, admm_reset, admm_get_state, admm_set_state, admm_get_info, admm_set_option,
     admm_get_trace, admm_status, admm_destroy, admm_solve_small_noalloc,
+    admm_batch_setup, admm_batch_set_g, admm_batch_iterate, admm_batch_get_v, admm_batch_get_residuals,
+    admm_batch_reset, admm_batch_forward, admm_batch_adjoint, admm_batch_status, admm_batch_get_info,
+    admm_batch_destroy,
 )
+from .solver import BatchSolver  # noqa: F401
 from .solver import Solver  # noqa: F401

@@ -49,6 +49,15 @@ class AdmmPlan(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class AdmmBatchInfo(ctypes.Structure):
+    _fields_ = [("m", c_int64), ("n", c_int64), ("batch", c_int32), ("row_blocks", c_int32),
+                ("col_blocks", c_int32), ("splits", c_int32), ("iterations", c_int64),
+                ("tensor_flops", c_double), ("method_flops", c_double), ("state_bytes", c_double)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
 class AdmmError(RuntimeError):
     def __init__(self, status: int, message: str):
         super().__init__(f"[{status}] {message}")
@@ -88,6 +97,19 @@ SIGNATURES = {
     "admm_destroy": (None, [c_void_p]),
     "admm_solve_small_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32,
                                            c_double, c_double, c_int32, c_void_p, c_void_p]),
+    "admm_batch_setup": (c_int32, [ctypes.POINTER(c_void_p), c_void_p, c_int64, c_int64, c_int32, c_int32,
+                                   c_int32, ctypes.POINTER(c_double), c_double, c_int32, c_void_p]),
+    "admm_batch_set_g": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "admm_batch_iterate": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "admm_batch_get_v": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "admm_batch_get_residuals": (c_int32, [c_void_p, ctypes.POINTER(c_double), c_void_p]),
+    "admm_batch_reset": (c_int32, [c_void_p, c_void_p]),
+    "admm_batch_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "admm_batch_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
+    "admm_batch_status": (c_int32, [c_void_p, c_void_p]),
+    "admm_batch_get_info": (c_int32, [c_void_p, ctypes.POINTER(AdmmBatchInfo)]),
+    "admm_batch_last_error": (ctypes.c_char_p, [c_void_p]),
+    "admm_batch_destroy": (None, [c_void_p]),
 }
 
 _LIB = None
@@ -285,3 +307,71 @@ def admm_solve_small_noalloc(H, g, m: int, n: int, row_blocks: int, col_blocks: 
     """Allocation-free solve of a small problem into the caller's v_out (see include/admm.h)."""
     _check(load().admm_solve_small_noalloc(_ptr(H), _ptr(g), m, n, row_blocks, col_blocks, lam, rho,
                                            iters, _ptr(v_out), _stream(stream)))
+
+
+# ---------------------------------------------------------------------------
+# batched shared-H solver
+# ---------------------------------------------------------------------------
+
+def _bcheck(status: int, handle=None) -> None:
+    if status != ADMM_OK:
+        lib = load(False)
+        msg = lib.admm_batch_last_error(handle)
+        raise AdmmError(status, (msg or lib.admm_strerror(status)).decode())
+
+
+def admm_batch_setup(H, m: int, n: int, row_blocks: int, col_blocks: int, batch: int, lam, rho: float,
+                     dtype: int, stream=None) -> int:
+    out = c_void_p()
+    lam = [float(x) for x in lam]
+    lam_arr = (c_double * max(1, len(lam)))(*lam)
+    _bcheck(load().admm_batch_setup(ctypes.byref(out), _ptr(H), m, n, row_blocks, col_blocks, batch, lam_arr,
+                                    rho, dtype, _stream(stream)))
+    return out.value
+
+
+def admm_batch_set_g(h: int, G, stream=None) -> None:
+    _bcheck(load().admm_batch_set_g(h, _ptr(G), _stream(stream)), h)
+
+
+def admm_batch_iterate(h: int, iters: int, stream=None) -> None:
+    _bcheck(load().admm_batch_iterate(h, iters, _stream(stream)), h)
+
+
+def admm_batch_get_v(h: int, V, stream=None) -> None:
+    _bcheck(load().admm_batch_get_v(h, _ptr(V), _stream(stream)), h)
+
+
+def admm_batch_get_residuals(h: int, batch: int, stream=None):
+    import numpy as np
+    out = (c_double * (2 * batch))()
+    _bcheck(load().admm_batch_get_residuals(h, out, _stream(stream)), h)
+    return np.array(out[:], dtype=np.float64).reshape(batch, 2)
+
+
+def admm_batch_reset(h: int, stream=None) -> None:
+    _bcheck(load().admm_batch_reset(h, _stream(stream)), h)
+
+
+def admm_batch_forward(h: int, X, Y, stream=None) -> None:
+    _bcheck(load().admm_batch_forward(h, _ptr(X), _ptr(Y), _stream(stream)), h)
+
+
+def admm_batch_adjoint(h: int, Y, X, stream=None) -> None:
+    _bcheck(load().admm_batch_adjoint(h, _ptr(Y), _ptr(X), _stream(stream)), h)
+
+
+def admm_batch_status(h: int, stream=None) -> int:
+    return load().admm_batch_status(h, _stream(stream))
+
+
+def admm_batch_get_info(h: int) -> dict:
+    info = AdmmBatchInfo()
+    _bcheck(load().admm_batch_get_info(h, ctypes.byref(info)), h)
+    return info.as_dict()
+
+
+def admm_batch_destroy(h: int) -> None:
+    if h:
+        load().admm_batch_destroy(h)
+

@@ -333,6 +333,20 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     return ADMM_OK;
 }
 
+int view_handle(const admm_t* h, HandleView* v) {
+    if (!h || !v || !h->H16) return ADMM_EINVAL;
+    v->H16 = h->H16;
+    v->scales = h->scales;
+    v->kinv16 = h->kinv16;
+    v->kinv_off = h->kinv_off_d;
+    v->kinv_pitch = h->kinv_pitch_d;
+    v->row_off = h->row_off_d;
+    v->col_off = h->col_off_d;
+    v->ld = h->plan.ld;
+    v->status = h->status;
+    return ADMM_OK;
+}
+
 }  // namespace admm
 
 // ---------------------------------------------------------------------------

@@ -72,6 +72,22 @@ void balanced_offsets(int64_t total, int parts, std::vector<int>& off);
 // Message returned by admm_last_error(NULL) (calls that have no handle).
 void set_handle_free_error(const char* msg);
 
+// Device buffers of a single-scene handle that the batched path reuses: the
+// FP16 copy of H, its group scales, the factors of the matrix it encodes and
+// the block tables.  ADMM_EINVAL until the FP16 copy exists.
+struct HandleView {
+    const void* H16;
+    const float* scales;
+    const float2* kinv16;
+    const long long* kinv_off;
+    const int* kinv_pitch;
+    const int* row_off;
+    const int* col_off;
+    int ld;
+    int* status;
+};
+int view_handle(const admm_t* h, HandleView* v);
+
 // Arguments of the persistent iteration kernel (passed by value).
 struct IterArgs {
     int m, n, ld, M, N, P;

@@ -142,3 +142,74 @@ class Solver:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class BatchSolver:
+    """`batch` scenes sharing one H, iterated together on the tensor cores
+    (include/admm.h, admm_batch_*).  G is batch x m, images batch x n."""
+
+    def __init__(self, H, row_blocks: int, col_blocks: int, lam, rho: float, stream=None):
+        import torch
+        self._torch = torch
+        H = _contig(H)
+        self.m, self.n = int(H.shape[0]), int(H.shape[1])
+        lam = [float(x) for x in lam]
+        self.batch = len(lam)
+        self.M, self.N = int(row_blocks), int(col_blocks)
+        self.stream = stream
+        self.h = B.admm_batch_setup(H, self.m, self.n, self.M, self.N, self.batch, lam, float(rho),
+                                    _dtype_code(H), stream)
+
+    def set_g(self, G) -> None:
+        G = _contig(G)
+        if _dtype_code(G) != B.ADMM_C64:
+            raise TypeError("G must be complex64")
+        B.admm_batch_set_g(self.h, G, self.stream)
+
+    def iterate(self, iters: int = 1) -> "BatchSolver":
+        B.admm_batch_iterate(self.h, int(iters), self.stream)
+        return self
+
+    def v(self, out=None):
+        t = self._torch
+        out = t.empty((self.batch, self.n), dtype=t.complex64, device="cuda") if out is None else out
+        B.admm_batch_get_v(self.h, out, self.stream)
+        if self.stream is not None and isinstance(out, t.Tensor) and out.is_cuda:
+            t.cuda.current_stream().wait_stream(self.stream)
+        return out
+
+    def residuals(self) -> np.ndarray:
+        return B.admm_batch_get_residuals(self.h, self.batch, self.stream)
+
+    def reset(self) -> None:
+        B.admm_batch_reset(self.h, self.stream)
+
+    def forward(self, X):
+        t = self._torch
+        Y = t.empty((self.batch, self.m), dtype=t.complex64, device="cuda")
+        B.admm_batch_forward(self.h, _contig(X), Y, self.stream)
+        return Y
+
+    def adjoint(self, Y):
+        t = self._torch
+        X = t.empty((self.batch, self.n), dtype=t.complex64, device="cuda")
+        B.admm_batch_adjoint(self.h, _contig(Y), X, self.stream)
+        return X
+
+    def status(self) -> int:
+        return B.admm_batch_status(self.h, self.stream)
+
+    def info(self) -> dict:
+        return B.admm_batch_get_info(self.h)
+
+    def close(self) -> None:
+        if getattr(self, "h", None):
+            B.admm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+

@@ -21,4 +21,5 @@ from .workloads import (  # noqa: F401
     CONFIG2,
     CONFIG3,
     gaussian_problem_device,
+    shared_h_scenes,
 )

@@ -288,3 +288,30 @@ def gaussian_problem_device(m: int, n: int, nnz: int, seed: int, snr_db: float =
     g = clean + w
     lam = float(lam_frac * (H.conj().T @ g).abs().max())
     return H, g, u, lam
+
+
+def shared_h_scenes(H: np.ndarray, count: int, seed0: int, kind: str = "sparse", nnz: int = 16,
+                    snr_db: float = 30.0, lam_frac: float = 0.05):
+    """``count`` scenes for one sensing matrix H (the batched workload): scene b
+    draws from default_rng(seed0 + b) -- for kind "sparse" ``nnz`` unit-magnitude
+    entries of uniform phase at distinct indices, for kind "plates" the
+    three-plate scene ``plate_scene(seed0 + b)`` with noise from
+    default_rng([seed0 + b, 1]) -- then w at exactly ``snr_db``.  Returns
+    (G, U, lam): G count x m and U count x n complex128 (G rounded to complex64)
+    and lam[b] = lam_frac * max|H^H g_b|."""
+    H = np.asarray(H)
+    m, n = H.shape
+    G = np.empty((count, m), dtype=np.complex128)
+    U = np.zeros((count, n), dtype=np.complex128)
+    lam = []
+    for b in range(count):
+        if kind == "plates":
+            U[b] = plate_scene(seed=seed0 + b)
+            rng = np.random.default_rng([seed0 + b, 1])
+        else:
+            rng = np.random.default_rng(seed0 + b)
+            support = rng.choice(n, size=nnz, replace=False)
+            U[b, support] = np.exp(1j * rng.uniform(0.0, 2.0 * np.pi, size=nnz))
+        G[b] = round_to_c64(noisy_measurements(H, U[b], rng, snr_db))
+        lam.append(lambda_from_fraction(H, G[b], lam_frac))
+    return G, U, lam

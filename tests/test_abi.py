@@ -160,3 +160,22 @@ def test_comm_elements_follow_table1_and_table3(cuda_lib):
     for bad in ((0, 5, 1, 1), (5, 0, 1, 1), (5, 5, 0, 1), (5, 5, 1, 0)):
         with pytest.raises(P.AdmmError):
             P.admm_comm_elements(*bad)
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(batch=0), 1), (dict(lam_bad=True), 1), (dict(m=10), 7), (dict(M=3, m=20), 7),
+])
+def test_batch_setup_argument_checks_need_no_gpu(cuda_lib, kw, code):
+    """The batched solver rejects bad sizes and block starts off the 4-element
+    grid of its FP16 tensor maps on the host, before any CUDA call."""
+    import paper_1811_05571_gb300 as P
+    args = dict(m=16, n=64, M=2, N=1, batch=2)
+    args.update({k: v for k, v in kw.items() if k != "lam_bad"})
+    H = np.zeros((args["m"], args["n"]), np.complex64)
+    lam = [0.1] * max(args["batch"], 1)
+    if kw.get("lam_bad"):
+        lam[0] = float("nan")
+    with pytest.raises(P.AdmmError) as e:
+        P.admm_batch_setup(H, args["m"], args["n"], args["M"], args["N"], args["batch"], lam, 1.0,
+                           P.ADMM_C64)
+    assert e.value.status == code
