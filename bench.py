@@ -50,6 +50,9 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12,
                     help="iterations per split in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched shared-H workload (tensor-core GEMMs)")
+    ap.add_argument("--batch", type=int, default=256, help="scenes of the batched workload")
     ap.add_argument("--no-large", action="store_true",
                     help="skip the 8192x131072 mixed-precision workload")
     ap.add_argument("--no-time-to-tol", action="store_true",
@@ -69,8 +72,9 @@ def load_peaks() -> dict:
     if os.path.exists(path):
         with open(path) as f:
             d = json.load(f)
-        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
-    return {"hbm_gbs": 6800.0, "source": "fallback"}
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d.get("bf16_tflops", 1900.0)),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
 def load_traffic() -> dict | None:
@@ -429,6 +433,52 @@ def mixed_precision_large(pkg, stream, dev, barrier, peaks) -> dict:
     return out
 
 
+def batched_shared_h(pkg, stream, dev, barrier, p, peaks, batch: int = 256, steps: int = 10) -> dict:
+    """B three-plate scenes (seeds 100 ...) on the CRA matrix, iterated together by
+    the tensor-core path in each split; per split the time of one iteration of
+    all scenes (CUDA events around `steps` graph launches), the tensor-core
+    FLOP rate issued, and the state bytes moved per second."""
+    import numpy as np
+    import torch
+    import synth
+    G, _, lam = synth.shared_h_scenes(p.H, batch, seed0=100, kind="plates")
+    H_d = torch.from_numpy(p.H_c64()).to(dev)
+    G_d = torch.from_numpy(G.astype(np.complex64)).to(dev)
+    out = {"workload": f"CRA-shaped 1440x32768, {batch} three-plate scenes (seeds 100-{99 + batch}), "
+                       f"30 dB, lambda_b = 0.05 max|H^H g_b|, rho {p.rho:.1f}, FP16 H",
+           "batch": batch, "splits": {}}
+    for M, N in SPLITS:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            bs = pkg.BatchSolver(H_d, M, N, lam, p.rho, stream=stream)
+            bs.set_g(G_d)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        bs.iterate(3)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        bs.iterate(steps)
+        b.record(stream)
+        barrier()
+        us = a.elapsed_time(b) / steps * 1e3
+        if bs.status() != 0:
+            raise RuntimeError("device status after the batched runs")
+        info = bs.info()
+        bs.close()
+        out["splits"][f"{M}x{N}"] = {
+            "us_per_iteration": us, "scene_iterations_per_s": batch / us * 1e6,
+            "tensor_tflops": info["tensor_flops"] / us / 1e6,
+            "tensor_frac": info["tensor_flops"] / us / 1e6 / peaks["bf16_tflops"],
+            "method_tflops": info["method_flops"] / us / 1e6,
+            "state_gbs": info["state_bytes"] / us / 1e3,
+            "state_frac": info["state_bytes"] / us / 1e3 / peaks["hbm_gbs"],
+            "tensor_flops_per_iter": info["tensor_flops"], "state_bytes_per_iter": info["state_bytes"],
+            "forward_k_splits": info["splits"], "setup_ms": setup_ms}
+    return out
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -559,6 +609,9 @@ def run_ours(args) -> None:
     large = None
     if not args.no_large:
         large = mixed_precision_large(pkg, stream, dev, barrier, peaks=load_peaks())
+    batched = None
+    if not args.no_batch:
+        batched = batched_shared_h(pkg, stream, dev, barrier, p, peaks=load_peaks(), batch=args.batch)
 
     phases = None
     if args.trace > 0:
@@ -634,6 +687,8 @@ def run_ours(args) -> None:
         line["time_to_tol"] = ttt
     if large is not None:
         line["mixed_precision_large"] = large
+    if batched is not None:
+        line["batched_shared_h"] = batched
     if phases is not None:
         line["phases"] = phases
     for s in solvers:
