@@ -23,6 +23,7 @@ constexpr int kTileK = 64;          // FP16 elements of K per pipeline stage
 // row_scale[(rs_off[p] + row) >> rs_shift] * col_scale[p * B + b].
 struct GemmArgs {
     int nprob, mtiles, ntiles, splits, kb_per_split;
+    int ctas;                // persistent CTAs (one per SM)
     const int* a_x0;
     const int* a_y0;
     const int* a_z;
@@ -60,6 +61,8 @@ struct PackArgs {
     int adjoint;           // 0: (re,-im),(im,re) form; 1: (re,im),(im,-re) form
     int second;            // __half2 offset of the (hi, hi, 0, 0) copy, or -1
     float* scale;          // [p * B + b]
+    const unsigned* vmax;  // when set: [p * B + b] largest |component| of the vector (float
+                           // bits), known beforehand, so packing takes one pass
 };
 
 // Elementwise steps of the batched iteration.
@@ -79,7 +82,12 @@ struct StepArgs {
     const float* kappa;   // per scene
     float rho, inv_M;
     double* res;     // 2 per scene: ||r_p||^2, ||r_d||^2 / (rho^2 M)
+    unsigned* zmax;  // [p * B + b] largest |component| of the next z_j^i (float bits)
+    const int* upd_tile_off;  // N + 1: first update tile of each column block
+    int upd_tiles;            // update tiles (kUpdCols columns, inside one block)
 };
+
+constexpr int kUpdCols = 1024;   // columns per update CTA
 
 cudaError_t prepare_gemm();
 cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const GemmArgs& a, cudaStream_t s);

@@ -37,6 +37,7 @@ struct admm_batch {
     float2 *V = nullptr, *S = nullptr, *G = nullptr, *Gt = nullptr, *Ghat = nullptr, *R = nullptr,
            *Ppart = nullptr, *W = nullptr, *Sig = nullptr, *X = nullptr, *Y = nullptr;
     float *zscale = nullptr, *rscale = nullptr, *wscale = nullptr, *kappa = nullptr;
+    unsigned* zmax = nullptr;   // largest |component| of the next z per (block, scene)
     double* res = nullptr;
     int* itab = nullptr;
     long long* ltab = nullptr;
@@ -87,7 +88,7 @@ void free_batch(admm_batch_t* h) {
     if (h->graph) cudaGraphDestroy(h->graph);
     void* ptrs[] = {h->H16T, h->Kpack, h->Zpack, h->Rpack, h->Wpack, h->kscale, h->V, h->S, h->G, h->Gt,
                     h->Ghat, h->R, h->Ppart, h->W, h->Sig, h->X, h->Y, h->zscale, h->rscale, h->wscale,
-                    h->kappa, h->res, h->itab, h->ltab, h->status};
+                    h->kappa, h->res, h->itab, h->ltab, h->status, h->zmax};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->inner) admm_destroy(h->inner);
@@ -135,6 +136,7 @@ cudaError_t enqueue_iteration(admm_batch_t* h, cudaStream_t s) {
     if (e == cudaSuccess) e = launch_pack(h->pw, h->P, s);
     if (e == cudaSuccess) e = launch_gemm(h->mapHT, h->mapW, h->g2, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->res, 0, 2 * sizeof(double) * h->B, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->zmax, 0, sizeof(unsigned) * h->P * h->B, s);
     if (e == cudaSuccess) e = launch_update(h->st, s);
     return e;
 }
@@ -251,6 +253,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
               dalloc0(&h->rscale, static_cast<size_t>(P) * Bn) == cudaSuccess &&
               dalloc0(&h->wscale, static_cast<size_t>(P) * Bn) == cudaSuccess &&
               dalloc0(&h->kappa, static_cast<size_t>(Bn)) == cudaSuccess &&
+              dalloc0(&h->zmax, static_cast<size_t>(P) * Bn) == cudaSuccess &&
               dalloc0(&h->res, static_cast<size_t>(2) * Bn) == cudaSuccess &&
               dalloc0(&h->status, 1) == cudaSuccess;
     if (!ok) return bail(bfail(h, ADMM_ENOMEM, "device allocation failed for the batched path"));
@@ -287,6 +290,9 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
             xr[p] = static_cast<long long>(p) * Bn * mp;
             xy[p] = ro[i];
         }
+    std::vector<int> uto(col_blocks + 1, 0);
+    for (int j = 0; j < col_blocks; ++j) uto[j + 1] = uto[j] + (co[j + 1] - co[j] + kUpdCols - 1) / kUpdCols;
+    const size_t o_uto = put(uto);
     const size_t o_a1x = put(a1x), o_a1y = put(a1y), o_zero = put(zero), o_rows1 = put(rows1), o_kb1 = put(kb1p),
                  o_rsr = put(rsr), o_a2x = put(a2x), o_a2y = put(a2y), o_rows2 = put(rows2), o_kb2 = put(kb2p),
                  o_kk = put(kkp), o_ksoff = put(ksoff), o_pz = put(pz), o_lenz = put(lenz), o_lenr = put(lenr),
@@ -346,6 +352,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
     g1.out_pitch = h->mpitch;
     g1.B = Bn;
     g1.status = h->status;
+    g1.ctas = sms;
     g1.timeout_ns = h->timeout_ns;
     // factor product K_ij^{-1} r_ij
     GemmArgs& gk = h->gk;
@@ -394,8 +401,10 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
     pz_.adjoint = 0;
     pz_.second = -1;
     pz_.scale = h->zscale;
+    pz_.vmax = h->zmax;
     PackArgs& pr_ = h->pr;
     pr_ = pz_;
+    pr_.vmax = nullptr;
     pr_.x = h->R;
     pr_.x_off = LT + o_xr;
     pr_.x_bs = mp;
@@ -418,6 +427,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
     PackArgs& px_ = h->px;
     px_ = pz_;
     px_.y = nullptr;
+    px_.vmax = nullptr;
     PackArgs& py_ = h->py;
     py_ = pw_;
     py_.x_off = LT + o_xy;
@@ -448,6 +458,9 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
     s_.rho = static_cast<float>(rho);
     s_.inv_M = 1.0f / row_blocks;
     s_.res = h->res;
+    s_.zmax = h->zmax;
+    s_.upd_tile_off = T + o_uto;
+    s_.upd_tiles = uto[col_blocks];
     *out = h;
     return ADMM_OK;
 }
@@ -468,6 +481,7 @@ int admm_batch_reset(admm_batch_t* h, void* stream) {
     BCK(h, cudaMemsetAsync(h->V, 0, static_cast<size_t>(h->B) * h->n * sizeof(float2), s));
     BCK(h, cudaMemsetAsync(h->S, 0, static_cast<size_t>(h->M) * h->B * h->n * sizeof(float2), s));
     BCK(h, cudaMemsetAsync(h->Ghat, 0, static_cast<size_t>(h->N) * h->B * h->m * sizeof(float2), s));
+    BCK(h, cudaMemsetAsync(h->zmax, 0, static_cast<size_t>(h->P) * h->B * sizeof(unsigned), s));
     BCK(h, cudaMemsetAsync(h->status, 0, sizeof(int), s));
     BCK(h, cudaStreamSynchronize(s));
     h->k = 0;

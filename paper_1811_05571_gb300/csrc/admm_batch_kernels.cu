@@ -98,10 +98,31 @@ __device__ bool wait_always(uint64_t* bar, uint32_t parity, const GemmArgs& a) {
     return true;
 }
 
-// The tensor cores' FP32 accumulation loses more than the FP16 operand split
-// over long K, so each CTA accumulates chunks of kChunk K blocks in one of two
-// TMEM accumulators and the epilogue warps add every chunk into FP32 registers
-// (hi and lo columns of a scene combined first: two values per scene).
+// One output tile: problem p, row tile mt, column tile nt, K split `split`
+struct Tile {
+    int p, mt, nt, split, kb0, nk;
+};
+
+__device__ __forceinline__ Tile tile_of(const GemmArgs& a, int t) {
+    Tile x;
+    x.nt = t % a.ntiles;
+    int r = t / a.ntiles;
+    x.mt = r % a.mtiles;
+    r /= a.mtiles;
+    x.p = r % a.nprob;
+    x.split = r / a.nprob;
+    x.kb0 = x.split * a.kb_per_split;
+    x.nk = max(min(a.kb_prob[x.p], x.kb0 + a.kb_per_split) - x.kb0, 0);
+    return x;
+}
+
+// Persistent GEMM: each CTA walks tiles t = blockIdx.x, + gridDim.x, ... (tiles
+// that share an A tile are adjacent).  The tensor cores' FP32 accumulation
+// loses more than the FP16 operand split over long K, so each tile is
+// accumulated in chunks of kChunk K blocks in one of two TMEM accumulators and
+// the epilogue warps add every chunk into FP32 registers (hi and lo columns of
+// a scene combined first: two values per scene).  Stage and chunk counters run
+// on across tiles, so the epilogue of one tile overlaps the MMAs of the next.
 __global__ void __launch_bounds__(kGemmThreads, 1)
     bgemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                  const __grid_constant__ GemmArgs a) {
@@ -115,12 +136,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     int* fail = reinterpret_cast<int*>(tmem_slot + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x / a.mtiles, mt = blockIdx.x - p * a.mtiles;
-    const int nt = blockIdx.y, split = blockIdx.z;
-    const int kbp = a.kb_prob[p];
-    const int kb0 = split * a.kb_per_split;
-    const int nk = max(min(kbp, kb0 + a.kb_per_split) - kb0, 0);
-    const int nchunks = (nk + kChunk - 1) / kChunk;
+    const int ntile = a.nprob * a.mtiles * a.ntiles * a.splits;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -147,89 +163,108 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         // producer: one A tile and one B tile per stage
         prefetch_tensormap(&tmA);
         prefetch_tensormap(&tmB);
-        const int ax = a.a_x0[p], ay = a.a_y0[p] + mt * kTileM, az = a.a_z[p];
-        int issued = 0;
-        for (int kb = 0; kb < nk; ++kb) {
-            const int slot = kb % kStages;
-            if (!wait_bounded(&empty[slot], ((kb / kStages) & 1) ^ 1, fail, a)) break;
-            unsigned char* st = smem + slot * kStageBytes;
-            mbar_arrive_expect_tx(&full[slot], kStageBytes);
-            tma_load_3d(st, &tmA, ax + (kb0 + kb) * kTileK, ay, az, &full[slot]);
-            tma_load_3d(st + kABytes, &tmB, (kb0 + kb) * kTileK, nt * kTileN, p, &full[slot]);
-            ++issued;
+        int g = 0;   // stages issued
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+            const Tile x = tile_of(a, t);
+            const int ax = a.a_x0[x.p], ay = a.a_y0[x.p] + x.mt * kTileM, az = a.a_z[x.p];
+            for (int kb = 0; kb < x.nk; ++kb, ++g) {
+                const int slot = g % kStages;
+                if (!wait_bounded(&empty[slot], ((g / kStages) & 1) ^ 1, fail, a)) {
+                    ok = false;
+                    break;
+                }
+                unsigned char* st = smem + slot * kStageBytes;
+                mbar_arrive_expect_tx(&full[slot], kStageBytes);
+                tma_load_3d(st, &tmA, ax + (x.kb0 + kb) * kTileK, ay, az, &full[slot]);
+                tma_load_3d(st + kABytes, &tmB, (x.kb0 + kb) * kTileK, x.nt * kTileN, x.p, &full[slot]);
+            }
         }
         // copies still in flight land before the CTA can exit
-        for (int kb = max(issued - kStages, 0); kb < issued; ++kb)
-            wait_always(&full[kb % kStages], (kb / kStages) & 1, a);
+        for (int q = max(g - kStages, 0); q < g; ++q) wait_always(&full[q % kStages], (q / kStages) & 1, a);
     } else if (warp == 1 && lane == 0) {
         // MMA issuer: four K=16 steps per 64-wide stage (32 bytes each)
-        int kb = 0;
-        for (int c = 0; c < nchunks; ++c) {
-            const int buf = c & 1;
-            // the epilogue has read the accumulator's previous chunk
-            if (!wait_bounded(&acc_free[buf], ((c >> 1) & 1) ^ 1, fail, a)) break;
-            tc_fence_after();
-            const uint32_t d = tmem + buf * kTileN;
-            const int kb_end = min(nk, kb + kChunk);
-            bool ok = true;
-            for (int first = kb; kb < kb_end; ++kb) {
-                const int slot = kb % kStages;
-                if (!wait_bounded(&full[slot], (kb / kStages) & 1, fail, a)) {
+        int g = 0, gc = 0;   // stages consumed, chunks started
+        bool ok = true;
+        for (int t = blockIdx.x; t < ntile && ok; t += gridDim.x) {
+            const Tile x = tile_of(a, t);
+            for (int kb = 0; kb < x.nk && ok; ++gc) {
+                const int buf = gc & 1;
+                // the epilogue has read this accumulator's previous chunk
+                if (!wait_bounded(&acc_free[buf], ((gc >> 1) & 1) ^ 1, fail, a)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const unsigned char* st = smem + slot * kStageBytes;
-                const uint64_t ad = umma_desc_k128(st), bd = umma_desc_k128(st + kABytes);
+                const uint32_t d = tmem + buf * kTileN;
+                const int kb_end = min(x.nk, kb + kChunk);
+                for (const int first = kb; kb < kb_end; ++kb, ++g) {
+                    const int slot = g % kStages;
+                    if (!wait_bounded(&full[slot], (g / kStages) & 1, fail, a)) {
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const unsigned char* st = smem + slot * kStageBytes;
+                    const uint64_t ad = umma_desc_k128(st), bd = umma_desc_k128(st + kABytes);
 #pragma unroll
-                for (int k = 0; k < kTileK / 16; ++k)
-                    umma_f16(d, ad + 2 * k, bd + 2 * k, kIdesc, (kb > first || k > 0) ? 1u : 0u);
-                umma_commit(&empty[slot]);
+                    for (int k = 0; k < kTileK / 16; ++k)
+                        umma_f16(d, ad + 2 * k, bd + 2 * k, kIdesc, (kb > first || k > 0) ? 1u : 0u);
+                    umma_commit(&empty[slot]);
+                }
+                umma_commit(&acc_full[buf]);   // also marks every earlier MMA complete
             }
-            umma_commit(&acc_full[buf]);   // also marks every earlier MMA complete
-            if (!ok) break;
         }
+        // every MMA issued has completed before TMEM can be released, also when
+        // the epilogue stopped early after a failure
+        if (gc > 0) wait_always(&acc_full[(gc - 1) & 1], ((gc - 1) >> 1) & 1, a);
     } else if (warp >= 2) {
         // epilogue: TMEM lane quarter (warp % 4); per chunk, 8 loads of 32 columns
         // (8 scenes each) added into two FP32 registers per scene
         const int q = warp & 3;
-        const int row = mt * kTileM + q * 32 + lane;
-        const bool row_ok = row < a.rows[p];
-        float acc[2 * (kTileN / 4)];
-#pragma unroll
-        for (int e = 0; e < 2 * (kTileN / 4); ++e) acc[e] = 0.f;
+        int gc = 0;
         bool ok = true;
-        for (int c = 0; c < nchunks && ok; ++c) {
-            const int buf = c & 1;
-            ok = wait_always(&acc_full[buf], (c >> 1) & 1, a) && !*reinterpret_cast<volatile int*>(fail);
-            tc_fence_after();
-            if (ok) {
+        for (int t = blockIdx.x; t < ntile; t += gridDim.x) {
+            const Tile x = tile_of(a, t);
+            const int nchunks = (x.nk + kChunk - 1) / kChunk;
+            float acc[2 * (kTileN / 4)];
 #pragma unroll
-                for (int cc = 0; cc < kTileN / 32; ++cc) {
-                    uint32_t r[32];
-                    tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * kTileN + cc * 32, r);
-                    tmem_ld_wait();
+            for (int e = 0; e < 2 * (kTileN / 4); ++e) acc[e] = 0.f;
+            for (int c = 0; c < nchunks && ok; ++c, ++gc) {
+                const int buf = gc & 1;
+                ok = wait_always(&acc_full[buf], (gc >> 1) & 1, a) && !*reinterpret_cast<volatile int*>(fail);
+                tc_fence_after();
+                if (ok) {
 #pragma unroll
-                    for (int s = 0; s < 8; ++s) {
-                        acc[2 * (cc * 8 + s)] += __uint_as_float(r[4 * s]) + __uint_as_float(r[4 * s + 2]);
-                        acc[2 * (cc * 8 + s) + 1] += __uint_as_float(r[4 * s + 1]) + __uint_as_float(r[4 * s + 3]);
+                    for (int cc = 0; cc < kTileN / 32; ++cc) {
+                        uint32_t r[32];
+                        tmem_ld32(tmem + (static_cast<uint32_t>(q * 32) << 16) + buf * kTileN + cc * 32, r);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int s = 0; s < 8; ++s) {
+                            acc[2 * (cc * 8 + s)] += __uint_as_float(r[4 * s]) + __uint_as_float(r[4 * s + 2]);
+                            acc[2 * (cc * 8 + s) + 1] +=
+                                __uint_as_float(r[4 * s + 1]) + __uint_as_float(r[4 * s + 3]);
+                        }
                     }
                 }
+                tc_fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&acc_free[buf]);
             }
-            tc_fence_before();
-            __syncwarp();
-            if (lane == 0) mbar_arrive(&acc_free[buf]);
-        }
-        float rs = 1.0f;
-        if (a.row_scale && row_ok) rs = a.row_scale[(a.rs_off[p] + row) >> a.rs_shift];
+            if (!ok) break;
+            const int row = x.mt * kTileM + q * 32 + lane;
+            const bool row_ok = row < a.rows[x.p];
+            float rs = 1.0f;
+            if (a.row_scale && row_ok) rs = a.row_scale[(a.rs_off[x.p] + row) >> a.rs_shift];
 #pragma unroll
-        for (int s = 0; s < kTileN / 4; ++s) {
-            const int b = nt * (kTileN / 4) + s;
-            if (!row_ok || b >= a.B) continue;
-            const float sc = rs * a.col_scale[p * a.B + b];
-            const float re = ok ? acc[2 * s] : 0.f, im = ok ? acc[2 * s + 1] : 0.f;
-            a.out[((static_cast<size_t>(split) * a.nprob + p) * a.B + b) * a.out_pitch + row] =
-                make_float2(re * sc, im * sc);
+            for (int s = 0; s < kTileN / 4; ++s) {
+                const int b = x.nt * (kTileN / 4) + s;
+                if (!row_ok || b >= a.B) continue;
+                const float sc = rs * a.col_scale[x.p * a.B + b];
+                a.out[((static_cast<size_t>(x.split) * a.nprob + x.p) * a.B + b) * a.out_pitch + row] =
+                    make_float2(acc[2 * s] * sc, acc[2 * s + 1] * sc);
+            }
         }
     }
     tc_fence_before();
@@ -265,11 +300,15 @@ __global__ void pack_kernel(PackArgs a) {
         return v;
     };
     float mx = 0.f;
-    for (int e = threadIdx.x; e < L; e += blockDim.x) {
-        const float2 v = value(e);
-        mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    if (a.vmax) {
+        mx = __uint_as_float(a.vmax[p * a.B + b]);
+    } else {
+        for (int e = threadIdx.x; e < L; e += blockDim.x) {
+            const float2 v = value(e);
+            mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+        }
+        mx = block_max(mx, red);
     }
-    mx = block_max(mx, red);
     const float sc = pow2_scale(mx), inv = 1.0f / sc;
     if (threadIdx.x == 0) a.scale[p * a.B + b] = sc;
     const size_t row = a.row2;
@@ -377,45 +416,96 @@ __device__ __forceinline__ float2 soft(float2 x, float kappa) {
 }
 
 // v_j = S_kappa(v_j + mean_i sigma_j^i), s_j^i <- v_old + sigma_j^i - v_new (the
-// u-step u = z + sigma and s += u - v combined); per-scene residual terms
-__global__ void update_kernel(StepArgs a) {
+// u-step u = z + sigma and s += u - v combined); per-scene residual terms, and
+// the largest |component| of the next z_j^i = v_new - s_new^i per (block, scene),
+// so that the next packing of z takes one pass
+constexpr int kUpdRegs = 16;     // replicas whose sigma and z maximum stay in registers
+constexpr int kUpdThreads = 256;
+
+// one CTA per (tile of kUpdCols columns inside one column block, scene); the
+// first MR replicas are kept in registers (loops unrolled to MR, guarded by M)
+template <int MR>
+__global__ void __launch_bounds__(kUpdThreads, 4) update_kernel(StepArgs a) {
+    __shared__ float zred[MR][kUpdThreads / 32];
     const int b = blockIdx.y;
+    int j = 0;
+    while (a.upd_tile_off[j + 1] <= static_cast<int>(blockIdx.x)) ++j;
+    const int c_beg = a.col_off[j] + (blockIdx.x - a.upd_tile_off[j]) * kUpdCols;
+    const int c_end = min(a.col_off[j + 1], c_beg + kUpdCols);
+    const int cb = c_beg - a.col_off[j];
     const float kappa = a.kappa[b];
-    double rp = 0.0, rd = 0.0;
-    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < a.n; c += gridDim.x * blockDim.x) {
-        int j = 0;
-        while (a.col_off[j + 1] <= c) ++j;
-        const int cl = c - a.col_off[j];
+    float rp = 0.f, rd = 0.f;   // a few terms per thread; FP64 from the warp sums on
+    float zm[MR];
+#pragma unroll
+    for (int i = 0; i < MR; ++i) zm[i] = 0.f;
+    for (int c = c_beg + threadIdx.x; c < c_end; c += kUpdThreads) {
+        const int cl = cb + (c - c_beg);
         float2* vp = a.V + static_cast<size_t>(b) * a.n + c;
         const float2 vo = *vp;
+        const float2* sgp = a.Sig + (static_cast<size_t>(j) * a.B + b) * a.npitch + cl;
+        const size_t sg_i = static_cast<size_t>(a.N) * a.B * a.npitch;   // next replica
+        float2 sg[MR];
         float2 mean = make_float2(0.f, 0.f);
-        for (int i = 0; i < a.M; ++i) {
-            const float2 sg = a.Sig[(static_cast<size_t>(i * a.N + j) * a.B + b) * a.npitch + cl];
-            mean.x += sg.x;
-            mean.y += sg.y;
+#pragma unroll
+        for (int i = 0; i < MR; ++i) {
+            sg[i] = i < a.M ? sgp[i * sg_i] : make_float2(0.f, 0.f);
+            mean.x += sg[i].x;
+            mean.y += sg[i].y;
+        }
+        for (int i = MR; i < a.M; ++i) {
+            const float2 x = sgp[i * sg_i];
+            mean.x += x.x;
+            mean.y += x.y;
         }
         const float2 vn = soft(make_float2(vo.x + mean.x * a.inv_M, vo.y + mean.y * a.inv_M), kappa);
         *vp = vn;
-        for (int i = 0; i < a.M; ++i) {
-            const float2 sg = a.Sig[(static_cast<size_t>(i * a.N + j) * a.B + b) * a.npitch + cl];
-            float2* sp = a.S + (static_cast<size_t>(i) * a.B + b) * a.n + c;
-            const float2 so = *sp;
+        float2* spb = a.S + static_cast<size_t>(b) * a.n + c;
+        const size_t s_i = static_cast<size_t>(a.B) * a.n;
+        auto step = [&](float2 x, float2 so, float2* sp) {
             // u = v_old - s + sigma; s_new = s + u - v_new
-            const float2 u = make_float2(vo.x - so.x + sg.x, vo.y - so.y + sg.y);
-            *sp = make_float2(so.x + u.x - vn.x, so.y + u.y - vn.y);
+            const float2 u = make_float2(vo.x - so.x + x.x, vo.y - so.y + x.y);
+            const float2 sn = make_float2(so.x + u.x - vn.x, so.y + u.y - vn.y);
+            *sp = sn;
             const float dx = u.x - vn.x, dy = u.y - vn.y;
-            rp += static_cast<double>(dx) * dx + static_cast<double>(dy) * dy;
-        }
+            rp = fmaf(dx, dx, fmaf(dy, dy, rp));
+            // largest component of the next z = v_new - s_new
+            return fmaxf(fabsf(vn.x - sn.x), fabsf(vn.y - sn.y));
+        };
+        // all duals of the register replicas loaded before any is stored
+        float2 so[MR];
+#pragma unroll
+        for (int i = 0; i < MR; ++i) so[i] = i < a.M ? spb[i * s_i] : make_float2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < MR; ++i)
+            if (i < a.M) zm[i] = fmaxf(zm[i], step(sg[i], so[i], spb + i * s_i));
+        for (int i = MR; i < a.M; ++i)
+            atomicMax(a.zmax + (i * a.N + j) * a.B + b,
+                      __float_as_uint(step(sgp[i * sg_i], spb[i * s_i], spb + i * s_i)));
         const float ex = vn.x - vo.x, ey = vn.y - vo.y;
-        rd += static_cast<double>(ex) * ex + static_cast<double>(ey) * ey;
+        rd = fmaf(ex, ex, fmaf(ey, ey, rd));
     }
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int mreg = min(a.M, MR);
+#pragma unroll
+    for (int i = 0; i < MR; ++i) {
+        float x = zm[i];
+        for (int o = 16; o > 0; o >>= 1) x = fmaxf(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (lane == 0) zred[i][warp] = x;
+    }
+    double dp = rp, dd = rd;
     for (int o = 16; o > 0; o >>= 1) {
-        rp += __shfl_xor_sync(0xffffffffu, rp, o);
-        rd += __shfl_xor_sync(0xffffffffu, rd, o);
+        dp += __shfl_xor_sync(0xffffffffu, dp, o);
+        dd += __shfl_xor_sync(0xffffffffu, dd, o);
     }
-    if ((threadIdx.x & 31) == 0) {
-        atomicAdd(a.res + 2 * b, rp);
-        atomicAdd(a.res + 2 * b + 1, rd);
+    if (lane == 0) {
+        atomicAdd(a.res + 2 * b, dp);
+        atomicAdd(a.res + 2 * b + 1, dd);
+    }
+    __syncthreads();
+    if (threadIdx.x < mreg) {
+        float x = 0.f;
+        for (int w = 0; w < kUpdThreads / 32; ++w) x = fmaxf(x, zred[threadIdx.x][w]);
+        atomicMax(a.zmax + (threadIdx.x * a.N + j) * a.B + b, __float_as_uint(x));
     }
 }
 
@@ -486,8 +576,8 @@ cudaError_t prepare_gemm() {
 }
 
 cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const GemmArgs& a, cudaStream_t s) {
-    dim3 grid(static_cast<unsigned>(a.nprob * a.mtiles), static_cast<unsigned>(a.ntiles),
-              static_cast<unsigned>(a.splits));
+    const int tiles = a.nprob * a.mtiles * a.ntiles * a.splits;
+    const int grid = std::max(1, std::min(tiles, a.ctas));
     bgemm_kernel<<<grid, kGemmThreads, kGemmSmem, s>>>(A, B, a);
     return cudaGetLastError();
 }
@@ -519,8 +609,12 @@ cudaError_t launch_sum_blocks(const float2* part, int splits, int P, int B, int 
 }
 
 cudaError_t launch_update(const StepArgs& a, cudaStream_t s) {
-    const int gx = std::max(1, std::min(64, (a.n + 255) / 256));
-    update_kernel<<<dim3(gx, a.B), 256, 0, s>>>(a);
+    const dim3 grid(a.upd_tiles, a.B);
+    if (a.M <= 1) update_kernel<1><<<grid, kUpdThreads, 0, s>>>(a);
+    else if (a.M <= 2) update_kernel<2><<<grid, kUpdThreads, 0, s>>>(a);
+    else if (a.M <= 4) update_kernel<4><<<grid, kUpdThreads, 0, s>>>(a);
+    else if (a.M <= 8) update_kernel<8><<<grid, kUpdThreads, 0, s>>>(a);
+    else update_kernel<kUpdRegs><<<grid, kUpdThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
