@@ -425,7 +425,7 @@ constexpr int kUpdThreads = 256;
 // one CTA per (tile of kUpdCols columns inside one column block, scene); the
 // first MR replicas are kept in registers (loops unrolled to MR, guarded by M)
 template <int MR>
-__global__ void __launch_bounds__(kUpdThreads, 4) update_kernel(StepArgs a) {
+__global__ void __launch_bounds__(kUpdThreads, MR <= 2 ? 4 : (MR <= 4 ? 3 : 2)) update_kernel(StepArgs a) {
     __shared__ float zred[MR][kUpdThreads / 32];
     const int b = blockIdx.y;
     int j = 0;
