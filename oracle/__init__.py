@@ -22,3 +22,4 @@ from .admm_fp64 import (  # noqa: F401
     lemma_applies,
 )
 from . import quantize  # noqa: F401,E402
+from . import adjoint  # noqa: F401,E402
