@@ -377,6 +377,26 @@ int admm_batch_forward(admm_batch_t* h, const void* X, void* Y, void* stream);
 /* X_b = Hq^H Y_b for every scene (the adjoint product of the u-step).  Synchronises. */
 int admm_batch_adjoint(admm_batch_t* h, const void* Y, void* X, void* stream);
 
+/* Record the next `iters` iterations for admm_batch_backward: per iteration
+ * the shrinkage arguments a = mean_i(u^i + s^i) (batch x n) and the factor
+ * solutions w_ij = K_ij^{-1} r_ij (every block), all the reverse sweep needs,
+ * since the soft-threshold is the iteration's only non-linear step.  0 turns
+ * recording off.  Resets the state (admm_batch_reset) and synchronises. */
+int admm_batch_record(admm_batch_t* h, int32_t iters);
+
+/* Reverse sweep over the iterations run since the last reset (all recorded):
+ * given dV = dL/dv (batch x n complex64, x_bar = dL/dRe x + i dL/dIm x) of a
+ * real loss L of the image v after those iterations, write dG = dL/dg
+ * (batch x m) and, per scene, dlambda = dL/dlambda_b and drho = dL/drho
+ * (host doubles, batch each).  Every step is the adjoint of the iteration of
+ * admm_batch_iterate: for |a| > kappa with a_hat = a/|a|, a_bar = t -
+ * (kappa/|a|)(t - a_hat Re(conj(a_hat) t)) and kappa_bar = -Re(conj(a_hat) t)
+ * (zero otherwise, Eq. softhresholding), and dw/drho = -K^{-1} w; the
+ * products H sigma_bar, K^{-1} w_bar and H^H r_bar run on the tensor-core
+ * GEMMs of the forward path.  Synchronises.  ADMM_EINVAL when the iterations
+ * since the reset were not all recorded.  The paper has no counterpart. */
+int admm_batch_backward(admm_batch_t* h, const void* dV, void* dG, double* dlambda, double* drho, void* stream);
+
 /* Synchronise `stream` and return the sticky device status. */
 int admm_batch_status(admm_batch_t* h, void* stream);
 

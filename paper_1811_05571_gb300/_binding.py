@@ -107,6 +107,9 @@ SIGNATURES = {
     "admm_batch_forward": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "admm_batch_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "admm_batch_status": (c_int32, [c_void_p, c_void_p]),
+    "admm_batch_record": (c_int32, [c_void_p, c_int32]),
+    "admm_batch_backward": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
+                                      ctypes.POINTER(c_double), c_void_p]),
     "admm_batch_get_info": (c_int32, [c_void_p, ctypes.POINTER(AdmmBatchInfo)]),
     "admm_batch_last_error": (ctypes.c_char_p, [c_void_p]),
     "admm_batch_destroy": (None, [c_void_p]),
@@ -374,4 +377,16 @@ def admm_batch_get_info(h: int) -> dict:
 def admm_batch_destroy(h: int) -> None:
     if h:
         load().admm_batch_destroy(h)
+
+
+def admm_batch_record(h: int, iters: int) -> None:
+    _bcheck(load().admm_batch_record(h, iters), h)
+
+
+def admm_batch_backward(h: int, batch: int, dV, dG, stream=None):
+    import numpy as np
+    dl = (c_double * batch)()
+    dr = (c_double * batch)()
+    _bcheck(load().admm_batch_backward(h, _ptr(dV), _ptr(dG), dl, dr, _stream(stream)), h)
+    return np.array(dl[:]), np.array(dr[:])
 

@@ -85,6 +85,21 @@ struct StepArgs {
     unsigned* zmax;  // [p * B + b] largest |component| of the next z_j^i (float bits)
     const int* upd_tile_off;  // N + 1: first update tile of each column block
     int upd_tiles;            // update tiles (kUpdCols columns, inside one block)
+    // recording for the adjoint (null when off): iteration k writes its
+    // shrinkage arguments a (B x n) and factor solutions w (P x B x mpitch)
+    // into slot *rec_k, while *rec_k < rec_cap
+    float2* rec_a;
+    float2* rec_w;
+    int* rec_k;
+    int rec_cap;
+    // reverse sweep
+    float2* Vb;          // B x n: adjoint of v
+    float2* Sb;          // M x B x n: adjoint of s
+    float2* Ghb;         // N x B x m: adjoint of the estimated data
+    float2* dG;          // B x m: gradient of g
+    double* kbar;        // per scene: adjoint of kappa
+    double* rbar;        // per scene: adjoint of rho (direct terms)
+    int bk;              // iteration whose records the sweep reads
 };
 
 constexpr int kUpdCols = 1024;   // columns per update CTA
@@ -96,6 +111,12 @@ cudaError_t launch_residual_r(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_ghat(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_update(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_gtilde(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_rec_advance(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_bw_soft(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_bw_wbar(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_bw_rbar(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_bw_state(const StepArgs& a, cudaStream_t s);
+cudaError_t launch_bw_gtilde(const StepArgs& a, cudaStream_t s);
 cudaError_t launch_sum_blocks(const float2* part, int splits, int P, int B, int pitch, const int* off, int nblk,
                               int N, int by_rows, float2* out, int out_len, cudaStream_t s);
 cudaError_t launch_transpose_h16(const void* H16, int m, int ld, void* HT, cudaStream_t s);

@@ -38,6 +38,13 @@ struct admm_batch {
            *Ppart = nullptr, *W = nullptr, *Sig = nullptr, *X = nullptr, *Y = nullptr;
     float *zscale = nullptr, *rscale = nullptr, *wscale = nullptr, *kappa = nullptr;
     unsigned* zmax = nullptr;   // largest |component| of the next z per (block, scene)
+    // recording for the adjoint and the reverse-sweep buffers
+    float2 *rec_a = nullptr, *rec_w = nullptr, *Vb = nullptr, *Sb = nullptr, *Ghb = nullptr, *dG = nullptr;
+    int* rec_k = nullptr;
+    double *kbar = nullptr, *rbar = nullptr;
+    int rec_cap = 0;
+    bool rec_valid = false;     // every iteration since the last reset was recorded
+    PackArgs psb{};             // packing of sigma_bar for the forward product
     double* res = nullptr;
     int* itab = nullptr;
     long long* ltab = nullptr;
@@ -88,7 +95,8 @@ void free_batch(admm_batch_t* h) {
     if (h->graph) cudaGraphDestroy(h->graph);
     void* ptrs[] = {h->H16T, h->Kpack, h->Zpack, h->Rpack, h->Wpack, h->kscale, h->V, h->S, h->G, h->Gt,
                     h->Ghat, h->R, h->Ppart, h->W, h->Sig, h->X, h->Y, h->zscale, h->rscale, h->wscale,
-                    h->kappa, h->res, h->itab, h->ltab, h->status, h->zmax};
+                    h->kappa, h->res, h->itab, h->ltab, h->status, h->zmax, h->rec_a, h->rec_w,
+                    h->Vb, h->Sb, h->Ghb, h->dG, h->rec_k, h->kbar, h->rbar};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (h->inner) admm_destroy(h->inner);
@@ -138,6 +146,23 @@ cudaError_t enqueue_iteration(admm_batch_t* h, cudaStream_t s) {
     if (e == cudaSuccess) e = cudaMemsetAsync(h->res, 0, 2 * sizeof(double) * h->B, s);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->zmax, 0, sizeof(unsigned) * h->P * h->B, s);
     if (e == cudaSuccess) e = launch_update(h->st, s);
+    if (e == cudaSuccess && h->st.rec_a) e = launch_rec_advance(h->st, s);
+    return e;
+}
+
+// one recorded iteration in reverse (st.bk selects the records)
+cudaError_t enqueue_backward(admm_batch_t* h, const StepArgs& st, cudaStream_t s) {
+    cudaError_t e = launch_bw_soft(st, s);
+    if (e == cudaSuccess) e = launch_pack(h->psb, h->P, s);
+    if (e == cudaSuccess) e = launch_gemm(h->mapH, h->mapZ, h->g1, s);
+    if (e == cudaSuccess) e = launch_bw_wbar(st, s);
+    if (e == cudaSuccess) e = launch_pack(h->pr, h->P, s);
+    if (e == cudaSuccess) e = launch_gemm(h->mapK, h->mapR, h->gk, s);
+    if (e == cudaSuccess) e = launch_bw_rbar(st, s);
+    if (e == cudaSuccess) e = launch_pack(h->pw, h->P, s);
+    if (e == cudaSuccess) e = launch_gemm(h->mapHT, h->mapW, h->g2, s);
+    if (e == cudaSuccess) e = launch_bw_state(st, s);
+    if (e == cudaSuccess) e = launch_bw_gtilde(st, s);
     return e;
 }
 
@@ -266,7 +291,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
     };
     std::vector<int> a1x(P), a1y(P), zero(P, 0), rows1(P), kb1p(P), rsr(P), a2x(P), a2y(P), rows2(P), kb2p(P),
         kkp(P), ksoff(P), pz(P), lenz(P), lenr(P), kidx(P);
-    std::vector<long long> xz(P), yz(P), xr(P), xy(P);
+    std::vector<long long> xz(P), yz(P), xr(P), xy(P), xs(P);
     for (int i = 0; i < row_blocks; ++i)
         for (int j = 0; j < col_blocks; ++j) {
             const int p = i * col_blocks + j;
@@ -289,6 +314,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
             yz[p] = static_cast<long long>(i) * Bn * n + co[j];
             xr[p] = static_cast<long long>(p) * Bn * mp;
             xy[p] = ro[i];
+            xs[p] = static_cast<long long>(p) * Bn * np;
         }
     std::vector<int> uto(col_blocks + 1, 0);
     for (int j = 0; j < col_blocks; ++j) uto[j + 1] = uto[j] + (co[j + 1] - co[j] + kUpdCols - 1) / kUpdCols;
@@ -303,7 +329,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
         lt.insert(lt.end(), x.begin(), x.end());
         return at;
     };
-    const size_t o_xz = lput(xz), o_yz = lput(yz), o_xr = lput(xr), o_xy = lput(xy);
+    const size_t o_xz = lput(xz), o_yz = lput(yz), o_xr = lput(xr), o_xy = lput(xy), o_xs = lput(xs);
     if (dalloc0(&h->itab, it.size()) != cudaSuccess || dalloc0(&h->ltab, lt.size()) != cudaSuccess)
         return bail(bfail(h, ADMM_ENOMEM, "device allocation failed for the batched tables"));
     if (cudaMemcpy(h->itab, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -432,6 +458,13 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
     py_ = pw_;
     py_.x_off = LT + o_xy;
     py_.x_bs = m;
+    PackArgs& psb_ = h->psb;
+    psb_ = pz_;
+    psb_.x = h->Sig;
+    psb_.x_off = LT + o_xs;
+    psb_.x_bs = np;
+    psb_.y = nullptr;
+    psb_.vmax = nullptr;
     // elementwise steps
     StepArgs& s_ = h->st;
     s_.m = h->m;
@@ -483,6 +516,8 @@ int admm_batch_reset(admm_batch_t* h, void* stream) {
     BCK(h, cudaMemsetAsync(h->Ghat, 0, static_cast<size_t>(h->N) * h->B * h->m * sizeof(float2), s));
     BCK(h, cudaMemsetAsync(h->zmax, 0, static_cast<size_t>(h->P) * h->B * sizeof(unsigned), s));
     BCK(h, cudaMemsetAsync(h->status, 0, sizeof(int), s));
+    if (h->rec_k) BCK(h, cudaMemsetAsync(h->rec_k, 0, sizeof(int), s));
+    h->rec_valid = h->rec_cap > 0;
     BCK(h, cudaStreamSynchronize(s));
     h->k = 0;
     h->broken = 0;
@@ -512,7 +547,80 @@ int admm_batch_iterate(admm_batch_t* h, int32_t iters, void* stream) {
     }
     for (int it = 0; it < iters; ++it) BCK(h, cudaGraphLaunch(h->exec, s));
     h->k += iters;
+    if (h->k > h->rec_cap) h->rec_valid = false;
     return ADMM_OK;
+}
+
+int admm_batch_record(admm_batch_t* h, int32_t iters) {
+    if (!h || iters < 0 || iters > (1 << 20)) return h ? bfail(h, ADMM_EINVAL, "bad record length") : ADMM_EINVAL;
+    BCK(h, cudaDeviceSynchronize());
+    void* old[] = {h->rec_a, h->rec_w, h->Vb, h->Sb, h->Ghb, h->dG, h->rec_k, h->kbar, h->rbar};
+    for (void* p : old)
+        if (p) cudaFree(p);
+    h->rec_a = h->rec_w = h->Vb = h->Sb = h->Ghb = h->dG = nullptr;
+    h->rec_k = nullptr;
+    h->kbar = h->rbar = nullptr;
+    h->rec_cap = 0;
+    h->rec_valid = false;
+    if (iters > 0) {
+        const size_t Bn = h->B;
+        if (dalloc0(&h->rec_a, static_cast<size_t>(iters) * Bn * h->n) != cudaSuccess ||
+            dalloc0(&h->rec_w, static_cast<size_t>(iters) * h->P * Bn * h->mpitch) != cudaSuccess ||
+            dalloc0(&h->Vb, Bn * h->n) != cudaSuccess || dalloc0(&h->Sb, static_cast<size_t>(h->M) * Bn * h->n) != cudaSuccess ||
+            dalloc0(&h->Ghb, static_cast<size_t>(h->N) * Bn * h->m) != cudaSuccess ||
+            dalloc0(&h->dG, Bn * h->m) != cudaSuccess || dalloc0(&h->rec_k, 1) != cudaSuccess ||
+            dalloc0(&h->kbar, Bn) != cudaSuccess || dalloc0(&h->rbar, Bn) != cudaSuccess)
+            return bfail(h, ADMM_ENOMEM, "no room to record %d iterations", iters);
+        h->rec_cap = iters;
+    }
+    StepArgs& st = h->st;
+    st.rec_a = h->rec_a;
+    st.rec_w = h->rec_w;
+    st.rec_k = h->rec_k;
+    st.rec_cap = h->rec_cap;
+    st.Vb = h->Vb;
+    st.Sb = h->Sb;
+    st.Ghb = h->Ghb;
+    st.dG = h->dG;
+    st.kbar = h->kbar;
+    st.rbar = h->rbar;
+    // the iteration graph is captured again with (or without) the recording launches
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    return admm_batch_reset(h, nullptr);
+}
+
+int admm_batch_backward(admm_batch_t* h, const void* dV, void* dG, double* dlambda, double* drho, void* stream) {
+    if (!h || !dV || !dG || !dlambda || !drho) return h ? bfail(h, ADMM_EINVAL, "NULL argument") : ADMM_EINVAL;
+    if (!h->rec_cap || !h->rec_valid || h->k < 1)
+        return bfail(h, ADMM_EINVAL, "no recorded iterations: admm_batch_record, then iterate at most the "
+                                     "recorded count from the reset state");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t Bn = h->B;
+    BCK(h, cudaMemcpyAsync(h->Vb, dV, Bn * h->n * sizeof(float2), cudaMemcpyDefault, s));
+    BCK(h, cudaMemsetAsync(h->Sb, 0, static_cast<size_t>(h->M) * Bn * h->n * sizeof(float2), s));
+    BCK(h, cudaMemsetAsync(h->Ghb, 0, static_cast<size_t>(h->N) * Bn * h->m * sizeof(float2), s));
+    BCK(h, cudaMemsetAsync(h->dG, 0, Bn * h->m * sizeof(float2), s));
+    BCK(h, cudaMemsetAsync(h->kbar, 0, Bn * sizeof(double), s));
+    BCK(h, cudaMemsetAsync(h->rbar, 0, Bn * sizeof(double), s));
+    StepArgs st = h->st;
+    for (int64_t k = h->k - 1; k >= 0; --k) {
+        st.bk = static_cast<int>(k);
+        BCK(h, enqueue_backward(h, st, s));
+    }
+    BCK(h, cudaMemcpyAsync(dG, h->dG, Bn * h->m * sizeof(float2), cudaMemcpyDefault, s));
+    std::vector<double> kb(Bn), rb(Bn);
+    BCK(h, cudaMemcpyAsync(kb.data(), h->kbar, Bn * sizeof(double), cudaMemcpyDeviceToHost, s));
+    BCK(h, cudaMemcpyAsync(rb.data(), h->rbar, Bn * sizeof(double), cudaMemcpyDeviceToHost, s));
+    const int code = check_status(h, s);
+    const double M = h->M, rho = h->rho;
+    for (size_t b = 0; b < Bn; ++b) {
+        dlambda[b] = kb[b] / (M * rho);
+        drho[b] = rb[b] - kb[b] * h->lam[b] / (M * rho * rho);
+    }
+    return code;
 }
 
 int admm_batch_status(admm_batch_t* h, void* stream) {

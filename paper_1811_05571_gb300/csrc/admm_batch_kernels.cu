@@ -380,8 +380,15 @@ __global__ void ghat_kernel(StepArgs a) {
         const size_t gi = (static_cast<size_t>(j) * a.B + b) * a.m + r0 + r;
         const float2 g = a.Gt[gi], w = a.W[e];
         a.Ghat[gi] = make_float2(g.x - a.rho * w.x, g.y - a.rho * w.y);
+        if (a.rec_w) {
+            const int k = *a.rec_k;
+            if (k < a.rec_cap) a.rec_w[static_cast<size_t>(k) * total + e] = w;
+        }
     }
 }
+
+// next recording slot (one thread, last in the iteration)
+__global__ void rec_advance_kernel(int* k) { *k += 1; }
 
 // out[b][e] = sum over splits and over the blocks meeting index e of part[sp][p][b][e - off[k]]:
 // by rows (forward: e in row block k = i, p = i N + q) or by columns (adjoint: k = j, p = q N + j)
@@ -457,8 +464,13 @@ __global__ void __launch_bounds__(kUpdThreads, MR <= 2 ? 4 : (MR <= 4 ? 3 : 2)) 
             mean.x += x.x;
             mean.y += x.y;
         }
-        const float2 vn = soft(make_float2(vo.x + mean.x * a.inv_M, vo.y + mean.y * a.inv_M), kappa);
+        const float2 av = make_float2(vo.x + mean.x * a.inv_M, vo.y + mean.y * a.inv_M);
+        const float2 vn = soft(av, kappa);
         *vp = vn;
+        if (a.rec_a) {
+            const int k = *a.rec_k;
+            if (k < a.rec_cap) a.rec_a[(static_cast<size_t>(k) * a.B + b) * a.n + c] = av;
+        }
         float2* spb = a.S + static_cast<size_t>(b) * a.n + c;
         const size_t s_i = static_cast<size_t>(a.B) * a.n;
         auto step = [&](float2 x, float2 so, float2* sp) {
@@ -506,6 +518,155 @@ __global__ void __launch_bounds__(kUpdThreads, MR <= 2 ? 4 : (MR <= 4 ? 3 : 2)) 
         float x = 0.f;
         for (int w = 0; w < kUpdThreads / 32; ++w) x = fmaxf(x, zred[threadIdx.x][w]);
         atomicMax(a.zmax + (threadIdx.x * a.N + j) * a.B + b, __float_as_uint(x));
+    }
+}
+
+// ---------------------------------------------------------------------------
+// reverse sweep of one recorded iteration (the adjoint of the iteration above;
+// complex adjoints x_bar = dL/dRe x + i dL/dIm x)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ double block_sum_d(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    double t = 0.0;
+    if (threadIdx.x == 0)
+        for (int w = 0; w < (blockDim.x >> 5); ++w) t += red[w];
+    __syncthreads();
+    return t;
+}
+
+// t = v_bar - sum_i s_bar_i (all that reaches v' = S(a)); a_bar = S'(a)^T t;
+// kappa_bar -= Re(conj(a_hat) t); sigma_bar_ij = s_bar_j^i + a_bar_j / M (into Sig);
+// v_bar <- sum_i s_bar_i + a_bar (the z_bar terms are added after the adjoint product)
+__global__ void bw_soft_kernel(StepArgs a) {
+    __shared__ double red[8];
+    const int b = blockIdx.y;
+    int j = 0;
+    while (a.upd_tile_off[j + 1] <= static_cast<int>(blockIdx.x)) ++j;
+    const int c_beg = a.col_off[j] + (blockIdx.x - a.upd_tile_off[j]) * kUpdCols;
+    const int c_end = min(a.col_off[j + 1], c_beg + kUpdCols);
+    const float kappa = a.kappa[b];
+    const float2* ak = a.rec_a + static_cast<size_t>(a.bk) * a.B * a.n;
+    float kb = 0.f;
+    for (int c = c_beg + threadIdx.x; c < c_end; c += blockDim.x) {
+        const int cl = c - a.col_off[j];
+        const size_t vi = static_cast<size_t>(b) * a.n + c;
+        float2 ssum = make_float2(0.f, 0.f);
+        for (int i = 0; i < a.M; ++i) {
+            const float2 x = a.Sb[static_cast<size_t>(i) * a.B * a.n + vi];
+            ssum.x += x.x;
+            ssum.y += x.y;
+        }
+        const float2 vb = a.Vb[vi];
+        const float2 t = make_float2(vb.x - ssum.x, vb.y - ssum.y);
+        const float2 av = ak[vi];
+        const float mag = hypotf(av.x, av.y);
+        float2 abar = make_float2(0.f, 0.f);
+        if (mag > kappa) {
+            const float hx = av.x / mag, hy = av.y / mag;
+            const float proj = hx * t.x + hy * t.y;   // Re(conj(a_hat) t)
+            const float f = kappa / mag;
+            abar = make_float2(t.x - f * (t.x - hx * proj), t.y - f * (t.y - hy * proj));
+            kb -= proj;
+        }
+        a.Vb[vi] = make_float2(ssum.x + abar.x, ssum.y + abar.y);
+        for (int i = 0; i < a.M; ++i) {
+            const float2 x = a.Sb[static_cast<size_t>(i) * a.B * a.n + vi];
+            float2* sg = const_cast<float2*>(a.Sig) + (static_cast<size_t>(i * a.N + j) * a.B + b) * a.npitch + cl;
+            *sg = make_float2(x.x + abar.x * a.inv_M, x.y + abar.y * a.inv_M);
+        }
+    }
+    const double tot = block_sum_d(kb, red);
+    if (threadIdx.x == 0) atomicAdd(a.kbar + b, tot);
+}
+
+// w_bar = H sigma_bar (split partials) - rho ghat_bar (into R); rho_bar -= Re(w^H ghat_bar)
+__global__ void bw_wbar_kernel(StepArgs a) {
+    __shared__ double red[8];
+    const int b = blockIdx.y, p = blockIdx.x;
+    const int i = p / a.N, j = p - (p / a.N) * a.N;
+    const int r0 = a.row_off[i], mi = a.row_off[i + 1] - r0;
+    const size_t pb = static_cast<size_t>(p) * a.B + b;
+    const float2* wk = a.rec_w + (static_cast<size_t>(a.bk) * a.P * a.B + pb) * a.mpitch;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < mi; r += blockDim.x) {
+        float2 hs = make_float2(0.f, 0.f);
+        for (int sp = 0; sp < a.splits; ++sp) {
+            const float2 x = a.Ppart[(static_cast<size_t>(sp) * a.P * a.B + pb) * a.mpitch + r];
+            hs.x += x.x;
+            hs.y += x.y;
+        }
+        const float2 gb = a.Ghb[(static_cast<size_t>(j) * a.B + b) * a.m + r0 + r];
+        a.R[pb * a.mpitch + r] = make_float2(hs.x - a.rho * gb.x, hs.y - a.rho * gb.y);
+        const float2 w = wk[r];
+        acc -= static_cast<double>(w.x) * gb.x + static_cast<double>(w.y) * gb.y;
+    }
+    const double tot = block_sum_d(acc, red);
+    if (threadIdx.x == 0) atomicAdd(a.rbar + b, tot);
+}
+
+// r_bar = K^{-1} w_bar (in W); rho_bar -= Re(w^H r_bar); gt_bar = ghat_bar + r_bar (into Gt)
+__global__ void bw_rbar_kernel(StepArgs a) {
+    __shared__ double red[8];
+    const int b = blockIdx.y, p = blockIdx.x;
+    const int i = p / a.N, j = p - (p / a.N) * a.N;
+    const int r0 = a.row_off[i], mi = a.row_off[i + 1] - r0;
+    const size_t pb = static_cast<size_t>(p) * a.B + b;
+    const float2* wk = a.rec_w + (static_cast<size_t>(a.bk) * a.P * a.B + pb) * a.mpitch;
+    double acc = 0.0;
+    for (int r = threadIdx.x; r < mi; r += blockDim.x) {
+        const float2 rb = a.W[pb * a.mpitch + r];
+        const float2 w = wk[r];
+        acc -= static_cast<double>(w.x) * rb.x + static_cast<double>(w.y) * rb.y;
+        const size_t gi = (static_cast<size_t>(j) * a.B + b) * a.m + r0 + r;
+        const float2 gb = a.Ghb[gi];
+        a.Gt[gi] = make_float2(gb.x + rb.x, gb.y + rb.y);
+    }
+    const double tot = block_sum_d(acc, red);
+    if (threadIdx.x == 0) atomicAdd(a.rbar + b, tot);
+}
+
+// z_bar_ij = -H_ij^H r_bar_ij (Sig holds H^H r_bar): v_bar += sum_i z_bar, s_bar_i = -z_bar
+__global__ void bw_state_kernel(StepArgs a) {
+    const int b = blockIdx.y;
+    int j = 0;
+    while (a.upd_tile_off[j + 1] <= static_cast<int>(blockIdx.x)) ++j;
+    const int c_beg = a.col_off[j] + (blockIdx.x - a.upd_tile_off[j]) * kUpdCols;
+    const int c_end = min(a.col_off[j + 1], c_beg + kUpdCols);
+    for (int c = c_beg + threadIdx.x; c < c_end; c += blockDim.x) {
+        const int cl = c - a.col_off[j];
+        const size_t vi = static_cast<size_t>(b) * a.n + c;
+        float2 vb = a.Vb[vi];
+        for (int i = 0; i < a.M; ++i) {
+            const float2 x = a.Sig[(static_cast<size_t>(i * a.N + j) * a.B + b) * a.npitch + cl];
+            vb.x -= x.x;
+            vb.y -= x.y;
+            a.Sb[static_cast<size_t>(i) * a.B * a.n + vi] = x;
+        }
+        a.Vb[vi] = vb;
+    }
+}
+
+// gt_ij = g_i - sum_{q != j} ghat_iq: g_bar_i += sum_j gt_bar_ij, ghat_bar_iq = -sum_{j != q} gt_bar_ij
+__global__ void bw_gtilde_kernel(StepArgs a) {
+    const size_t total = static_cast<size_t>(a.B) * a.m;
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        float2 tot = make_float2(0.f, 0.f);
+        for (int j = 0; j < a.N; ++j) {
+            const float2 x = a.Gt[j * total + e];
+            tot.x += x.x;
+            tot.y += x.y;
+        }
+        float2 g = a.dG[e];
+        a.dG[e] = make_float2(g.x + tot.x, g.y + tot.y);
+        for (int q = 0; q < a.N; ++q) {
+            const float2 x = a.Gt[q * total + e];
+            a.Ghb[q * total + e] = make_float2(x.x - tot.x, x.y - tot.y);
+        }
     }
 }
 
@@ -571,6 +732,10 @@ __global__ void pack_kinv_kernel(const float2* __restrict__ kinv, const long lon
 
 }  // namespace
 
+static int grid_of(size_t total) {
+    return static_cast<int>(std::max<size_t>(1, std::min<size_t>(8192, (total + 255) / 256)));
+}
+
 cudaError_t prepare_gemm() {
     return cudaFuncSetAttribute(bgemm_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
 }
@@ -585,10 +750,6 @@ cudaError_t launch_gemm(const CUtensorMap& A, const CUtensorMap& B, const GemmAr
 cudaError_t launch_pack(const PackArgs& a, int nprob, cudaStream_t s) {
     pack_kernel<<<dim3(nprob, a.B), 256, 0, s>>>(a);
     return cudaGetLastError();
-}
-
-static int grid_of(size_t total) {
-    return static_cast<int>(std::max<size_t>(1, std::min<size_t>(8192, (total + 255) / 256)));
 }
 
 cudaError_t launch_residual_r(const StepArgs& a, cudaStream_t s) {
@@ -615,6 +776,37 @@ cudaError_t launch_update(const StepArgs& a, cudaStream_t s) {
     else if (a.M <= 4) update_kernel<4><<<grid, kUpdThreads, 0, s>>>(a);
     else if (a.M <= 8) update_kernel<8><<<grid, kUpdThreads, 0, s>>>(a);
     else update_kernel<kUpdRegs><<<grid, kUpdThreads, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rec_advance(const StepArgs& a, cudaStream_t s) {
+    rec_advance_kernel<<<1, 1, 0, s>>>(a.rec_k);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bw_soft(const StepArgs& a, cudaStream_t s) {
+    bw_soft_kernel<<<dim3(a.upd_tiles, a.B), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bw_wbar(const StepArgs& a, cudaStream_t s) {
+    bw_wbar_kernel<<<dim3(a.P, a.B), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bw_rbar(const StepArgs& a, cudaStream_t s) {
+    bw_rbar_kernel<<<dim3(a.P, a.B), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bw_state(const StepArgs& a, cudaStream_t s) {
+    bw_state_kernel<<<dim3(a.upd_tiles, a.B), 256, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bw_gtilde(const StepArgs& a, cudaStream_t s) {
+    const size_t total = static_cast<size_t>(a.B) * a.m;
+    bw_gtilde_kernel<<<grid_of(total), 256, 0, s>>>(a);
     return cudaGetLastError();
 }
 

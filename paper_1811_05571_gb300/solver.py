@@ -196,6 +196,17 @@ class BatchSolver:
         B.admm_batch_adjoint(self.h, _contig(Y), X, self.stream)
         return X
 
+    def record(self, iters: int) -> None:
+        """Record the next `iters` iterations for backward() (resets the state)."""
+        B.admm_batch_record(self.h, int(iters))
+
+    def backward(self, dV):
+        """(dG, dlambda, drho) of a loss of the current image, given dL/dv (per scene)."""
+        t = self._torch
+        dG = t.empty((self.batch, self.m), dtype=t.complex64, device="cuda")
+        dl, dr = B.admm_batch_backward(self.h, self.batch, _contig(dV), dG, self.stream)
+        return dG, dl, dr
+
     def status(self) -> int:
         return B.admm_batch_status(self.h, self.stream)
 
@@ -212,4 +223,43 @@ class BatchSolver:
             self.close()
         except Exception:
             pass
+
+
+def _unrolled_function():
+    import torch
+
+    class _Unrolled(torch.autograd.Function):
+        """v = ADMM_K(G) for every scene of a BatchSolver; backward runs the
+        library's reverse sweep and leaves dL/dlambda and dL/drho per scene in
+        ``solver.last_param_grads``."""
+
+        @staticmethod
+        def forward(ctx, G, solver, iters):
+            solver.record(int(iters))
+            solver.set_g(G.detach().to(torch.complex64).contiguous())
+            solver.iterate(int(iters))
+            ctx.solver = solver
+            return solver.v()
+
+        @staticmethod
+        def backward(ctx, dV):
+            dG, dl, dr = ctx.solver.backward(dV.to(torch.complex64).contiguous())
+            ctx.solver.last_param_grads = (dl, dr)
+            return dG, None, None
+
+    return _Unrolled
+
+
+class UnrolledADMM:
+    """``UnrolledADMM.apply(G, solver, iters)``: the images after `iters`
+    iterations from the zero state as a differentiable function of the
+    measurements G (batch x m); see BatchSolver.record / backward."""
+
+    _fn = None
+
+    @classmethod
+    def apply(cls, G, solver, iters):
+        if cls._fn is None:
+            cls._fn = _unrolled_function()
+        return cls._fn.apply(G, solver, iters)
 
