@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12,
                     help="iterations per split in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-adjoint", action="store_true",
+                    help="skip the differentiable workload (forward with recording + reverse sweep)")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched shared-H workload (tensor-core GEMMs)")
     ap.add_argument("--batch", type=int, default=256, help="scenes of the batched workload")
@@ -479,6 +481,49 @@ def batched_shared_h(pkg, stream, dev, barrier, p, peaks, batch: int = 256, step
     return out
 
 
+def differentiable(pkg, stream, dev, barrier, K: int = 100) -> dict:
+    """The differentiable workload: H 2048 x 16384, 16 scenes of 64 nonzeros
+    (seeds 500-515), consensus over 8 row blocks, loss sum_b ||v_K - u_b||^2.
+    Times K recorded forward iterations and the reverse sweep (CUDA events on
+    the launching stream; the loss gradient dL/dv is formed on the device)."""
+    import numpy as np
+    import torch
+    import synth
+    p = synth.gaussian_problem(2048, 16384, 64, seed=5)
+    G, U, lam = synth.shared_h_scenes(p.H, 16, seed0=500, nnz=64)
+    with torch.cuda.stream(stream):
+        bs = pkg.BatchSolver(torch.from_numpy(p.H_c64()).to(dev), 8, 1, lam, 1.0, stream=stream)
+        G_d = torch.from_numpy(G.astype(np.complex64)).to(dev)
+        U_d = torch.from_numpy(U.astype(np.complex64)).to(dev)
+
+    def once():
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        bs.record(K)
+        bs.set_g(G_d)
+        barrier()
+        a.record(stream)
+        bs.iterate(K)
+        b.record(stream)
+        with torch.cuda.stream(stream):
+            dV = (2.0 * (bs.v() - U_d)).contiguous()
+        bs.backward(dV)
+        c.record(stream)
+        barrier()
+        return a.elapsed_time(b), b.elapsed_time(c)
+
+    once()
+    fw, bw = zip(*[once() for _ in range(3)])
+    if bs.status() != 0:
+        raise RuntimeError("device status after the differentiable workload")
+    info = bs.info()
+    bs.close()
+    fwd, bwd = statistics.median(fw), statistics.median(bw)
+    return {"workload": "gaussian 2048x16384 CN(0,1/2048), 16 scenes x 64 nonzeros (seeds 500-515), "
+                        "consensus 8x1, K = 100, loss sum ||v_K - u||^2, FP16 H",
+            "forward_ms": fwd, "backward_ms": bwd, "gradients_per_s": 16 / ((fwd + bwd) / 1e3),
+            "backward_over_forward": bwd / fwd, "tensor_flops_per_iter": info["tensor_flops"]}
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -612,6 +657,9 @@ def run_ours(args) -> None:
     batched = None
     if not args.no_batch:
         batched = batched_shared_h(pkg, stream, dev, barrier, p, peaks=load_peaks(), batch=args.batch)
+    diff = None
+    if not args.no_adjoint:
+        diff = differentiable(pkg, stream, dev, barrier)
 
     phases = None
     if args.trace > 0:
@@ -689,6 +737,8 @@ def run_ours(args) -> None:
         line["mixed_precision_large"] = large
     if batched is not None:
         line["batched_shared_h"] = batched
+    if diff is not None:
+        line["differentiable"] = diff
     if phases is not None:
         line["phases"] = phases
     for s in solvers:
