@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12,
                     help="iterations per split in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-uneven", action="store_true",
+                    help="skip the 48 uneven problems workload")
     ap.add_argument("--no-adjoint", action="store_true",
                     help="skip the differentiable workload (forward with recording + reverse sweep)")
     ap.add_argument("--no-batch", action="store_true",
@@ -481,6 +483,49 @@ def batched_shared_h(pkg, stream, dev, barrier, p, peaks, batch: int = 256, step
     return out
 
 
+def uneven_problems(pkg, stream, dev, barrier, peaks, iters: int = 300) -> dict:
+    """48 Gaussian problems of uneven sizes (synth.uneven_problem_sizes), each
+    with its own handle (consensus over ceil(m/256) row blocks, lambda 0.05
+    max|H^H g|, rho 1), each run for `iters` iterations as one persistent
+    launch, all on one stream: total time with CUDA events, problem-iterations
+    per second and the algorithmic bytes moved per second."""
+    import torch
+    import synth
+    sizes = synth.uneven_problem_sizes()
+    solvers, alg = [], 0.0
+    with torch.cuda.stream(stream):
+        for m, n, nnz, M, seed in sizes:
+            H, g, _, lam = synth.gaussian_problem_device(m, n, nnz, seed, device=dev)
+            s = pkg.Solver(H, g, M, 1, lam, 1.0, stream=stream)
+            info = s.info()
+            alg += 2 * info["h_bytes"] + info["factor_bytes"] + (2 * M + 2) * n * 8
+            solvers.append(s)
+            del H, g
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    for s in solvers:
+        s.iterate(3)
+    barrier()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for s in solvers:
+        s.iterate(iters)
+    b.record(stream)
+    barrier()
+    ms = a.elapsed_time(b)
+    for s in solvers:
+        if s.status() != 0:
+            raise RuntimeError("device status after the uneven problems")
+        s.close()
+    elems = sum(m * n for m, n, _, _, _ in sizes)
+    return {"workload": f"{len(sizes)} Gaussian problems, m in [256, 4096], n in [4096, 32768] "
+                        f"(log-uniform, seeds 1000-{999 + len(sizes)}), consensus ceil(m/256)x1, "
+                        f"{iters} iterations each, one launch per problem",
+            "problems": len(sizes), "elements": elems, "ms": ms,
+            "problem_iterations_per_s": len(sizes) * iters / (ms / 1e3),
+            "alg_gbs": alg * iters / (ms / 1e3) / 1e9, "frac": alg * iters / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+
+
 def differentiable(pkg, stream, dev, barrier, K: int = 100) -> dict:
     """The differentiable workload: H 2048 x 16384, 16 scenes of 64 nonzeros
     (seeds 500-515), consensus over 8 row blocks, loss sum_b ||v_K - u_b||^2.
@@ -660,6 +705,9 @@ def run_ours(args) -> None:
     diff = None
     if not args.no_adjoint:
         diff = differentiable(pkg, stream, dev, barrier)
+    uneven = None
+    if not args.no_uneven:
+        uneven = uneven_problems(pkg, stream, dev, barrier, peaks=load_peaks())
 
     phases = None
     if args.trace > 0:
@@ -739,6 +787,8 @@ def run_ours(args) -> None:
         line["batched_shared_h"] = batched
     if diff is not None:
         line["differentiable"] = diff
+    if uneven is not None:
+        line["uneven_problems"] = uneven
     if phases is not None:
         line["phases"] = phases
     for s in solvers:

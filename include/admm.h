@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define ADMM_ABI_VERSION 2
+#define ADMM_ABI_VERSION 3
 
 /* status codes */
 #define ADMM_OK            0  /* success */
@@ -114,6 +114,7 @@ typedef struct admm_info {
     int32_t h_fp16;           /* 1 while the iterations stream the FP16 copy of H */
     int32_t h16_ready;        /* 1 once the FP16 copy and its factors exist */
     int64_t h16_bytes;        /* bytes of H streamed by one pass in FP16 (m * n * 4), 0 if none */
+    int64_t l2_keep_bytes;    /* current ADMM_OPT_L2_KEEP_BYTES (admm_tune may change it) */
 } admm_info_t;
 
 /* Launch plan of the iteration kernel, computed on the host (admm_plan). */
@@ -271,6 +272,12 @@ int admm_get_info(const admm_t* h, admm_info_t* info);
 /* Set an ADMM_OPT_* option. */
 int admm_set_option(admm_t* h, int32_t option, int64_t value);
 
+/* Autotune the L2 policy of the current mode (complex64 or FP16 H): time
+ * single-iteration launches with candidate ADMM_OPT_L2_KEEP_BYTES values
+ * (0 to 96 MiB, at most one pass of H) and keep the fastest.  Leaves the
+ * handle reset (admm_reset).  Synchronises. */
+int admm_tune(admm_t* h, void* stream);
+
 /* Phase trace of the last launch (needs ADMM_OPT_TRACE_ITERS > 0): for CTA 0
  * and the last CTA, and for each of the first min(cap, trace length)
  * iterations, 8 %globaltimer stamps in nanoseconds: iteration start, first
@@ -376,6 +383,12 @@ int admm_batch_forward(admm_batch_t* h, const void* X, void* Y, void* stream);
 
 /* X_b = Hq^H Y_b for every scene (the adjoint product of the u-step).  Synchronises. */
 int admm_batch_adjoint(admm_batch_t* h, const void* Y, void* X, void* stream);
+
+/* Autotune: time the forward product with every K split the partial-product
+ * buffer allows (powers of two, at least 4 K blocks of 64 per split) on the
+ * current state and keep the fastest for later iterations (the graph is
+ * captured again).  The state is not changed.  Synchronises. */
+int admm_batch_tune(admm_batch_t* h, void* stream);
 
 /* Record the next `iters` iterations for admm_batch_backward: per iteration
  * the shrinkage arguments a = mean_i(u^i + s^i) (batch x n) and the factor

@@ -21,7 +21,7 @@ ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED = 5, 6, 7, 8
 ADMM_C64, ADMM_C128 = 0, 1
 ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS = 1, 2, 3, 4
 ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16 = 5, 6
-ABI_VERSION = 2
+ABI_VERSION = 3
 
 
 class AdmmInfo(ctypes.Structure):
@@ -33,7 +33,7 @@ class AdmmInfo(ctypes.Structure):
                 ("num_sms", c_int32), ("h_bytes", c_int64), ("factor_bytes", c_int64),
                 ("state_bytes", c_int64), ("setup_gram_ms", c_double),
                 ("setup_factor_ms", c_double), ("h_fp16", c_int32), ("h16_ready", c_int32),
-                ("h16_bytes", c_int64)]
+                ("h16_bytes", c_int64), ("l2_keep_bytes", c_int64)]
 
     def as_dict(self) -> dict:
         return {name.rstrip("_"): getattr(self, name) for name, _ in self._fields_}
@@ -94,6 +94,7 @@ SIGNATURES = {
     "admm_get_trace": (c_int32, [c_void_p, ctypes.POINTER(c_int64), c_int32,
                                  ctypes.POINTER(c_int32), c_void_p]),
     "admm_status": (c_int32, [c_void_p, c_void_p]),
+    "admm_tune": (c_int32, [c_void_p, c_void_p]),
     "admm_destroy": (None, [c_void_p]),
     "admm_solve_small_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32,
                                            c_double, c_double, c_int32, c_void_p, c_void_p]),
@@ -108,6 +109,7 @@ SIGNATURES = {
     "admm_batch_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "admm_batch_status": (c_int32, [c_void_p, c_void_p]),
     "admm_batch_record": (c_int32, [c_void_p, c_int32]),
+    "admm_batch_tune": (c_int32, [c_void_p, c_void_p]),
     "admm_batch_backward": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
                                       ctypes.POINTER(c_double), c_void_p]),
     "admm_batch_get_info": (c_int32, [c_void_p, ctypes.POINTER(AdmmBatchInfo)]),
@@ -389,4 +391,12 @@ def admm_batch_backward(h: int, batch: int, dV, dG, stream=None):
     dr = (c_double * batch)()
     _bcheck(load().admm_batch_backward(h, _ptr(dV), _ptr(dG), dl, dr, _stream(stream)), h)
     return np.array(dl[:]), np.array(dr[:])
+
+
+def admm_batch_tune(h: int, stream=None) -> None:
+    _bcheck(load().admm_batch_tune(h, _stream(stream)), h)
+
+
+def admm_tune(h: int, stream=None) -> None:
+    _check(load().admm_tune(h, _stream(stream)), h)
 

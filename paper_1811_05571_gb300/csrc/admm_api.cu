@@ -1079,6 +1079,7 @@ int admm_get_info(const admm_t* h, admm_info_t* info) {
     info->h_fp16 = h->use_f16;
     info->h16_ready = h->H16 ? 1 : 0;
     info->h16_bytes = h->H16 ? h->m * h->n * 4 : 0;
+    info->l2_keep_bytes = h->l2_keep_bytes;
     return ADMM_OK;
 }
 
@@ -1133,6 +1134,47 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
         default:
             return fail(h, ADMM_EINVAL, "unknown option %d", option);
     }
+}
+
+int admm_tune(admm_t* h, void* stream) {
+    if (!h) return ADMM_EINVAL;
+    if (h->broken) return fail(h, ADMM_ECUDA, "handle is in an error state; call admm_reset");
+    cudaStream_t st = as_stream(stream);
+    const int64_t mib = 1LL << 20;
+    const int64_t cand[] = {0, 16 * mib, 32 * mib, 44 * mib, 52 * mib, 64 * mib, 80 * mib, 96 * mib};
+    const int64_t hb = h->m * h->plan.ld * (h->use_f16 ? 4 : 8);
+    cudaEvent_t e0, e1;
+    CK(h, cudaEventCreate(&e0));
+    CK(h, cudaEventCreate(&e1));
+    int64_t best = h->l2_keep_bytes;
+    float best_ms = 1e30f;
+    int code = ADMM_OK;
+    for (int64_t keep : cand) {
+        if (keep > hb) break;
+        h->l2_keep_bytes = keep;
+        for (int r = 0; r < 2 && code == ADMM_OK; ++r) code = run_kernel(h, 1, 0, 0.0, 0.0, st);
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 5 && code == ADMM_OK; ++r) code = run_kernel(h, 1, 0, 0.0, 0.0, st);
+        cudaEventRecord(e1, st);
+        if (code) break;
+        cudaEventSynchronize(e1);
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = keep;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->l2_keep_bytes = best;
+    if (code) return code;
+    code = device_status(h, st);
+    if (code) return code;
+    code = zero_state(h, st);
+    if (code) return code;
+    CK(h, cudaStreamSynchronize(st));
+    return ADMM_OK;
 }
 
 int admm_get_trace(admm_t* h, int64_t* out, int32_t cap, int32_t* count, void* stream) {

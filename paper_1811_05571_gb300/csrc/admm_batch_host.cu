@@ -19,6 +19,8 @@ namespace {
 
 thread_local std::string g_batch_error;
 
+constexpr int kTuneMaxSplits = 32;
+
 int round_up(int64_t x, int64_t q) { return static_cast<int>((x + q - 1) / q * q); }
 
 }  // namespace
@@ -43,6 +45,7 @@ struct admm_batch {
     int* rec_k = nullptr;
     double *kbar = nullptr, *rbar = nullptr;
     int rec_cap = 0;
+    int max_splits = 1;         // K splits the partial-product buffer holds (autotuner range)
     bool rec_valid = false;     // every iteration since the last reset was recorded
     PackArgs psb{};             // packing of sigma_bar for the forward product
     double* res = nullptr;
@@ -254,6 +257,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int kb1 = h->kz / kTileK;
     h->splits1 = std::max(1, std::min(kb1 / 8, (2 * sms + P * mt1 * ntiles - 1) / (P * mt1 * ntiles)));
+    h->max_splits = std::max(h->splits1, std::max(1, std::min(kTuneMaxSplits, kb1 / 4)));
     const size_t mp = h->mpitch, np = h->npitch;
     bool ok = cudaMalloc(&h->H16T, static_cast<size_t>(h->ld) * m * 4) == cudaSuccess &&
               dalloc0(reinterpret_cast<unsigned short**>(&h->Kpack), static_cast<size_t>(P) * h->mimax * h->kr) ==
@@ -271,7 +275,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
               dalloc0(&h->Gt, static_cast<size_t>(col_blocks) * Bn * m) == cudaSuccess &&
               dalloc0(&h->Ghat, static_cast<size_t>(col_blocks) * Bn * m) == cudaSuccess &&
               dalloc0(&h->R, static_cast<size_t>(P) * Bn * mp) == cudaSuccess &&
-              dalloc0(&h->Ppart, static_cast<size_t>(h->splits1) * P * Bn * mp) == cudaSuccess &&
+              dalloc0(&h->Ppart, static_cast<size_t>(h->max_splits) * P * Bn * mp) == cudaSuccess &&
               dalloc0(&h->W, static_cast<size_t>(P) * Bn * mp) == cudaSuccess &&
               dalloc0(&h->Sig, static_cast<size_t>(P) * Bn * np) == cudaSuccess &&
               dalloc0(&h->zscale, static_cast<size_t>(P) * Bn) == cudaSuccess &&
@@ -549,6 +553,55 @@ int admm_batch_iterate(admm_batch_t* h, int32_t iters, void* stream) {
     h->k += iters;
     if (h->k > h->rec_cap) h->rec_valid = false;
     return ADMM_OK;
+}
+
+int admm_batch_tune(admm_batch_t* h, void* stream) {
+    if (!h) return ADMM_EINVAL;
+    if (h->broken) return bfail(h, ADMM_ECUDA, "handle is in an error state; call admm_batch_reset");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // candidates: powers of two up to the buffer's capacity, each with at least 4 K blocks per split
+    const int kb1 = h->kz / kTileK;
+    cudaEvent_t e0, e1;
+    BCK(h, cudaEventCreate(&e0));
+    BCK(h, cudaEventCreate(&e1));
+    int best = h->splits1;
+    float best_ms = 1e30f;
+    // the packed operand of the current state is what the timed products read
+    BCK(h, launch_pack(h->pz, h->P, s));
+    for (int sp = 1; sp <= h->max_splits; sp *= 2) {
+        if (kb1 / sp < 4 && sp > 1) break;
+        GemmArgs g = h->g1;
+        g.splits = sp;
+        g.kb_per_split = (kb1 + sp - 1) / sp;
+        cudaError_t e = launch_gemm(h->mapH, h->mapZ, g, s);   // warm
+        if (e == cudaSuccess) e = cudaEventRecord(e0, s);
+        for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_gemm(h->mapH, h->mapZ, g, s);
+        if (e == cudaSuccess) e = cudaEventRecord(e1, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            h->broken = 1;
+            return bfail(h, ADMM_ECUDA, "tuning launch failed: %s", cudaGetErrorString(e));
+        }
+        if (ms < best_ms) {
+            best_ms = ms;
+            best = sp;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->splits1 = best;
+    h->g1.splits = best;
+    h->g1.kb_per_split = (kb1 + best - 1) / best;
+    h->st.splits = best;
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    return check_status(h, s);
 }
 
 int admm_batch_record(admm_batch_t* h, int32_t iters) {

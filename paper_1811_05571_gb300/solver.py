@@ -113,6 +113,11 @@ class Solver:
     def set_option(self, option: int, value: int) -> None:
         B.admm_set_option(self.h, int(option), int(value))
 
+    def tune(self) -> int:
+        """Autotune the L2 keep size of the current mode; resets the state. Returns the bytes kept."""
+        B.admm_tune(self.h, self.stream)
+        return int(self.info()["l2_keep_bytes"])
+
     def use_fp16(self, on: bool = True) -> None:
         """Stream the FP16 copy of H (built on first use) or the complex64 H."""
         B.admm_set_option(self.h, B.ADMM_OPT_H_FP16, 1 if on else 0)
@@ -195,6 +200,11 @@ class BatchSolver:
         X = t.empty((self.batch, self.n), dtype=t.complex64, device="cuda")
         B.admm_batch_adjoint(self.h, _contig(Y), X, self.stream)
         return X
+
+    def tune(self) -> int:
+        """Pick the fastest K split of the forward product; returns it."""
+        B.admm_batch_tune(self.h, self.stream)
+        return int(self.info()["splits"])
 
     def record(self, iters: int) -> None:
         """Record the next `iters` iterations for backward() (resets the state)."""

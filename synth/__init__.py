@@ -22,4 +22,5 @@ from .workloads import (  # noqa: F401
     CONFIG3,
     gaussian_problem_device,
     shared_h_scenes,
+    uneven_problem_sizes,
 )

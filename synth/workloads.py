@@ -315,3 +315,18 @@ def shared_h_scenes(H: np.ndarray, count: int, seed0: int, kind: str = "sparse",
         G[b] = round_to_c64(noisy_measurements(H, U[b], rng, snr_db))
         lam.append(lambda_from_fraction(H, G[b], lam_frac))
     return G, U, lam
+
+
+def uneven_problem_sizes(count: int = 48, seed0: int = 1000):
+    """Sizes of the uneven multi-problem workload: problem p draws, from
+    default_rng(seed0 + p), m = round(exp U[ln 256, ln 4096]) and
+    n = round(exp U[ln 4096, ln 32768]); nnz = max(1, round(m / 16)) and
+    ceil(m / 256) row blocks.  Returns a list of (m, n, nnz, row_blocks, seed)."""
+    out = []
+    for p in range(count):
+        rng = np.random.default_rng(seed0 + p)
+        m = int(round(np.exp(rng.uniform(np.log(256), np.log(4096)))))
+        n = int(round(np.exp(rng.uniform(np.log(4096), np.log(32768)))))
+        out.append((m, n, max(1, int(round(m / 16))), int(np.ceil(m / 256)), seed0 + p))
+    return out
+

@@ -33,7 +33,7 @@ def test_library_loads_and_exports_every_declared_symbol(cuda_lib):
 
 def test_abi_version_and_strerror(cuda_lib):
     import paper_1811_05571_gb300 as P
-    assert P.admm_abi_version() == P.ABI_VERSION == 2
+    assert P.admm_abi_version() == P.ABI_VERSION == 3
     for code in range(0, 9):
         assert P.admm_strerror(code)
     assert P.admm_strerror(99) == "unknown status"

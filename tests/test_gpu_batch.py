@@ -123,3 +123,18 @@ def test_batch_scenes_are_independent():
     for k, b in enumerate((0, 65, 69)):
         ref = V70[b].astype(np.complex128)
         assert np.linalg.norm(V3[k] - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+def test_autotuned_split_keeps_parity():
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(256, 4096, 16, seed=0)
+    G, _, lam = synth.shared_h_scenes(p.H, 6, seed0=40, nnz=16)
+    bs = P.BatchSolver(torch.from_numpy(p.H_c64()).cuda(), 4, 1, lam, 1.0)
+    bs.set_g(torch.from_numpy(G.astype(np.complex64)).cuda())
+    sp = bs.tune()
+    assert sp >= 1 and (sp & (sp - 1)) == 0
+    bs.iterate(300)
+    V = bs.v().cpu().numpy()
+    res = bs.residuals()
+    bs.close()
+    _check_scene(V, res, Q.dequantized(p.H), G, lam, 4, 1, 1.0, 300, 2)

@@ -322,3 +322,15 @@ def test_several_handles_with_different_plans_coexist():
     for s in (a, b, c, a, c, b):
         s.iterate(3)
         assert s.status() == 0
+
+
+def test_autotuned_l2_policy_keeps_parity(cra):
+    import paper_1811_05571_gb300 as P
+    s = P.Solver(torch.from_numpy(cra.H_c64()).cuda(), torch.from_numpy(cra.g_c64()).cuda(), 4, 4,
+                 cra.lam, cra.rho)
+    keep = s.tune()
+    assert keep in [x << 20 for x in (0, 16, 32, 44, 52, 64, 80, 96)]
+    assert s.info()["iterations"] == 0
+    s.iterate(50)
+    assert s.status() == 0
+    compare_all(s, oracle_run(cra, 4, 4, 50), 4, 4)
