@@ -77,6 +77,11 @@ extern "C" {
                                      rows in the opposite order) finds them in L2; the rest
                                      of H and the factors are loaded evict_first (default
                                      52 MiB; 0 = no L2 policy hints) */
+#define ADMM_OPT_L2_PREFETCH_BYTES 7  /* bytes of H per pass prefetched into L2 (TMA
+                                     prefetch, no shared memory) while the previous pass
+                                     ends and the grid waits at its barriers: the rows the
+                                     next pass reads right after its L2-resident head
+                                     (default 0) */
 #define ADMM_OPT_H_FP16        6  /* 1: stream an FP16 copy of H (half the bytes per pass);
                                      0: stream the complex64 H (the default).  The first 1
                                      builds the copy: every 64-row group g of H gets the scale

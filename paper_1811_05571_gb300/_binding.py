@@ -20,7 +20,7 @@ ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ENOTPD = 0, 1, 2, 3, 4
 ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED = 5, 6, 7, 8
 ADMM_C64, ADMM_C128 = 0, 1
 ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS = 1, 2, 3, 4
-ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16 = 5, 6
+ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ADMM_OPT_L2_PREFETCH_BYTES = 5, 6, 7
 ABI_VERSION = 3
 
 

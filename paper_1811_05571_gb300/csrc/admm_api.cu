@@ -68,6 +68,7 @@ struct admm_problem {
     int64_t k = 0;       // iterations completed (host mirror)
     int pending = 0;     // the last launch's final residual record has not been summed yet
     int64_t l2_keep_bytes = 52LL << 20;  // H bytes per pass kept for the reversed next pass
+    int64_t l2_prefetch_bytes = 0;       // H bytes prefetched into L2 ahead of each pass
     int broken = 0;      // sticky error that blocks further iterations
     double gram_ms = 0.0, factor_ms = 0.0;
     std::string err;
@@ -642,6 +643,10 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.trace = h->trace;
     a.trace_iters = h->trace_iters;
     a.keep_stages = keep_stages(h);
+    {
+        const int64_t per_stage = f16 ? static_cast<int64_t>(pl.R16) * pl.ld * 4 : static_cast<int64_t>(pl.R) * pl.ld * 8;
+        a.prefetch_stages = static_cast<int>(h->l2_prefetch_bytes / std::max<int64_t>(per_stage, 1));
+    }
     a.pending_prev = h->pending && h->k > 0 ? 1 : 0;
     cudaError_t e = admm::launch_iterate(f16 ? h->tmap16 : h->tmap, a, pl.chunks, pl.smem, st, f16);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the iteration kernel");
@@ -1127,6 +1132,10 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
             h->use_f16 = static_cast<int>(value);
             return ADMM_OK;
         }
+        case ADMM_OPT_L2_PREFETCH_BYTES:
+            if (value < 0) return fail(h, ADMM_EINVAL, "L2 prefetch bytes must be >= 0");
+            h->l2_prefetch_bytes = value;
+            return ADMM_OK;
         case ADMM_OPT_BARRIER_EXTRA:
             if (value < 0 || value > 1024) return fail(h, ADMM_EINVAL, "barrier extra out of range");
             h->bar_extra = static_cast<int>(value);

@@ -139,6 +139,7 @@ struct IterArgs {
     long long* trace;     // optional phase timestamps (2 CTAs x trace_iters x 8)
     int trace_iters;
     int keep_stages;      // last stages of each pass keep the normal L2 priority (0 = no L2 hints)
+    int prefetch_stages;  // stages after a pass's L2-resident head prefetched into L2 before it starts
     int pending_prev;     // the previous launch's last residual record is still to be summed
 };
 

@@ -156,6 +156,19 @@ __device__ bool producer_wait(uint64_t* bar, uint32_t parity, const IterArgs& a,
     return *reinterpret_cast<volatile int*>(&misc->stop) == 0;
 }
 
+// first row of stage `pos` of a pass (pass 0: blocks and rows ascending,
+// pass 1: both descending); -1 past the end
+__device__ int stage_row(const IterArgs& a, int pass, int pos) {
+    for (int bi = 0; bi < a.M; ++bi) {
+        const int i = pass == 0 ? bi : a.M - 1 - bi;
+        const int r0 = a.row_off[i], r1 = a.row_off[i + 1];
+        const int nb = (r1 - r0 + a.R - 1) / a.R;
+        if (pos < nb) return r0 + (pass == 0 ? pos : nb - 1 - pos) * a.R;
+        pos -= nb;
+    }
+    return -1;
+}
+
 __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* full,
                          uint64_t* empty, Misc* misc, unsigned char* ring, int c_beg_slab) {
     prefetch_tensormap(tmap);
@@ -181,6 +194,18 @@ __device__ void producer(const CUtensorMap* tmap, const IterArgs& a, uint64_t* f
                 for (int bb = 0; bb < nb; ++bb, ++pos) {
                     const int b = pass == 0 ? bb : nb - 1 - bb;
                     const int y = r0 + b * a.R;
+                    if (pos == 0 && a.prefetch_stages > 0) {
+                        // while the consumers finish the previous pass and wait at
+                        // the grid barriers, pull into L2 the rows this pass reads
+                        // right after its L2-resident head (the kept tail of the
+                        // previous pass) and after the stages the ring holds
+                        const int q0 = max(a.keep_stages, a.nstages);
+                        for (int q = q0; q < q0 + a.prefetch_stages; ++q) {
+                            const int yq = stage_row(a, pass, q);
+                            if (yq < 0) break;
+                            for (int sb = 0; sb < a.nsub; ++sb) tma_prefetch_2d(tmap, c_beg + sb * a.wbox, yq);
+                        }
+                    }
                     const uint32_t parity = pphase ^ 1u;
                     if (!producer_wait(&empty[slot], parity, a, misc)) {
                         ok = false;
