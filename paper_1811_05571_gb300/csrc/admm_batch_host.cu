@@ -753,10 +753,9 @@ int admm_batch_get_info(const admm_batch_t* h, admm_batch_info_t* info) {
     for (int p = 0; p < h->P; ++p) {
         const int i = p / h->N, j = p % h->N;
         const int mi = h->ro[i + 1] - h->ro[i], nj = h->co[j + 1] - h->co[j];
-        fl += 2.0 * mt1 * 128 * cols * 64.0 * ((2 * nj + 63) / 64);
-        fl += 2.0 * mt1 * 128 * cols * h->kr;
-        fl += 2.0 * mt2 * 128 * cols * 64.0 * ((2 * mi + 63) / 64);
-        (void)mi;
+        fl += 2.0 * mt1 * 128 * cols * 64.0 * ((2 * nj + 63) / 64);   // H z
+        fl += 2.0 * mt1 * 128 * cols * h->kr;                          // K^{-1} r
+        fl += 2.0 * mt2 * 128 * cols * 64.0 * ((2 * mi + 63) / 64);   // H^H w
     }
     info->tensor_flops = fl;
     // complex products of the method (8 real flops per complex MAC), all scenes
