@@ -82,6 +82,9 @@ extern "C" {
                                      ends and the grid waits at its barriers: the rows the
                                      next pass reads right after its L2-resident head
                                      (default 0) */
+#define ADMM_OPT_RECORD_ITERS  8  /* record the next `value` iterations for admm_backward
+                                     (their shrinkage arguments a and factor solutions w);
+                                     0 turns recording off.  Resets the state. */
 #define ADMM_OPT_H_FP16        6  /* 1: stream an FP16 copy of H (half the bytes per pass);
                                      0: stream the complex64 H (the default).  The first 1
                                      builds the copy: every 64-row group g of H gets the scale
@@ -291,6 +294,18 @@ int admm_tune(admm_t* h, void* stream);
  * and state update done.  `out` holds 2 * cap * 8 int64 (CTA 0 first); *count
  * receives the iterations written per CTA.  Synchronises `stream`. */
 int admm_get_trace(admm_t* h, int64_t* out, int32_t cap, int32_t* count, void* stream);
+
+/* Gradient of a real loss L of the image v after the iterations run since the
+ * last reset (all recorded: ADMM_OPT_RECORD_ITERS, with g, lambda, rho and the
+ * H mode unchanged): given grad_v = dL/dv (n complex64, host or device, in the
+ * convention x_bar = dL/dRe x + i dL/dIm x), write grad_g = dL/dg (m complex64)
+ * and *grad_lambda, *grad_rho.  The reverse sweep is the adjoint of every
+ * step of the iteration (see admm_batch_backward for the formulas), with the
+ * products H sigma_bar, K^{-1} w_bar and H^H r_bar over the matrix the forward
+ * streamed.  Synchronises.  ADMM_EINVAL when the iterations were not all
+ * recorded.  The paper has no counterpart. */
+int admm_backward(admm_t* h, const void* grad_v, void* grad_g, double* grad_lambda, double* grad_rho,
+                  void* stream);
 
 /* Synchronise `stream` and return the sticky device status of `h`. */
 int admm_status(admm_t* h, void* stream);

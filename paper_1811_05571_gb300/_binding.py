@@ -20,7 +20,7 @@ ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ENOTPD = 0, 1, 2, 3, 4
 ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED = 5, 6, 7, 8
 ADMM_C64, ADMM_C128 = 0, 1
 ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS = 1, 2, 3, 4
-ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ADMM_OPT_L2_PREFETCH_BYTES = 5, 6, 7
+ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ADMM_OPT_L2_PREFETCH_BYTES, ADMM_OPT_RECORD_ITERS = 5, 6, 7, 8
 ABI_VERSION = 3
 
 
@@ -95,6 +95,8 @@ SIGNATURES = {
                                  ctypes.POINTER(c_int32), c_void_p]),
     "admm_status": (c_int32, [c_void_p, c_void_p]),
     "admm_tune": (c_int32, [c_void_p, c_void_p]),
+    "admm_backward": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
+                                c_void_p]),
     "admm_destroy": (None, [c_void_p]),
     "admm_solve_small_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32,
                                            c_double, c_double, c_int32, c_void_p, c_void_p]),
@@ -399,4 +401,11 @@ def admm_batch_tune(h: int, stream=None) -> None:
 
 def admm_tune(h: int, stream=None) -> None:
     _check(load().admm_tune(h, _stream(stream)), h)
+
+
+def admm_backward(h: int, grad_v, grad_g, stream=None):
+    gl, gr = c_double(), c_double()
+    _check(load().admm_backward(h, _ptr(grad_v), _ptr(grad_g), ctypes.byref(gl), ctypes.byref(gr),
+                                _stream(stream)), h)
+    return gl.value, gr.value
 

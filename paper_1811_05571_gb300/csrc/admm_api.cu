@@ -11,6 +11,7 @@
 
 #include <cudaTypedefs.h>
 
+#include "admm_batch.h"
 #include "admm_internal.h"
 
 using admm::Plan;
@@ -56,6 +57,16 @@ struct admm_problem {
     float2* kinv16 = nullptr;
     CUtensorMap tmap16;
     int use_f16 = 0;     // the iteration kernel streams H16
+    // recording of the forward for admm_backward, and the reverse-sweep buffers
+    float2 *rec_a = nullptr, *rec_w = nullptr;
+    int rec_cap = 0, rec_pitch = 0, rec_f16 = 0;
+    bool rec_valid = false;   // every iteration since the reset was recorded, inputs unchanged
+    float2 *bVb = nullptr, *bSb = nullptr, *bGhb = nullptr, *bGt = nullptr, *bdG = nullptr, *bSig = nullptr,
+           *bP = nullptr, *bR = nullptr, *bW = nullptr;
+    double *bkbar = nullptr, *brbar = nullptr;
+    float* bkappa = nullptr;
+    int* bupd = nullptr;
+    int bupd_tiles = 0, bnpitch = 0;
     std::vector<long long> kinv_off;
     std::vector<int> kinv_pitch;
     int64_t kinv_elems = 0;
@@ -108,7 +119,9 @@ cudaError_t dalloc(T** p, size_t count) {
 void free_all(admm_t* h) {
     void* ptrs[] = {h->H, h->g, h->v, h->s, h->u, h->ghat, h->gt, h->r, h->w, h->part, h->kinv,
                     h->kinv_off_d, h->ints_d, h->res_part, h->hist, h->k_done, h->bar, h->status,
-                    h->stop_flag, h->trace, h->H16, h->scales, h->gmax, h->kinv16};
+                    h->stop_flag, h->trace, h->H16, h->scales, h->gmax, h->kinv16, h->rec_a, h->rec_w,
+                    h->bVb, h->bSb, h->bGhb, h->bGt, h->bdG, h->bSig, h->bP, h->bR, h->bW, h->bkbar,
+                    h->brbar, h->bkappa, h->bupd};
     for (void* p : ptrs)
         if (p) cudaFree(p);
 }
@@ -335,8 +348,10 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
 }
 
 int view_handle(const admm_t* h, HandleView* v) {
-    if (!h || !v || !h->H16) return ADMM_EINVAL;
+    if (!h || !v) return ADMM_EINVAL;
+    v->H = h->H;
     v->H16 = h->H16;
+    v->kinv = h->kinv;
     v->scales = h->scales;
     v->kinv16 = h->kinv16;
     v->kinv_off = h->kinv_off_d;
@@ -550,6 +565,8 @@ int zero_state(admm_t* h, cudaStream_t st) {
     h->k = 0;
     h->broken = 0;
     h->pending = 0;
+    h->rec_valid = h->rec_cap > 0;
+    h->rec_f16 = h->use_f16;
     return ADMM_OK;
 }
 
@@ -648,6 +665,13 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
         a.prefetch_stages = static_cast<int>(h->l2_prefetch_bytes / std::max<int64_t>(per_stage, 1));
     }
     a.pending_prev = h->pending && h->k > 0 ? 1 : 0;
+    if (h->rec_cap > 0) {
+        if (h->use_f16 != h->rec_f16 || h->k + iters > h->rec_cap) h->rec_valid = false;
+        a.rec_a = h->rec_a;
+        a.rec_w = h->rec_w;
+        a.rec_cap = h->rec_cap;
+        a.rec_pitch = h->rec_pitch;
+    }
     cudaError_t e = admm::launch_iterate(f16 ? h->tmap16 : h->tmap, a, pl.chunks, pl.smem, st, f16);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the iteration kernel");
     h->k += iters;
@@ -686,6 +710,59 @@ int device_status(admm_t* h, cudaStream_t st) {
     }
     if (code == ADMM_EDIVERGED) return fail(h, code, "the iterates became NaN or Inf");
     if (code != 0) return fail(h, code, "device status %d", code);
+    return ADMM_OK;
+}
+
+void free_record(admm_t* h) {
+    void* ptrs[] = {h->rec_a, h->rec_w, h->bVb, h->bSb, h->bGhb, h->bGt, h->bdG, h->bSig, h->bP, h->bR,
+                    h->bW, h->bkbar, h->brbar, h->bkappa, h->bupd};
+    for (void* p : ptrs)
+        if (p) cudaFree(p);
+    h->rec_a = h->rec_w = h->bVb = h->bSb = h->bGhb = h->bGt = h->bdG = h->bSig = h->bP = h->bR = h->bW = nullptr;
+    h->bkbar = h->brbar = nullptr;
+    h->bkappa = nullptr;
+    h->bupd = nullptr;
+    h->rec_cap = 0;
+    h->rec_valid = false;
+}
+
+// record the next `value` iterations (and allocate the reverse sweep's buffers); resets the state
+int set_record(admm_t* h, int64_t value) {
+    if (value < 0 || value > (1 << 20)) return fail(h, ADMM_EINVAL, "record length out of range");
+    CK(h, cudaDeviceSynchronize());
+    free_record(h);
+    if (value > 0) {
+        const Plan& pl = h->plan;
+        int mimax = 0, njmax = 0;
+        for (int i = 0; i < h->M; ++i) mimax = std::max(mimax, h->row_off[i + 1] - h->row_off[i]);
+        for (int j = 0; j < h->N; ++j) njmax = std::max(njmax, h->col_off[j + 1] - h->col_off[j]);
+        h->rec_pitch = round_up(mimax, 32);
+        h->bnpitch = round_up(njmax, 32);
+        const size_t P = static_cast<size_t>(h->M) * h->N, ld = pl.ld, m = h->m;
+        std::vector<int> uto(h->N + 1, 0);
+        for (int j = 0; j < h->N; ++j)
+            uto[j + 1] = uto[j] + (h->col_off[j + 1] - h->col_off[j] + admm::batch::kUpdCols - 1) / admm::batch::kUpdCols;
+        h->bupd_tiles = uto[h->N];
+        const bool ok = dalloc(&h->rec_a, static_cast<size_t>(value) * ld) == cudaSuccess &&
+                        dalloc(&h->rec_w, static_cast<size_t>(value) * P * h->rec_pitch) == cudaSuccess &&
+                        dalloc(&h->bVb, ld) == cudaSuccess && dalloc(&h->bSb, ld * h->M) == cudaSuccess &&
+                        dalloc(&h->bGhb, m * h->N) == cudaSuccess && dalloc(&h->bGt, m * h->N) == cudaSuccess &&
+                        dalloc(&h->bdG, m) == cudaSuccess && dalloc(&h->bSig, P * h->bnpitch) == cudaSuccess &&
+                        dalloc(&h->bP, P * h->rec_pitch) == cudaSuccess && dalloc(&h->bR, P * h->rec_pitch) == cudaSuccess &&
+                        dalloc(&h->bW, P * h->rec_pitch) == cudaSuccess && dalloc(&h->bkbar, 1) == cudaSuccess &&
+                        dalloc(&h->brbar, 1) == cudaSuccess && dalloc(&h->bkappa, 1) == cudaSuccess &&
+                        dalloc(&h->bupd, uto.size()) == cudaSuccess;
+        if (!ok) {
+            free_record(h);
+            return fail(h, ADMM_ENOMEM, "no room to record %lld iterations", static_cast<long long>(value));
+        }
+        CK(h, cudaMemset(h->rec_a, 0, static_cast<size_t>(value) * ld * sizeof(float2)));
+        CK(h, cudaMemcpy(h->bupd, uto.data(), uto.size() * sizeof(int), cudaMemcpyHostToDevice));
+        h->rec_cap = static_cast<int>(value);
+    }
+    const int code = zero_state(h, nullptr);
+    if (code) return code;
+    CK(h, cudaDeviceSynchronize());
     return ADMM_OK;
 }
 
@@ -982,6 +1059,7 @@ int admm_get_residuals(admm_t* h, double* out, int32_t cap, int32_t* count, void
 int admm_set_g(admm_t* h, const void* g, int32_t h_dtype, void* stream) {
     if (!h || !g) return h ? fail(h, ADMM_EINVAL, "g is NULL") : ADMM_EINVAL;
     if (h_dtype != ADMM_C64 && h_dtype != ADMM_C128) return fail(h, ADMM_EINVAL, "bad dtype");
+    if (h->k > 0) h->rec_valid = false;
     return copy_vector_in(h, h->g, g, h->m, h_dtype, as_stream(stream));
 }
 
@@ -989,6 +1067,7 @@ int admm_set_lambda(admm_t* h, double lambda) {
     if (!h) return ADMM_EINVAL;
     if (!(lambda >= 0.0) || !std::isfinite(lambda)) return fail(h, ADMM_EINVAL, "lambda must be finite and >= 0");
     h->lambda = lambda;
+    if (h->k > 0) h->rec_valid = false;
     return ADMM_OK;
 }
 
@@ -1006,6 +1085,7 @@ int admm_set_rho(admm_t* h, double rho, void* stream) {
         if (h->H16) build_factors_f16(h, st);
         return code;
     }
+    h->rec_valid = false;
     CK(h, admm::launch_scale(h->s, static_cast<int64_t>(h->plan.ld) * h->M, static_cast<float>(old / rho), st));
     CK(h, cudaStreamSynchronize(st));
     return ADMM_OK;
@@ -1055,6 +1135,7 @@ int admm_set_state(admm_t* h, int64_t k, const void* v, const void* s, const voi
     CK(h, cudaStreamSynchronize(st));
     h->k = k;
     h->pending = 0;   // the restored state has no residual record of its own
+    h->rec_valid = false;
     return ADMM_OK;
 }
 
@@ -1132,6 +1213,8 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
             h->use_f16 = static_cast<int>(value);
             return ADMM_OK;
         }
+        case ADMM_OPT_RECORD_ITERS:
+            return set_record(h, value);
         case ADMM_OPT_L2_PREFETCH_BYTES:
             if (value < 0) return fail(h, ADMM_EINVAL, "L2 prefetch bytes must be >= 0");
             h->l2_prefetch_bytes = value;
@@ -1201,6 +1284,101 @@ int admm_get_trace(admm_t* h, int64_t* out, int32_t cap, int32_t* count, void* s
                     buf[(static_cast<size_t>(sel) * h->trace_iters + it) * 8 + q];
     *count = n;
     return ADMM_OK;
+}
+
+int admm_backward(admm_t* h, const void* grad_v, void* grad_g, double* grad_lambda, double* grad_rho,
+                  void* stream) {
+    if (!h || !grad_v || !grad_g || !grad_lambda || !grad_rho)
+        return h ? fail(h, ADMM_EINVAL, "NULL argument") : ADMM_EINVAL;
+    cudaStream_t st = as_stream(stream);
+    int code = device_status(h, st);
+    if (code) return code;
+    if (!h->rec_cap || !h->rec_valid || h->k < 1 || h->k > h->rec_cap)
+        return fail(h, ADMM_EINVAL, "no recorded iterations: set ADMM_OPT_RECORD_ITERS, then iterate at most that "
+                                    "many times from the reset state without changing g, lambda, rho or the mode");
+    const Plan& pl = h->plan;
+    const size_t ld = pl.ld, m = h->m, P = static_cast<size_t>(h->M) * h->N;
+    int mimax = 0, njmax = 0;
+    for (int i = 0; i < h->M; ++i) mimax = std::max(mimax, h->row_off[i + 1] - h->row_off[i]);
+    for (int j = 0; j < h->N; ++j) njmax = std::max(njmax, h->col_off[j + 1] - h->col_off[j]);
+    const float kappa = static_cast<float>(h->lambda / (h->M * h->rho));
+    CK(h, cudaMemsetAsync(h->bVb, 0, ld * sizeof(float2), st));
+    CK(h, cudaMemcpyAsync(h->bVb, grad_v, h->n * sizeof(float2), cudaMemcpyDefault, st));
+    CK(h, cudaMemsetAsync(h->bSb, 0, ld * h->M * sizeof(float2), st));
+    CK(h, cudaMemsetAsync(h->bGhb, 0, m * h->N * sizeof(float2), st));
+    CK(h, cudaMemsetAsync(h->bdG, 0, m * sizeof(float2), st));
+    CK(h, cudaMemsetAsync(h->bkbar, 0, sizeof(double), st));
+    CK(h, cudaMemsetAsync(h->brbar, 0, sizeof(double), st));
+    CK(h, cudaMemcpyAsync(h->bkappa, &kappa, sizeof(float), cudaMemcpyHostToDevice, st));
+    admm::batch::StepArgs sa;
+    std::memset(&sa, 0, sizeof sa);
+    sa.m = static_cast<int>(m);
+    sa.n = static_cast<int>(ld);   // row pitch of v, s and the records
+    sa.M = h->M;
+    sa.N = h->N;
+    sa.P = static_cast<int>(P);
+    sa.B = 1;
+    sa.splits = 1;
+    sa.mpitch = h->rec_pitch;
+    sa.npitch = h->bnpitch;
+    sa.row_off = h->row_off_d;
+    sa.col_off = h->col_off_d;
+    sa.Gt = h->bGt;
+    sa.R = h->bR;
+    sa.Ppart = h->bP;
+    sa.W = h->bW;
+    sa.Sig = h->bSig;
+    sa.kappa = h->bkappa;
+    sa.rho = static_cast<float>(h->rho);
+    sa.inv_M = 1.0f / h->M;
+    sa.upd_tile_off = h->bupd;
+    sa.upd_tiles = h->bupd_tiles;
+    sa.rec_a = h->rec_a;
+    sa.rec_w = h->rec_w;
+    sa.rec_cap = h->rec_cap;
+    sa.Vb = h->bVb;
+    sa.Sb = h->bSb;
+    sa.Ghb = h->bGhb;
+    sa.dG = h->bdG;
+    sa.kbar = h->bkbar;
+    sa.rbar = h->brbar;
+    admm::ProdArgs pa;
+    pa.M = h->M;
+    pa.N = h->N;
+    pa.ld = pl.ld;
+    pa.mimax = mimax;
+    pa.njmax = njmax;
+    pa.mpitch = h->rec_pitch;
+    pa.npitch = h->bnpitch;
+    pa.row_off = h->row_off_d;
+    pa.col_off = h->col_off_d;
+    pa.H = h->H;
+    pa.H16 = h->H16;
+    pa.scales = h->scales;
+    pa.kinv = h->rec_f16 ? h->kinv16 : h->kinv;
+    pa.kinv_off = h->kinv_off_d;
+    pa.kinv_pitch = h->kinv_pitch_d;
+    const bool f16 = h->rec_f16 != 0;
+    for (int64_t k = h->k - 1; k >= 0; --k) {
+        sa.bk = static_cast<int>(k);
+        CK(h, admm::batch::launch_bw_soft(sa, st));
+        CK(h, admm::launch_bw_rows(pa, f16, h->bSig, h->bP, st));
+        CK(h, admm::batch::launch_bw_wbar(sa, st));
+        CK(h, admm::launch_bw_factor(pa, h->bR, h->bW, st));
+        CK(h, admm::batch::launch_bw_rbar(sa, st));
+        CK(h, admm::launch_bw_cols(pa, f16, h->bW, h->bSig, st));
+        CK(h, admm::batch::launch_bw_state(sa, st));
+        CK(h, admm::batch::launch_bw_gtilde(sa, st));
+    }
+    CK(h, cudaMemcpyAsync(grad_g, h->bdG, m * sizeof(float2), cudaMemcpyDefault, st));
+    double kb = 0.0, rb = 0.0;
+    CK(h, cudaMemcpyAsync(&kb, h->bkbar, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaMemcpyAsync(&rb, h->brbar, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(h, cudaStreamSynchronize(st));
+    const double Md = h->M;
+    *grad_lambda = kb / (Md * h->rho);
+    *grad_rho = rb - kb * h->lambda / (Md * h->rho * h->rho);
+    return device_status(h, st);
 }
 
 int admm_status(admm_t* h, void* stream) {

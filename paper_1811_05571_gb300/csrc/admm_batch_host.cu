@@ -239,6 +239,7 @@ int admm_batch_setup(admm_batch_t** out, const void* H, int64_t m, int64_t n, in
         return bail(code);
     }
     admm::view_handle(h->inner, &h->hv);
+    if (!h->hv.H16) return bail(bfail(h, ADMM_ECUDA, "the FP16 copy of H is missing"));
     h->ld = h->hv.ld;
     for (int i = 0; i < row_blocks; ++i) h->mimax = std::max(h->mimax, ro[i + 1] - ro[i]);
     for (int j = 0; j < col_blocks; ++j) h->njmax = std::max(h->njmax, co[j + 1] - co[j]);

@@ -76,6 +76,7 @@ void set_handle_free_error(const char* msg);
 // FP16 copy of H, its group scales, the factors of the matrix it encodes and
 // the block tables.  ADMM_EINVAL until the FP16 copy exists.
 struct HandleView {
+    const float2* H;
     const void* H16;
     const float* scales;
     const float2* kinv16;
@@ -85,8 +86,29 @@ struct HandleView {
     const int* col_off;
     int ld;
     int* status;
+    const float2* kinv;
 };
 int view_handle(const admm_t* h, HandleView* v);
+
+// SIMT products of the single-scene reverse sweep (admm_backward.cu): for block
+// p = i N + j of the complex64 (f16 = false) or FP16 (group scales) H,
+//   rows:   out[p][r] = sum_c H[r0_i + r][c0_j + c] x[p][c]              (x pitch xp)
+//   cols:   out[p][c] = sum_r conj(H[r0_i + r][c0_j + c]) s_r y[p][r]    (s_r: FP16 row scale or 1)
+//   factor: out[p][r] = sum_t Kinv_p[r][t] y[p][t]
+struct ProdArgs {
+    int M, N, ld, mimax, njmax, mpitch, npitch;
+    const int* row_off;
+    const int* col_off;
+    const float2* H;
+    const void* H16;
+    const float* scales;
+    const float2* kinv;
+    const long long* kinv_off;
+    const int* kinv_pitch;
+};
+cudaError_t launch_bw_rows(const ProdArgs& a, bool f16, const float2* x, float2* out, cudaStream_t s);
+cudaError_t launch_bw_cols(const ProdArgs& a, bool f16, const float2* y, float2* out, cudaStream_t s);
+cudaError_t launch_bw_factor(const ProdArgs& a, const float2* y, float2* out, cudaStream_t s);
 
 // Arguments of the persistent iteration kernel (passed by value).
 struct IterArgs {
@@ -140,6 +162,13 @@ struct IterArgs {
     int trace_iters;
     int keep_stages;      // last stages of each pass keep the normal L2 priority (0 = no L2 hints)
     int prefetch_stages;  // stages after a pass's L2-resident head prefetched into L2 before it starts
+    // recording for the adjoint (null when off): iteration k0 + it writes its
+    // shrinkage arguments a (ld) and factor solutions w ([i N + j][rec_pitch])
+    // into slot k0 + it while that is < rec_cap
+    float2* rec_a;
+    float2* rec_w;
+    int rec_cap;
+    int rec_pitch;
     int pending_prev;     // the previous launch's last residual record is still to be summed
 };
 

@@ -652,6 +652,14 @@ struct Consumer {
                         const float2 gb = ldcg2(a.gt + qb);
                         stcg2(ghat_nxt + qb, make_float2(gb.x - a.rho * ab.x, gb.y - a.rho * ab.y));
                     }
+                    if (a.rec_w) {
+                        const long long slot = a.k0 + it;
+                        if (slot < a.rec_cap) {
+                            float2* rw = a.rec_w + (static_cast<size_t>(slot) * a.M * a.N + i * a.N + j) * a.rec_pitch;
+                            rw[rla] = aa;
+                            if (has_b) rw[rlb] = ab;
+                        }
+                    }
                 }
             }
             idx = seg_end;
@@ -777,7 +785,7 @@ struct Consumer {
     }
 
     // ---- epilogue: u_i = z_i + sigma_i, v = S(mean u + mean s), s += u - v ----
-    __device__ void update_state() {
+    __device__ void update_state(long long rec_slot) {
         float rp = 0.f, rdv = 0.f, u2 = 0.f, v2 = 0.f, s2 = 0.f;
         for (int p = tid; p < npairs; p += kConsumerThreads) {
             const int c = c_beg + 2 * p;
@@ -790,6 +798,15 @@ struct Consumer {
                 sb = sb + ss;
             }
             const float4 av = scale4(us + sb, a.inv_M);
+            if (a.rec_a && rec_slot < a.rec_cap) {
+                float2* ra = a.rec_a + static_cast<size_t>(rec_slot) * a.ld + c;
+                if (o0 && o1) {
+                    *reinterpret_cast<float4*>(ra) = av;
+                } else {
+                    if (o0) ra[0] = lo2(av);
+                    if (o1) ra[1] = hi2(av);
+                }
+            }
             const float2 vn0 = soft_threshold(lo2(av), a.kappa);
             const float2 vn1 = soft_threshold(hi2(av), a.kappa);
             const float4 vn = make_float4(vn0.x, vn0.y, vn1.x, vn1.y);
@@ -883,7 +900,7 @@ struct Consumer {
             // leaves v, s and the current estimated data of iteration it-1
             if (a.check_stop && it > 0 && __ldcg(a.stop_flag) != 0) break;
             if (multi) pass_down<true>(); else pass_down<false>();
-            update_state();
+            update_state(a.k0 + it);
             stamp(it, 7);
             completed = it + 1;
         }

@@ -113,6 +113,17 @@ class Solver:
     def set_option(self, option: int, value: int) -> None:
         B.admm_set_option(self.h, int(option), int(value))
 
+    def record(self, iters: int) -> None:
+        """Record the next `iters` iterations for backward() (resets the state)."""
+        B.admm_set_option(self.h, B.ADMM_OPT_RECORD_ITERS, int(iters))
+
+    def backward(self, grad_v):
+        """(grad_g, grad_lambda, grad_rho) of a loss of the current image, given dL/dv."""
+        t = self._torch
+        gg = t.empty(self.m, dtype=t.complex64, device="cuda")
+        gl, gr = B.admm_backward(self.h, _contig(grad_v), gg, self.stream)
+        return gg, gl, gr
+
     def tune(self) -> int:
         """Autotune the L2 keep size of the current mode; resets the state. Returns the bytes kept."""
         B.admm_tune(self.h, self.stream)

@@ -114,3 +114,42 @@ def test_autograd_function_returns_the_library_gradient():
     dG, dl, dr = bs.backward(dV)
     assert torch.allclose(Gt.grad, dG, rtol=1e-5, atol=1e-6 * dG.abs().max().item())
     bs.close()
+
+
+@pytest.mark.parametrize("M,N,K,fp16", [(4, 1, 30, False), (1, 4, 25, False), (2, 2, 25, False), (4, 1, 30, True)])
+def test_single_scene_backward_matches_the_oracle(M, N, K, fp16):
+    """admm_backward on a single-scene handle (complex64 or FP16 H) against the
+    oracle gradient on the matrix that handle streams."""
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(256, 4096, 16, seed=3)
+    rho = _rho(p.H, N)
+    Hm = Q.dequantized(p.H) if fp16 else p.H
+    G, U, lam = synth.shared_h_scenes(p.H, 6, seed0=60, nnz=16)
+    checked = 0
+    for b in range(6):
+        v, rec_a, _, _ = AD.unrolled_forward(Hm, G[b], M, N, lam[b], rho, K)
+        kappa = lam[b] / (M * rho)
+        if min(float(np.min(np.abs(np.abs(a) - kappa))) for a in rec_a) / kappa < KINK:
+            continue
+        s = P.Solver(torch.from_numpy(p.H_c64()).cuda(), torch.from_numpy(G[b].astype(np.complex64)).cuda(),
+                     M, N, lam[b], rho)
+        if fp16:
+            s.use_fp16(True)
+        s.record(K)
+        s.iterate(K)
+        vb = 2.0 * (v - U[b])
+        gg, gl, gr = s.backward(torch.from_numpy(vb.astype(np.complex64)).cuda())
+        g_ref, l_ref, r_ref = AD.unrolled_grad(Hm, G[b], M, N, lam[b], rho, K, vb)
+        eg = np.linalg.norm(gg.cpu().numpy() - g_ref) / np.linalg.norm(g_ref)
+        assert eg <= TOL_GRAD, f"scene {b}: {eg:.3e}"
+        assert abs(gl - l_ref) <= TOL_GRAD * abs(l_ref), (gl, l_ref)
+        assert abs(gr - r_ref) <= TOL_GRAD * abs(r_ref), (gr, r_ref)
+        # changing the data after recording invalidates the record
+        s.set_g(torch.from_numpy(G[b].astype(np.complex64)).cuda())
+        with pytest.raises(P.AdmmError):
+            s.backward(torch.from_numpy(vb.astype(np.complex64)).cuda())
+        s.close()
+        checked += 1
+        if checked == 2:
+            break
+    assert checked >= 1
