@@ -486,9 +486,11 @@ def batched_shared_h(pkg, stream, dev, barrier, p, peaks, batch: int = 256, step
 def uneven_problems(pkg, stream, dev, barrier, peaks, iters: int = 300) -> dict:
     """48 Gaussian problems of uneven sizes (synth.uneven_problem_sizes), each
     with its own handle (consensus over ceil(m/256) row blocks, lambda 0.05
-    max|H^H g|, rho 1), each run for `iters` iterations as one persistent
-    launch, all on one stream: total time with CUDA events, problem-iterations
-    per second and the algorithmic bytes moved per second."""
+    max|H^H g|, rho 1), run for `iters` iterations (a) as one persistent launch
+    per problem, all on one stream, and (b) grouped (admm_group_*: the problems
+    of a wave share one persistent launch, each on its share of the SMs):
+    total time with CUDA events, problem-iterations per second and the
+    algorithmic bytes moved per second."""
     import torch
     import synth
     sizes = synth.uneven_problem_sizes()
@@ -516,6 +518,20 @@ def uneven_problems(pkg, stream, dev, barrier, peaks, iters: int = 300) -> dict:
     for s in solvers:
         if s.status() != 0:
             raise RuntimeError("device status after the uneven problems")
+    # the same problems in one persistent launch per wave (admm_group_*)
+    grp = pkg.Group(solvers, stream=stream)
+    ginfo = grp.info()
+    grp.iterate(3)
+    barrier()
+    a.record(stream)
+    grp.iterate(iters)
+    b.record(stream)
+    barrier()
+    ms_group = a.elapsed_time(b)
+    grp.close()
+    for s in solvers:
+        if s.status() != 0:
+            raise RuntimeError("device status after the grouped uneven problems")
         s.close()
     elems = sum(m * n for m, n, _, _, _ in sizes)
     return {"workload": f"{len(sizes)} Gaussian problems, m in [256, 4096], n in [4096, 32768] "
@@ -523,7 +539,11 @@ def uneven_problems(pkg, stream, dev, barrier, peaks, iters: int = 300) -> dict:
                         f"{iters} iterations each, one launch per problem",
             "problems": len(sizes), "elements": elems, "ms": ms,
             "problem_iterations_per_s": len(sizes) * iters / (ms / 1e3),
-            "alg_gbs": alg * iters / (ms / 1e3) / 1e9, "frac": alg * iters / (ms / 1e3) / 1e9 / peaks["hbm_gbs"]}
+            "alg_gbs": alg * iters / (ms / 1e3) / 1e9, "frac": alg * iters / (ms / 1e3) / 1e9 / peaks["hbm_gbs"],
+            "group": {"waves": ginfo["waves"], "ms": ms_group,
+                      "problem_iterations_per_s": len(sizes) * iters / (ms_group / 1e3),
+                      "alg_gbs": alg * iters / (ms_group / 1e3) / 1e9,
+                      "frac": alg * iters / (ms_group / 1e3) / 1e9 / peaks["hbm_gbs"]}}
 
 
 def differentiable(pkg, stream, dev, barrier, K: int = 100) -> dict:

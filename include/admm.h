@@ -344,6 +344,34 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
                              int32_t iters, void* v_out, void* stream);
 
 /* ---------------------------------------------------------------------------
+ * Several independent problems in one persistent launch.  Each handle keeps
+ * its state; the group re-plans every problem for a share of the SMs (in
+ * proportion to its bytes of H and factors, at least what its column slabs
+ * need) and runs all problems of a wave together in one cooperative launch,
+ * each on its own CTAs with its own grid barriers.  Problems that do not fit
+ * the SMs together go to further waves (launched one after another).  The
+ * paper solves one problem at a time; this is the library's scheduler for
+ * many uneven ones.
+ * ------------------------------------------------------------------------- */
+typedef struct admm_group admm_group_t;
+
+/* Build a group over `count` handles (which must outlive it).  Host planning
+ * plus small allocations; synchronises the device.  On failure *out is NULL
+ * and admm_group_last_error(NULL) says why. */
+int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, void* stream);
+
+/* Run `iters` iterations of every problem (one launch per wave); each handle's
+ * iteration count, history and state advance as under admm_iterate.  All
+ * problems of a wave must share the H mode (complex64 or FP16).  Synchronises. */
+int admm_group_iterate(admm_group_t* g, int32_t iters, void* stream);
+
+/* Number of waves, and the CTAs each problem was given (cap entries). */
+int admm_group_info(const admm_group_t* g, int32_t* waves, int32_t* ctas, int32_t cap);
+
+const char* admm_group_last_error(const admm_group_t* g);
+void admm_group_destroy(admm_group_t* g);
+
+/* ---------------------------------------------------------------------------
  * Batched shared-H solver.  `batch` independent scenes g_b (b = 0..batch-1)
  * with one sensing matrix H are iterated together under the same split: each
  * scene runs exactly the iteration of admm_iterate (Sections III-A..C, with

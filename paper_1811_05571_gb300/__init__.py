@@ -21,6 +21,7 @@ from ._binding import (  # noqa: F401
     admm_batch_setup, admm_batch_set_g, admm_batch_iterate, admm_batch_get_v, admm_batch_get_residuals,
     admm_batch_reset, admm_batch_forward, admm_batch_adjoint, admm_batch_status, admm_batch_get_info,
     admm_batch_destroy, admm_batch_record, admm_batch_backward, admm_batch_tune, admm_tune, admm_backward,
+    admm_group_setup, admm_group_iterate, admm_group_info, admm_group_destroy,
 )
-from .solver import BatchSolver, UnrolledADMM  # noqa: F401
+from .solver import BatchSolver, Group, UnrolledADMM  # noqa: F401
 from .solver import Solver  # noqa: F401

@@ -95,6 +95,11 @@ SIGNATURES = {
                                  ctypes.POINTER(c_int32), c_void_p]),
     "admm_status": (c_int32, [c_void_p, c_void_p]),
     "admm_tune": (c_int32, [c_void_p, c_void_p]),
+    "admm_group_setup": (c_int32, [ctypes.POINTER(c_void_p), ctypes.POINTER(c_void_p), c_int32, c_void_p]),
+    "admm_group_iterate": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "admm_group_info": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32), c_int32]),
+    "admm_group_last_error": (ctypes.c_char_p, [c_void_p]),
+    "admm_group_destroy": (None, [c_void_p]),
     "admm_backward": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                 c_void_p]),
     "admm_destroy": (None, [c_void_p]),
@@ -408,4 +413,34 @@ def admm_backward(h: int, grad_v, grad_g, stream=None):
     _check(load().admm_backward(h, _ptr(grad_v), _ptr(grad_g), ctypes.byref(gl), ctypes.byref(gr),
                                 _stream(stream)), h)
     return gl.value, gr.value
+
+
+def _gcheck(status: int, handle=None) -> None:
+    if status != ADMM_OK:
+        lib = load(False)
+        msg = lib.admm_group_last_error(handle)
+        raise AdmmError(status, (msg or lib.admm_strerror(status)).decode())
+
+
+def admm_group_setup(handles, stream=None) -> int:
+    out = c_void_p()
+    arr = (c_void_p * len(handles))(*handles)
+    _gcheck(load().admm_group_setup(ctypes.byref(out), arr, len(handles), _stream(stream)))
+    return out.value
+
+
+def admm_group_iterate(g: int, iters: int, stream=None) -> None:
+    _gcheck(load().admm_group_iterate(g, iters, _stream(stream)), g)
+
+
+def admm_group_info(g: int, count: int):
+    waves = c_int32()
+    ctas = (c_int32 * max(1, count))()
+    _gcheck(load().admm_group_info(g, ctypes.byref(waves), ctas, count), g)
+    return waves.value, list(ctas[:count])
+
+
+def admm_group_destroy(g: int) -> None:
+    if g:
+        load().admm_group_destroy(g)
 

@@ -149,7 +149,7 @@ void balanced_offsets(int64_t total, int parts, std::vector<int>& off) {
 
 int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_off,
               const std::vector<int>& col_off, int num_sms, int smem_limit, Plan& pl,
-              const char** why) {
+              const char** why, int force_chunks) {
     *why = "";
     if (num_sms < 1 || smem_limit < 16384) {
         *why = "bad device limits";
@@ -270,6 +270,7 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     const int need = (pl.npmax + 31) / 32;
     int ch = 1;
     while (ch < need) ch *= 2;
+    while (ch < force_chunks) ch *= 2;   // a multi-problem launch shares one kernel instance
     if (ch > 16) {
         *why = "column slab wider than 1024 pairs per CTA";
         return ADMM_EUNSUPPORTED;
@@ -570,18 +571,24 @@ int zero_state(admm_t* h, cudaStream_t st) {
     return ADMM_OK;
 }
 
-// stages per pass whose H rows stay in L2 for the reversed next pass
-int keep_stages(const admm_t* h) {
-    const Plan& pl = h->plan;
-    const int64_t per_stage = h->use_f16 ? static_cast<int64_t>(pl.R16) * pl.ld * 4
-                                         : static_cast<int64_t>(pl.R) * pl.ld * 8;
-    return static_cast<int>(std::max<int64_t>(0, h->l2_keep_bytes / std::max<int64_t>(per_stage, 1)));
+
+// device tables and scratch that depend on the launch plan
+struct PlanBuffers {
+    const int *cta_col, *cta_end, *own0, *own1, *jlo, *nj, *j_lo, *j_hi, *solve_lo;
+    float2* part;
+    double* res_part;
+    unsigned* bar;
+};
+
+PlanBuffers handle_buffers(admm_t* h) {
+    return PlanBuffers{h->cta_col_d, h->cta_end_d, h->cta_own0_d, h->cta_own1_d,
+                       h->cta_jlo_d, h->cta_nj_d, h->j_cta_lo_d, h->j_cta_hi_d, h->solve_lo_d, h->part,
+                       h->res_part, h->bar};
 }
 
-int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_rel,
-               cudaStream_t st) {
-    const Plan& pl = h->plan;
-    admm::IterArgs a;
+// kernel arguments of `iters` iterations of h under plan pl
+void fill_args(admm_t* h, const Plan& pl, const PlanBuffers& b, int iters, int check_stop, double eps_abs,
+               double eps_rel, admm::IterArgs& a) {
     std::memset(&a, 0, sizeof a);
     a.m = static_cast<int>(h->m);
     a.n = static_cast<int>(h->n);
@@ -621,15 +628,15 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.inv_M = 1.0f / static_cast<float>(h->M);
     a.row_off = h->row_off_d;
     a.col_off = h->col_off_d;
-    a.cta_col = h->cta_col_d;
-    a.cta_end = h->cta_end_d;
-    a.cta_own0 = h->cta_own0_d;
-    a.cta_own1 = h->cta_own1_d;
-    a.cta_jlo = h->cta_jlo_d;
-    a.cta_nj = h->cta_nj_d;
-    a.j_cta_lo = h->j_cta_lo_d;
-    a.j_cta_hi = h->j_cta_hi_d;
-    a.solve_lo = h->solve_lo_d;
+    a.cta_col = b.cta_col;
+    a.cta_end = b.cta_end;
+    a.cta_own0 = b.own0;
+    a.cta_own1 = b.own1;
+    a.cta_jlo = b.jlo;
+    a.cta_nj = b.nj;
+    a.j_cta_lo = b.j_lo;
+    a.j_cta_hi = b.j_hi;
+    a.solve_lo = b.solve_lo;
     a.v = h->v;
     a.s = h->s;
     a.u = h->u;
@@ -638,15 +645,15 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.gt = h->gt;
     a.r = h->r;
     a.w = h->w;
-    a.part = h->part;
+    a.part = b.part;
     a.kinv = f16 ? h->kinv16 : h->kinv;
     a.scales = f16 ? h->scales : nullptr;
     a.kinv_off = h->kinv_off_d;
     a.kinv_pitch = h->kinv_pitch_d;
-    a.res_part = h->res_part;
+    a.res_part = b.res_part;
     a.hist = h->hist;
     a.k_done = h->k_done;
-    a.bar = h->bar;
+    a.bar = b.bar;
     a.status = h->status;
     a.stop_flag = h->stop_flag;
     a.k0 = h->k;
@@ -659,9 +666,9 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
     a.bar_extra = h->bar_extra;
     a.trace = h->trace;
     a.trace_iters = h->trace_iters;
-    a.keep_stages = keep_stages(h);
     {
         const int64_t per_stage = f16 ? static_cast<int64_t>(pl.R16) * pl.ld * 4 : static_cast<int64_t>(pl.R) * pl.ld * 8;
+        a.keep_stages = static_cast<int>(std::max<int64_t>(0, h->l2_keep_bytes / std::max<int64_t>(per_stage, 1)));
         a.prefetch_stages = static_cast<int>(h->l2_prefetch_bytes / std::max<int64_t>(per_stage, 1));
     }
     a.pending_prev = h->pending && h->k > 0 ? 1 : 0;
@@ -672,6 +679,14 @@ int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
         a.rec_cap = h->rec_cap;
         a.rec_pitch = h->rec_pitch;
     }
+}
+
+int run_kernel(admm_t* h, int iters, int check_stop, double eps_abs, double eps_rel,
+               cudaStream_t st) {
+    const Plan& pl = h->plan;
+    admm::IterArgs a;
+    fill_args(h, pl, handle_buffers(h), iters, check_stop, eps_abs, eps_rel, a);
+    const bool f16 = h->use_f16 != 0;
     cudaError_t e = admm::launch_iterate(f16 ? h->tmap16 : h->tmap, a, pl.chunks, pl.smem, st, f16);
     if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the iteration kernel");
     h->k += iters;
@@ -1391,6 +1406,314 @@ void admm_destroy(admm_t* h) {
     cudaDeviceSynchronize();
     free_all(h);
     delete h;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// several problems in one persistent launch
+// ---------------------------------------------------------------------------
+
+struct admm_group {
+    struct Prob {
+        admm_t* h = nullptr;
+        Plan pl;
+        int* tabs = nullptr;
+        float2* part = nullptr;
+        double* res_part = nullptr;
+        unsigned* bar = nullptr;
+        CUtensorMap tmap, tmap16;
+        int o_beg = 0, o_end = 0, o_own0 = 0, o_own1 = 0, o_jlo = 0, o_nj = 0, o_jl = 0, o_jh = 0, o_sl = 0;
+    };
+    struct Wave {
+        std::vector<int> probs;
+        int ctas = 0, chunks = 1, smem = 0;
+        int* cta_map = nullptr;   // [ctas] problem index in the wave, then [ctas] local CTA index
+    };
+    std::vector<Prob> probs;
+    std::vector<Wave> waves;
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_group_error;
+
+int gfail(admm_group_t* g, int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (g) g->err = buf;
+    else g_group_error = buf;
+    return code;
+}
+
+void free_group(admm_group_t* g) {
+    for (auto& p : g->probs) {
+        void* ptrs[] = {p.tabs, p.part, p.res_part, p.bar};
+        for (void* q : ptrs)
+            if (q) cudaFree(q);
+    }
+    for (auto& w : g->waves)
+        if (w.cta_map) cudaFree(w.cta_map);
+}
+
+// tensor map of h's H (f16: its FP16 copy) with the box of plan pl
+int encode_for(admm_t* h, const Plan& pl, bool f16, CUtensorMap* map) {
+    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+    if (!encode) {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
+            return ADMM_ECUDA;
+        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    const size_t eb = f16 ? 4 : 8;
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(pl.ld), static_cast<cuuint64_t>(h->m)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(pl.ld) * eb};
+    cuuint32_t box[2] = {static_cast<cuuint32_t>(f16 ? pl.wbox16 : pl.wbox), static_cast<cuuint32_t>(f16 ? pl.R16 : pl.R)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode(map, f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2,
+                        f16 ? h->H16 : static_cast<void*>(h->H), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                        CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? ADMM_OK : ADMM_ECUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* admm_group_last_error(const admm_group_t* g) { return g ? g->err.c_str() : g_group_error.c_str(); }
+
+int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, void* stream) {
+    (void)stream;
+    if (!out || !handles || count < 1) return gfail(nullptr, ADMM_EINVAL, "need out, handles and count >= 1");
+    *out = nullptr;
+    for (int q = 0; q < count; ++q)
+        if (!handles[q]) return gfail(nullptr, ADMM_EINVAL, "handle %d is NULL", q);
+    const int sms = handles[0]->num_sms, limit = handles[0]->smem_optin;
+    admm_group_t* g = new admm_group_t();
+    auto bail = [&](int c) {
+        g_group_error = g->err;
+        free_group(g);
+        delete g;
+        return c;
+    };
+    // smallest CTA count each problem runs well with (slabs of at most 512
+    // columns: the 4-chunk kernel instance, which keeps its accumulators in
+    // registers), and its work per iteration
+    std::vector<int> pmin(count), pmax(count);
+    std::vector<double> work(count);
+    for (int q = 0; q < count; ++q) {
+        admm_t* h = handles[q];
+        const int ld = h->plan.ld;
+        pmax[q] = std::max(1, std::min(sms, ld / 64));
+        pmin[q] = 0;
+        for (int P = std::min(pmax[q], std::max(1, (ld + 511) / 512)); P <= pmax[q]; ++P) {
+            Plan pl;
+            const char* why = "";
+            if (admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P, limit, pl, &why) == ADMM_OK &&
+                pl.P == P) {
+                pmin[q] = P;
+                break;
+            }
+        }
+        if (!pmin[q]) return bail(gfail(g, ADMM_EUNSUPPORTED, "problem %d has no plan on fewer than %d CTAs", q, sms));
+        work[q] = static_cast<double>(h->m) * ld + 1.0 * h->kinv_elems;
+    }
+    // waves: a problem whose two passes over H take several times the fixed
+    // per-iteration cost (grid barriers, reductions: about 15 us) on the whole
+    // GPU runs alone with every CTA it can use (sharing its wave with small
+    // problems measured slower); the others, by decreasing work, go first fit
+    // into shared waves at their minimum CTA counts
+    g->probs.resize(count);
+    std::vector<int> order(count);
+    for (int q = 0; q < count; ++q) order[q] = q;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+    std::vector<int> used;
+    const double solo_work = 2.0e7;   // complex entries of H (and factors): about 45 us per iteration
+    for (int q : order) {
+        if (work[q] >= solo_work) {
+            g->waves.emplace_back();
+            g->waves.back().probs.push_back(q);
+            pmin[q] = pmax[q];
+            used.push_back(sms);
+            continue;
+        }
+        size_t w = 0;
+        while (w < g->waves.size() &&
+               (used[w] + pmin[q] > sms || g->waves[w].probs.size() >= static_cast<size_t>(admm::kMaxGroupWave)))
+            ++w;
+        if (w == g->waves.size()) {
+            g->waves.emplace_back();
+            used.push_back(0);
+        }
+        g->waves[w].probs.push_back(q);
+        used[w] += pmin[q];
+    }
+    for (auto& w : g->waves) {
+        // CTAs in proportion to the work, within [pmin, pmax], at most one per SM in total
+        double tot = 0.0;
+        for (int q : w.probs) tot += work[q];
+        std::vector<int> P(w.probs.size());
+        int sum = 0;
+        for (size_t t = 0; t < w.probs.size(); ++t) {
+            const int q = w.probs[t];
+            P[t] = std::max(pmin[q], std::min(pmax[q], static_cast<int>(sms * work[q] / tot)));
+            sum += P[t];
+        }
+        while (sum > sms) {
+            int best = -1;
+            for (size_t t = 0; t < P.size(); ++t)
+                if (P[t] > pmin[w.probs[t]] && (best < 0 || P[t] * work[w.probs[best]] > P[best] * work[w.probs[t]]))
+                    best = static_cast<int>(t);
+            if (best < 0) break;
+            --P[best];
+            --sum;
+        }
+        // plans: first per problem, then all with the largest chunk count (one kernel instance)
+        int ch = 1;
+        for (size_t t = 0; t < P.size(); ++t) {
+            admm_t* h = handles[w.probs[t]];
+            Plan pl;
+            const char* why = "";
+            int code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pl, &why);
+            // the planner may settle on fewer CTAs than offered; try fewer offers until one fits
+            while (code != ADMM_OK && P[t] > pmin[w.probs[t]]) {
+                --P[t];
+                code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pl, &why);
+            }
+            if (code) return bail(gfail(g, code, "problem %d: %s", w.probs[t], why));
+            ch = std::max(ch, pl.chunks);
+        }
+        w.chunks = ch;
+        w.ctas = 0;
+        w.smem = 0;
+        std::vector<int> cta_map;
+        std::vector<int> cprob, clocal;
+        for (size_t t = 0; t < P.size(); ++t) {
+            const int q = w.probs[t];
+            admm_t* h = handles[q];
+            admm_group_t::Prob& pr = g->probs[q];
+            pr.h = h;
+            const char* why = "";
+            int code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pr.pl, &why, ch);
+            if (code) return bail(gfail(g, code, "problem %d with %d chunks: %s", q, ch, why));
+            w.smem = std::max(w.smem, pr.pl.smem);
+            for (int c = 0; c < pr.pl.P; ++c) {
+                cprob.push_back(static_cast<int>(t));
+                clocal.push_back(c);
+            }
+            w.ctas += pr.pl.P;
+            // the plan's tables and scratch
+            std::vector<int> it;
+            auto put = [&](const std::vector<int>& x) {
+                const size_t at = it.size();
+                it.insert(it.end(), x.begin(), x.end());
+                return static_cast<int>(at);
+            };
+            pr.o_beg = put(pr.pl.cta_beg);
+            pr.o_end = put(pr.pl.cta_end);
+            pr.o_own0 = put(pr.pl.cta_own0);
+            pr.o_own1 = put(pr.pl.cta_own1);
+            pr.o_jlo = put(pr.pl.cta_jlo);
+            pr.o_nj = put(pr.pl.cta_nj);
+            pr.o_jl = put(pr.pl.j_cta_lo);
+            pr.o_jh = put(pr.pl.j_cta_hi);
+            pr.o_sl = put(pr.pl.solve_lo);
+            const size_t Nm = static_cast<size_t>(h->N) * h->m;
+            if (dalloc(&pr.tabs, it.size()) != cudaSuccess || dalloc(&pr.part, Nm * pr.pl.P) != cudaSuccess ||
+                dalloc(&pr.res_part, static_cast<size_t>(pr.pl.P) * 8) != cudaSuccess ||
+                dalloc(&pr.bar, 2) != cudaSuccess)
+                return bail(gfail(g, ADMM_ENOMEM, "device allocation failed for problem %d", q));
+            if (cudaMemcpy(pr.tabs, it.data(), it.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemset(pr.bar, 0, 2 * sizeof(unsigned)) != cudaSuccess)
+                return bail(gfail(g, ADMM_ECUDA, "copy of the plan tables failed"));
+            if (encode_for(h, pr.pl, false, &pr.tmap) != ADMM_OK ||
+                (h->H16 && encode_for(h, pr.pl, true, &pr.tmap16) != ADMM_OK))
+                return bail(gfail(g, ADMM_ECUDA, "cuTensorMapEncodeTiled failed for problem %d", q));
+        }
+        if (w.ctas > sms) return bail(gfail(g, ADMM_EUNSUPPORTED, "a wave needs %d CTAs on %d SMs", w.ctas, sms));
+        cta_map = cprob;
+        cta_map.insert(cta_map.end(), clocal.begin(), clocal.end());
+        if (dalloc(&w.cta_map, cta_map.size()) != cudaSuccess ||
+            cudaMemcpy(w.cta_map, cta_map.data(), cta_map.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(gfail(g, ADMM_ENOMEM, "device allocation failed for a wave"));
+    }
+    *out = g;
+    return ADMM_OK;
+}
+
+int admm_group_iterate(admm_group_t* g, int32_t iters, void* stream) {
+    if (!g || iters < 0) return g ? gfail(g, ADMM_EINVAL, "iters must be >= 0") : ADMM_EINVAL;
+    if (iters == 0) return ADMM_OK;
+    cudaStream_t st = as_stream(stream);
+    for (auto& w : g->waves) {
+        const bool f16 = g->probs[w.probs[0]].h->use_f16 != 0;
+        std::vector<admm::GroupParams> gpv(1);   // ~30 KB: on the heap
+        admm::GroupParams& gp = gpv[0];
+        std::memset(&gp, 0, sizeof gp);
+        gp.count = static_cast<int>(w.probs.size());
+        for (size_t t = 0; t < w.probs.size(); ++t) {
+            admm_group_t::Prob& pr = g->probs[w.probs[t]];
+            admm_t* h = pr.h;
+            if (h->broken) return gfail(g, ADMM_ECUDA, "problem %d is in an error state", w.probs[t]);
+            if ((h->use_f16 != 0) != f16) return gfail(g, ADMM_EINVAL, "the problems of a wave must share the H mode");
+            if (h->pending) {
+                const int code = device_status(h, st);
+                if (code) return gfail(g, code, "problem %d: %s", w.probs[t], h->err.c_str());
+            }
+            const int* T = pr.tabs;
+            PlanBuffers b{T + pr.o_beg, T + pr.o_end, T + pr.o_own0, T + pr.o_own1, T + pr.o_jlo, T + pr.o_nj,
+                          T + pr.o_jl, T + pr.o_jh, T + pr.o_sl, pr.part, pr.res_part, pr.bar};
+            fill_args(h, pr.pl, b, iters, 0, 0.0, 0.0, gp.a[t]);
+            gp.a[t].trace = nullptr;
+            gp.tmap[t] = f16 ? pr.tmap16 : pr.tmap;
+            if (!admm::group_stage_geometry_ok(gp.a[t], w.chunks, f16))
+                return gfail(g, ADMM_EUNSUPPORTED, "inconsistent stage geometry for problem %d", w.probs[t]);
+        }
+        cudaError_t e = admm::launch_group(gp, w.cta_map, w.cta_map + w.ctas, w.ctas, w.chunks, f16, w.smem, st);
+        if (e != cudaSuccess) return gfail(g, ADMM_ECUDA, "group launch failed: %s", cudaGetErrorString(e));
+        for (size_t t = 0; t < w.probs.size(); ++t) {
+            admm_group_t::Prob& pr = g->probs[w.probs[t]];
+            admm_t* h = pr.h;
+            h->k += iters;
+            // the launch's last residual record, from this plan's partials
+            admm::IterArgs a;
+            std::memset(&a, 0, sizeof a);
+            a.M = h->M;
+            a.n = static_cast<int>(h->n);
+            a.P = pr.pl.P;
+            a.rho_d = h->rho;
+            a.res_part = pr.res_part;
+            a.hist = h->hist;
+            a.hist_cap = h->hist_cap;
+            a.status = h->status;
+            e = admm::launch_finalize(a, h->k - 1, st);
+            if (e != cudaSuccess) return gfail(g, ADMM_ECUDA, "finalize failed: %s", cudaGetErrorString(e));
+            h->pending = 0;
+        }
+    }
+    return ADMM_OK;
+}
+
+int admm_group_info(const admm_group_t* g, int32_t* waves, int32_t* ctas, int32_t cap) {
+    if (!g || !waves) return ADMM_EINVAL;
+    *waves = static_cast<int32_t>(g->waves.size());
+    if (ctas)
+        for (int q = 0; q < cap && q < static_cast<int>(g->probs.size()); ++q) ctas[q] = g->probs[q].pl.P;
+    return ADMM_OK;
+}
+
+void admm_group_destroy(admm_group_t* g) {
+    if (!g) return;
+    cudaDeviceSynchronize();
+    free_group(g);
+    delete g;
 }
 
 }  // extern "C"

@@ -65,7 +65,7 @@ struct Plan {
 // Returns ADMM_OK, ADMM_EINVAL or ADMM_EUNSUPPORTED; fills `plan`.
 int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_off,
               const std::vector<int>& col_off, int num_sms, int smem_limit, Plan& plan,
-              const char** why);
+              const char** why, int force_chunks = 0);
 
 void balanced_offsets(int64_t total, int parts, std::vector<int>& off);
 
@@ -171,6 +171,23 @@ struct IterArgs {
     int rec_pitch;
     int pending_prev;     // the previous launch's last residual record is still to be summed
 };
+
+// The problems of a multi-problem launch, passed as kernel parameters (so the
+// tensor maps and arguments sit in the parameter space, as for one problem).
+constexpr int kMaxGroupWave = 24;
+struct GroupParams {
+    CUtensorMap tmap[kMaxGroupWave];
+    IterArgs a[kMaxGroupWave];
+    int count;
+};
+
+// Cooperative launch of `ctas` CTAs running several problems (the kernel
+// instance with `chunks` chunks, complex64 or FP16 H, `smem` bytes of dynamic
+// shared memory for the largest problem layout); CTA b runs local CTA
+// cta_local[b] of problem cta_prob[b].
+cudaError_t launch_group(const GroupParams& gp, const int* cta_prob, const int* cta_local, int ctas, int chunks,
+                         bool f16, int smem, cudaStream_t stream);
+bool group_stage_geometry_ok(const IterArgs& a, int chunks, bool f16);
 
 // Sum the per-CTA residual partials of iteration kabs into the history ring.
 cudaError_t launch_finalize(const IterArgs& a, long long kabs, cudaStream_t stream);

@@ -306,12 +306,12 @@ struct Consumer {
     uint32_t phase;       // parity of that slot's current fill
 
     __device__ Consumer(const IterArgs& args, unsigned char* sm, Misc* mi, uint64_t* f,
-                        uint64_t* e, const unsigned char* rg)
+                        uint64_t* e, const unsigned char* rg, int cta_index)
         : a(args), smem(sm), misc(mi), full(f), empty(e), ring(rg) {
         tid = threadIdx.x;
         warp = tid >> 5;
         lane = tid & 31;
-        cta = blockIdx.x;
+        cta = cta_index;
         c_beg = a.cta_col[cta];
         npairs = (a.cta_end[cta] - c_beg) >> 1;
         jlo = a.cta_jlo[cta];
@@ -909,10 +909,10 @@ struct Consumer {
     }
 };
 
+// One CTA of a problem's persistent iteration: local CTA index `cta` of a.P.
 template <int CH, bool F16>
-__global__ void __launch_bounds__(kIterThreads, 1)
-    iterate_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ IterArgs a) {
-    extern __shared__ __align__(1024) unsigned char smem[];
+__device__ __forceinline__ void iterate_body(const CUtensorMap* tmap, const IterArgs& a, int cta,
+                                             unsigned char* smem) {
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.off_full);
     uint64_t* empty = reinterpret_cast<uint64_t*>(smem + a.off_empty);
     Misc* misc = reinterpret_cast<Misc*>(smem + a.off_misc);
@@ -933,11 +933,31 @@ __global__ void __launch_bounds__(kIterThreads, 1)
     __syncthreads();
     if (warp == kConsumerWarps) {
         if ((threadIdx.x & 31) == 0)
-            producer(&tmap, a, full, empty, misc, ring, a.cta_col[blockIdx.x]);
+            producer(tmap, a, full, empty, misc, ring, a.cta_col[cta]);
         return;
     }
-    Consumer<CH, F16> c(a, smem, misc, full, empty, ring);
+    Consumer<CH, F16> c(a, smem, misc, full, empty, ring, cta);
     c.run();
+}
+
+template <int CH, bool F16>
+__global__ void __launch_bounds__(kIterThreads, 1)
+    iterate_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ IterArgs a) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    iterate_body<CH, F16>(&tmap, a, blockIdx.x, smem);
+}
+
+// Several problems in one cooperative launch: CTA b runs local CTA cta_local[b]
+// of problem cta_prob[b]; arguments and tensor maps are kernel parameters.
+static_assert(sizeof(GroupParams) <= 32000, "group parameters exceed the kernel parameter space");
+
+template <int CH, bool F16>
+__global__ void __launch_bounds__(kIterThreads, 1)
+    iterate_group_kernel(const __grid_constant__ GroupParams gp, const int* __restrict__ cta_prob,
+                         const int* __restrict__ cta_local) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int p = cta_prob[blockIdx.x];
+    iterate_body<CH, F16>(&gp.tmap[p], gp.a[p], cta_local[blockIdx.x], smem);
 }
 
 __global__ void __launch_bounds__(32) finalize_kernel(const __grid_constant__ IterArgs a, long long kabs) {
@@ -962,6 +982,25 @@ void* pick_t(int chunks) {
 }
 
 void* pick(int chunks, bool f16 = false) { return f16 ? pick_t<true>(chunks) : pick_t<false>(chunks); }
+
+template <int CH, bool F16>
+void* group_fn() {
+    return reinterpret_cast<void*>(&iterate_group_kernel<CH, F16>);
+}
+
+template <bool F16>
+void* pick_group_t(int chunks) {
+    switch (chunks) {
+        case 1: return group_fn<1, F16>();
+        case 2: return group_fn<2, F16>();
+        case 4: return group_fn<4, F16>();
+        case 8: return group_fn<8, F16>();
+        case 16: return group_fn<16, F16>();
+        default: return nullptr;
+    }
+}
+
+void* pick_group(int chunks, bool f16) { return f16 ? pick_group_t<true>(chunks) : pick_group_t<false>(chunks); }
 
 }  // namespace
 
@@ -1022,4 +1061,17 @@ cudaError_t launch_iterate(const CUtensorMap& tmap, const IterArgs& a, int chunk
                                        static_cast<size_t>(smem), stream);
 }
 
+cudaError_t launch_group(const GroupParams& gp, const int* cta_prob, const int* cta_local, int ctas, int chunks,
+                         bool f16, int smem, cudaStream_t stream) {
+    void* fn = pick_group(chunks, f16);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {const_cast<GroupParams*>(&gp), const_cast<int**>(&cta_prob), const_cast<int**>(&cta_local)};
+    return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kIterThreads), args, static_cast<size_t>(smem), stream);
+}
+
+bool group_stage_geometry_ok(const IterArgs& a, int chunks, bool f16) { return stage_geometry_ok(a, chunks, f16); }
+
 }  // namespace admm
+

@@ -284,3 +284,32 @@ class UnrolledADMM:
             cls._fn = _unrolled_function()
         return cls._fn.apply(G, solver, iters)
 
+
+class Group:
+    """Several Solver handles iterated together in one persistent launch per
+    wave (include/admm.h, admm_group_*).  The solvers must outlive the group."""
+
+    def __init__(self, solvers, stream=None):
+        self.solvers = list(solvers)
+        self.stream = stream
+        self.g = B.admm_group_setup([s.h for s in self.solvers], stream)
+
+    def iterate(self, iters: int = 1) -> "Group":
+        B.admm_group_iterate(self.g, int(iters), self.stream)
+        return self
+
+    def info(self):
+        waves, ctas = B.admm_group_info(self.g, len(self.solvers))
+        return {"waves": waves, "ctas": ctas}
+
+    def close(self) -> None:
+        if getattr(self, "g", None):
+            B.admm_group_destroy(self.g)
+            self.g = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
