@@ -50,6 +50,8 @@ def parse_args(argv=None):
     ap.add_argument("--cpu-iters", type=int, default=12,
                     help="iterations per split in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-direct", action="store_true",
+                    help="skip the direct-factor-form leg (overdetermined 32768 x 2048)")
     ap.add_argument("--no-uneven", action="store_true",
                     help="skip the 48 uneven problems workload")
     ap.add_argument("--no-adjoint", action="store_true",
@@ -589,6 +591,63 @@ def differentiable(pkg, stream, dev, barrier, K: int = 100) -> dict:
             "backward_over_forward": bwd / fwd, "tensor_flops_per_iter": info["tensor_flops"]}
 
 
+def direct_form(pkg, stream, dev, barrier, peaks, iters: int = 64) -> dict:
+    """The direct factor form on an overdetermined 32768 x 2048 Gaussian
+    problem in three splits (every block has m_b >= n_b), and the lemma form on
+    the consensus split for comparison.  Per split: one call of `iters`
+    iterations timed with CUDA events on the launching stream, after three
+    warm-up iterations.  Algorithmic bytes per iteration: the passes over H
+    (none with one column block: H_i^H g_i is cached, two otherwise), every
+    factor once, the state v, s read and written, and with one column block
+    the cached H_i^H g_i."""
+    import torch
+    import synth
+    c = synth.TALL
+    H, g, _, lam = synth.gaussian_problem_device(c["m"], c["n"], c["nnz"], c["seed"], device=dev)
+    torch.cuda.synchronize()
+    out = {"workload": f"gaussian {c['m']}x{c['n']} CN(0,1/{c['m']}), {c['nnz']} nonzeros, 30 dB, "
+                       f"seed {c['seed']} (device generator), lambda 0.05 max|H^H g|, rho {c['rho']}",
+           "iters_per_call": iters, "splits": {}}
+
+    def measure(M, N, form):
+        t0 = time.perf_counter()
+        with torch.cuda.stream(stream):
+            s = pkg.Solver(H, g, M, N, lam, c["rho"], stream=stream, form=form)
+        torch.cuda.synchronize()
+        setup_ms = (time.perf_counter() - t0) * 1e3
+        info = s.info()
+        s.iterate(3)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.iterate(iters)
+        b.record(stream)
+        barrier()
+        if s.status() != 0:
+            raise RuntimeError(f"device status after the {form} {M}x{N} run")
+        us = a.elapsed_time(b) / iters * 1e3
+        state = (2 * M + 2) * c["n"] * 8
+        if form == "direct":
+            passes = 0 if N == 1 else 2
+            alg = passes * info["h_bytes"] + info["factor_bytes"] + state + (M * c["n"] * 8 if N == 1 else 0)
+        else:
+            alg = 2 * info["h_bytes"] + info["factor_bytes"] + state
+        s.close()
+        return {"factor_form": form, "us_per_iter": us, "iters_per_s": 1e6 / us, "alg_bytes_per_iter": alg,
+                "gbs": alg / us / 1e3, "frac": alg / us / 1e3 / peaks["hbm_gbs"],
+                "factor_bytes": info["factor_bytes"], "setup_ms": setup_ms,
+                "setup_gram_ms": info["setup_gram_ms"], "setup_factor_ms": info["setup_factor_ms"]}
+
+    for M, N in c["splits"]:
+        out["splits"][f"{M}x{N}"] = measure(M, N, "direct")
+    lem = measure(8, 1, "lemma")
+    out["lemma_8x1"] = lem
+    out["speedup_8x1"] = lem["us_per_iter"] / out["splits"]["8x1"]["us_per_iter"]
+    del H, g
+    torch.cuda.empty_cache()
+    return out
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -747,6 +806,9 @@ def run_ours(args) -> None:
     uneven = None
     if not args.no_uneven:
         uneven = uneven_problems(pkg, stream, dev, barrier, peaks=load_peaks())
+    direct = None
+    if not args.no_direct:
+        direct = direct_form(pkg, stream, dev, barrier, peaks=load_peaks())
 
     phases = None
     if args.trace > 0:
@@ -837,6 +899,8 @@ def run_ours(args) -> None:
         line["differentiable"] = diff
     if uneven is not None:
         line["uneven_problems"] = uneven
+    if direct is not None:
+        line["direct_form"] = direct
     if phases is not None:
         line["phases"] = phases
     for s in solvers:

@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define ADMM_ABI_VERSION 3
+#define ADMM_ABI_VERSION 4
 
 /* status codes */
 #define ADMM_OK            0  /* success */
@@ -99,6 +99,12 @@ extern "C" {
                                      more device memory and is kept until admm_destroy;
                                      admm_set_rho refactors both.  Synchronises the device. */
 
+/* factor form of the block update (admm_setup_form) */
+#define ADMM_FORM_LEMMA   0   /* m_b x m_b factor K_b^{-1} = (rho I + H_b H_b^H)^{-1}, any block shape */
+#define ADMM_FORM_DIRECT  1   /* n_b x n_b factor (H_b^H H_b + rho I)^{-1}, column blocks <= 12288 wide */
+#define ADMM_FORM_AUTO    2   /* the paper's rule (Section III-B): DIRECT when every block has at
+                                 least as many rows as columns (and fits), else LEMMA */
+
 typedef struct admm_problem admm_t;
 
 /* Sizes and plan of a handle (admm_get_info). */
@@ -123,6 +129,8 @@ typedef struct admm_info {
     int32_t h16_ready;        /* 1 once the FP16 copy and its factors exist */
     int64_t h16_bytes;        /* bytes of H streamed by one pass in FP16 (m * n * 4), 0 if none */
     int64_t l2_keep_bytes;    /* current ADMM_OPT_L2_KEEP_BYTES (admm_tune may change it) */
+    int32_t factor_form;      /* ADMM_FORM_LEMMA or ADMM_FORM_DIRECT */
+    int32_t reserved;         /* 0 */
 } admm_info_t;
 
 /* Launch plan of the iteration kernel, computed on the host (admm_plan). */
@@ -203,6 +211,34 @@ int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks,
 int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
                int32_t row_blocks, int32_t col_blocks, double lambda, double rho,
                int32_t h_dtype, void* stream);
+
+/* admm_setup with a choice of factor form.  ADMM_FORM_LEMMA is admm_setup.
+ * ADMM_FORM_DIRECT caches, for every block, the n_b x n_b inverse
+ *     L_b = (H_b^H H_b + rho I)^{-1}
+ * (the original inversion of Eq. x_solution_columns, which Section III-B
+ * prefers when N_m > N_p / N), formed with the same FP32-product / FP64-sum
+ * Gram kernels and FP64 Cholesky inverse over the blocks of H^H, stored as
+ * complex64.  Each iteration then computes
+ *     q_b    = H_b^H gt_b + rho (v_j - s_j^i)     (one pass over H_b; with one
+ *                                                  column block gt_b = g_i and
+ *                                                  H_b^H g_i is computed once
+ *                                                  per data vector, so H is not
+ *                                                  read at all)
+ *     u_b    = L_b q_b
+ *     ghat_b = H_b u_b                            (one pass, col_blocks > 1)
+ * and the same v, s update and residual record as the lemma form: the
+ * iterates are the same algorithm's, so every getter, admm_set_g /
+ * _lambda / _rho (which refactors L_b), checkpoints and admm_solve behave
+ * as documented for admm_setup.  The persistent-kernel options
+ * (ADMM_OPT_H_FP16, ADMM_OPT_RECORD_ITERS, ADMM_OPT_TRACE_ITERS,
+ * ADMM_OPT_BARRIER_EXTRA) and admm_backward return ADMM_EUNSUPPORTED, the L2
+ * options have no effect, admm_tune does nothing and admm_group_setup
+ * refuses the handle.  Column blocks wider than 12288 columns return
+ * ADMM_EUNSUPPORTED.  ADMM_FORM_AUTO picks DIRECT when every block has
+ * m_b >= n_b and fits, else LEMMA; admm_get_info reports the choice. */
+int admm_setup_form(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
+                    int32_t row_blocks, int32_t col_blocks, double lambda, double rho,
+                    int32_t h_dtype, int32_t form, void* stream);
 
 /* Run `iters` >= 0 iterations, each the block update of Sections III-A..C:
  *   z_b   = v_b - s_b

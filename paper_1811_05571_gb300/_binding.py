@@ -21,7 +21,8 @@ ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED = 5, 6, 7, 8
 ADMM_C64, ADMM_C128 = 0, 1
 ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS = 1, 2, 3, 4
 ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ADMM_OPT_L2_PREFETCH_BYTES, ADMM_OPT_RECORD_ITERS = 5, 6, 7, 8
-ABI_VERSION = 3
+ADMM_FORM_LEMMA, ADMM_FORM_DIRECT, ADMM_FORM_AUTO = 0, 1, 2
+ABI_VERSION = 4
 
 
 class AdmmInfo(ctypes.Structure):
@@ -33,7 +34,8 @@ class AdmmInfo(ctypes.Structure):
                 ("num_sms", c_int32), ("h_bytes", c_int64), ("factor_bytes", c_int64),
                 ("state_bytes", c_int64), ("setup_gram_ms", c_double),
                 ("setup_factor_ms", c_double), ("h_fp16", c_int32), ("h16_ready", c_int32),
-                ("h16_bytes", c_int64), ("l2_keep_bytes", c_int64)]
+                ("h16_bytes", c_int64), ("l2_keep_bytes", c_int64), ("factor_form", c_int32),
+                ("reserved", c_int32)]
 
     def as_dict(self) -> dict:
         return {name.rstrip("_"): getattr(self, name) for name, _ in self._fields_}
@@ -75,6 +77,8 @@ SIGNATURES = {
                             ctypes.POINTER(AdmmPlan), ctypes.POINTER(c_int32)]),
     "admm_setup": (c_int32, [ctypes.POINTER(c_void_p), c_void_p, c_void_p, c_int64, c_int64,
                              c_int32, c_int32, c_double, c_double, c_int32, c_void_p]),
+    "admm_setup_form": (c_int32, [ctypes.POINTER(c_void_p), c_void_p, c_void_p, c_int64, c_int64,
+                                  c_int32, c_int32, c_double, c_double, c_int32, c_int32, c_void_p]),
     "admm_iterate": (c_int32, [c_void_p, c_int32, c_void_p]),
     "admm_solve": (c_int32, [c_void_p, c_int32, c_double, c_double, ctypes.POINTER(c_int32),
                              c_void_p]),
@@ -226,6 +230,14 @@ def admm_setup(H, g, m: int, n: int, row_blocks: int, col_blocks: int, lam: floa
     h = c_void_p()
     _check(load().admm_setup(ctypes.byref(h), _ptr(H), _ptr(g), m, n, row_blocks, col_blocks,
                              lam, rho, h_dtype, _stream(stream)))
+    return h.value
+
+
+def admm_setup_form(H, g, m: int, n: int, row_blocks: int, col_blocks: int, lam: float, rho: float,
+                    h_dtype: int = ADMM_C64, form: int = ADMM_FORM_LEMMA, stream=None) -> int:
+    h = c_void_p()
+    _check(load().admm_setup_form(ctypes.byref(h), _ptr(H), _ptr(g), m, n, row_blocks, col_blocks,
+                                  lam, rho, h_dtype, form, _stream(stream)))
     return h.value
 
 

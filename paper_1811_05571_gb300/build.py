@@ -25,7 +25,7 @@ LIB = os.path.join(PKG, "libadmm.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 SOURCES = ["admm_api.cu", "admm_iterate.cu", "admm_factor.cu", "admm_misc.cu", "admm_noalloc.cu",
-           "admm_batch_kernels.cu", "admm_batch_host.cu", "admm_backward.cu"]
+           "admm_batch_kernels.cu", "admm_batch_host.cu", "admm_backward.cu", "admm_direct.cu"]
 HEADERS = ["admm_internal.h", "ptx.cuh", "admm_batch.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",

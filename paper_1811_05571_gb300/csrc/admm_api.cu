@@ -24,6 +24,24 @@ int round_up(int64_t x, int64_t q) { return static_cast<int>((x + q - 1) / q * q
 
 }  // namespace
 
+// device buffers and launch geometry of the direct form
+struct DirectState {
+    float2 *C = nullptr, *Q = nullptr, *part = nullptr;
+    unsigned* cnt = nullptr;       // column tiles, update chunks, two global counters
+    int* ints = nullptr;           // chunk_off (N + 1), L_pitch (P)
+    long long* L_off = nullptr;    // P
+    double* res_chunk = nullptr;
+    int* stop_pending = nullptr;
+    int npitch = 0, njmax = 0, S = 1, ccn = 1, fcn = 1, rtn = 1, nchunks = 0, ncnt = 0;
+    int64_t bytes = 0;
+    bool c_valid = false;          // C = H_i^H g_i matches g (one column block)
+    cudaStream_t cap = nullptr;    // capture stream of the iteration graphs
+    cudaGraphExec_t g1 = nullptr, g16 = nullptr;   // one and sixteen iterations
+    double key[6] = {0, 0, 0, 0, 0, 0};
+    const void* key_hist = nullptr;
+    bool key_set = false;
+};
+
 struct admm_problem {
     int device = 0;
     int num_sms = 0;
@@ -80,6 +98,8 @@ struct admm_problem {
     int pending = 0;     // the last launch's final residual record has not been summed yet
     int64_t l2_keep_bytes = 52LL << 20;  // H bytes per pass kept for the reversed next pass
     int64_t l2_prefetch_bytes = 0;       // H bytes prefetched into L2 ahead of each pass
+    int form = ADMM_FORM_LEMMA;          // factor form of every block
+    DirectState dir;
     int broken = 0;      // sticky error that blocks further iterations
     double gram_ms = 0.0, factor_ms = 0.0;
     std::string err;
@@ -124,6 +144,13 @@ void free_all(admm_t* h) {
                     h->brbar, h->bkappa, h->bupd};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    DirectState& d = h->dir;
+    void* dptrs[] = {d.C, d.Q, d.part, d.cnt, d.ints, d.L_off, d.res_chunk, d.stop_pending};
+    for (void* p : dptrs)
+        if (p) cudaFree(p);
+    if (d.g1) cudaGraphExecDestroy(d.g1);
+    if (d.g16) cudaGraphExecDestroy(d.g16);
+    if (d.cap) cudaStreamDestroy(d.cap);
 }
 
 }  // namespace
@@ -408,31 +435,22 @@ int copy_vector_in(admm_t* h, float2* dst, const void* src, int64_t count, int d
     return ADMM_OK;
 }
 
-int build_factors(admm_t* h, cudaStream_t st, const float2* H, float2* kinv, bool timed) {
-    const Plan& pl = h->plan;
-    const int T = (pl.mimax + admm::kTile - 1) / admm::kTile;
+// Gram products and FP64 Cholesky inverse of every block of the factor
+// problem f (f.A, f.W are allocated here); `dim` is the largest factor edge.
+int run_factor(admm_t* h, cudaStream_t st, admm::FactorArgs f, int dim, float2* kinv, bool timed) {
+    const int T = (dim + admm::kTile - 1) / admm::kTile;
     const size_t S = static_cast<size_t>(T) * admm::kTile;
-    const int nb = h->M * h->N;
+    const int nb = f.M * f.N;
     double2 *A = nullptr, *W = nullptr;
     if (dalloc(&A, S * S * nb) != cudaSuccess || dalloc(&W, S * S * nb) != cudaSuccess) {
         if (A) cudaFree(A);
         return fail(h, ADMM_ENOMEM, "cannot allocate %.1f MB of FP64 factor workspace",
                     2.0 * S * S * nb * 16 / 1e6);
     }
-    admm::FactorArgs f;
-    f.m = static_cast<int>(h->m);
-    f.ld = pl.ld;
-    f.M = h->M;
-    f.N = h->N;
     f.T = T;
-    f.row_off = h->row_off_d;
-    f.col_off = h->col_off_d;
-    f.H = H;
     f.A = A;
     f.W = W;
     f.kinv = kinv;
-    f.kinv_off = h->kinv_off_d;
-    f.kinv_pitch = h->kinv_pitch_d;
     f.rho = h->rho;
     f.status = h->status;
     cudaEvent_t e0, e1, e2;
@@ -465,9 +483,52 @@ int build_factors(admm_t* h, cudaStream_t st, const float2* H, float2* kinv, boo
     int st_code = 0;
     CK(h, cudaMemcpy(&st_code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st_code == ADMM_ENOTPD)
-        return fail(h, ADMM_ENOTPD, "a block rho I + H_b H_b^H is not positive definite in FP64");
+        return fail(h, ADMM_ENOTPD, "a block factor is not positive definite in FP64");
     if (st_code != 0) return fail(h, st_code, "factor kernels raised status %d", st_code);
     return ADMM_OK;
+}
+
+// Factors of the handle's form from the complex64 matrix H (m x ld):
+//  lemma:  K_b^{-1} = (rho I + H_b H_b^H)^{-1}, m_i x m_i;
+//  direct: L_b = (H_b^H H_b + rho I)^{-1}, n_j x n_j, the same Gram and
+//          inverse taken over the blocks of H^H (block (j, i) of H^H is H_b^H).
+int build_factors(admm_t* h, cudaStream_t st, const float2* H, float2* kinv, bool timed) {
+    admm::FactorArgs f;
+    std::memset(&f, 0, sizeof f);
+    if (h->form != ADMM_FORM_DIRECT) {
+        f.m = static_cast<int>(h->m);
+        f.ld = h->plan.ld;
+        f.M = h->M;
+        f.N = h->N;
+        f.row_off = h->row_off_d;
+        f.col_off = h->col_off_d;
+        f.H = H;
+        f.kinv_off = h->kinv_off_d;
+        f.kinv_pitch = h->kinv_pitch_d;
+        return run_factor(h, st, f, h->plan.mimax, kinv, timed);
+    }
+    const int64_t ldT = round_up(h->m, 32);
+    float2* HT = nullptr;
+    if (dalloc(&HT, static_cast<size_t>(ldT) * h->n) != cudaSuccess)
+        return fail(h, ADMM_ENOMEM, "no room for the conjugate transpose of H (%.1f MB)", ldT * h->n * 8 / 1e6);
+    cudaError_t e = cudaMemsetAsync(HT, 0, static_cast<size_t>(ldT) * h->n * sizeof(float2), st);
+    if (e == cudaSuccess) e = admm::launch_conj_transpose(H, h->m, h->n, h->plan.ld, HT, ldT, st);
+    if (e != cudaSuccess) {
+        cudaFree(HT);
+        return cuda_fail(h, e, "conjugate transpose of H");
+    }
+    f.m = static_cast<int>(h->n);
+    f.ld = static_cast<int>(ldT);
+    f.M = h->N;
+    f.N = h->M;
+    f.row_off = h->col_off_d;
+    f.col_off = h->row_off_d;
+    f.H = HT;
+    f.kinv_off = h->kinv_off_d;      // indexed by the H^H block (j, i)
+    f.kinv_pitch = h->kinv_pitch_d;
+    const int code = run_factor(h, st, f, h->dir.njmax, kinv, timed);
+    cudaFree(HT);
+    return code;
 }
 
 // factors of the matrix the FP16 copy encodes (dequantised into a scratch copy)
@@ -563,11 +624,170 @@ int zero_state(admm_t* h, cudaStream_t st) {
     CK(h, cudaMemsetAsync(h->stop_flag, 0, sizeof(int), st));
     CK(h, cudaMemsetAsync(h->k_done, 0, sizeof(long long), st));
     CK(h, cudaMemsetAsync(h->hist, 0, static_cast<size_t>(h->hist_cap) * 5 * sizeof(double), st));
+    if (h->form == ADMM_FORM_DIRECT) {
+        CK(h, cudaMemsetAsync(h->dir.cnt, 0, static_cast<size_t>(h->dir.ncnt) * sizeof(unsigned), st));
+        CK(h, cudaMemsetAsync(h->dir.stop_pending, 0, sizeof(int), st));
+    }
     h->k = 0;
     h->broken = 0;
     h->pending = 0;
     h->rec_valid = h->rec_cap > 0;
     h->rec_f16 = h->use_f16;
+    return ADMM_OK;
+}
+
+// buffers of the direct form; off / pitch locate the factor of block p = i * N + j
+int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector<int>& pitch, int njmax) {
+    DirectState& d = h->dir;
+    const int P = h->M * h->N;
+    const int mimax = h->plan.mimax;
+    d.njmax = njmax;
+    d.npitch = round_up(njmax, 4);
+    d.ccn = (njmax + admm::kDirColTile - 1) / admm::kDirColTile;
+    d.fcn = (njmax + admm::kDirChunk - 1) / admm::kDirChunk;
+    d.rtn = (mimax + admm::kDirRowTile - 1) / admm::kDirRowTile;
+    // row splits of the column pass: about four CTAs per SM, at least 64 rows
+    // per split where the blocks allow, at most 4096 (the staged gt_b)
+    int S = (4 * h->num_sms + P * d.ccn - 1) / (P * d.ccn);
+    S = std::min(S, std::max(1, mimax / 64));
+    S = std::max(S, (mimax + 4095) / 4096);
+    d.S = std::max(S, 1);
+    std::vector<int> ints(h->N + 1, 0);
+    for (int j = 0; j < h->N; ++j)
+        ints[j + 1] = ints[j] + (h->col_off[j + 1] - h->col_off[j] + admm::kDirChunk - 1) / admm::kDirChunk;
+    d.nchunks = ints[h->N];
+    ints.insert(ints.end(), pitch.begin(), pitch.end());
+    d.ncnt = P * d.ccn + d.nchunks + 2;
+    const size_t vec = static_cast<size_t>(P) * d.npitch;
+    // the column pass writes partials in both uses (q_b every iteration with
+    // several column blocks, C = H_i^H g_i once per data vector with one)
+    const size_t nc = h->N == 1 ? vec : 1, np = static_cast<size_t>(d.S) * vec;
+    const bool ok = dalloc(&d.C, nc) == cudaSuccess && dalloc(&d.Q, vec) == cudaSuccess &&
+                    dalloc(&d.part, np) == cudaSuccess && dalloc(&d.cnt, d.ncnt) == cudaSuccess &&
+                    dalloc(&d.ints, ints.size()) == cudaSuccess && dalloc(&d.L_off, off.size()) == cudaSuccess &&
+                    dalloc(&d.res_chunk, static_cast<size_t>(d.nchunks) * 5) == cudaSuccess &&
+                    dalloc(&d.stop_pending, 1) == cudaSuccess;
+    if (!ok) return ADMM_ENOMEM;
+    // Q and C padding entries stay zero (the factor pass reads whole pairs)
+    CK(h, cudaMemset(d.C, 0, nc * sizeof(float2)));
+    CK(h, cudaMemset(d.Q, 0, vec * sizeof(float2)));
+    CK(h, cudaMemset(d.cnt, 0, static_cast<size_t>(d.ncnt) * sizeof(unsigned)));
+    CK(h, cudaMemset(d.stop_pending, 0, sizeof(int)));
+    CK(h, cudaMemcpy(d.ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
+    CK(h, cudaMemcpy(d.L_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
+    d.bytes = static_cast<int64_t>((nc + vec + np) * sizeof(float2) + d.nchunks * 5 * sizeof(double));
+    return ADMM_OK;
+}
+
+admm::DirectArgs direct_args(admm_t* h, int check_stop, double eps_abs, double eps_rel) {
+    const DirectState& d = h->dir;
+    admm::DirectArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.m = static_cast<int>(h->m);
+    a.n = static_cast<int>(h->n);
+    a.ld = h->plan.ld;
+    a.M = h->M;
+    a.N = h->N;
+    a.P = h->M * h->N;
+    a.npitch = d.npitch;
+    a.njmax = d.njmax;
+    a.mimax = h->plan.mimax;
+    a.row_off = h->row_off_d;
+    a.col_off = h->col_off_d;
+    a.H = h->H;
+    a.g = h->g;
+    a.v = h->v;
+    a.s = h->s;
+    a.u = h->u;
+    a.ghat = h->ghat;
+    a.L = h->kinv;
+    a.L_off = d.L_off;
+    a.L_pitch = d.ints + (h->N + 1);
+    a.C = d.C;
+    a.Q = d.Q;
+    a.part = d.part;
+    a.S = d.S;
+    a.ccn = d.ccn;
+    a.fcn = d.fcn;
+    a.rtn = d.rtn;
+    a.cnt_cols = d.cnt;
+    a.cnt_upd = d.cnt + a.P * d.ccn;
+    a.cnt_glob = d.cnt + a.P * d.ccn + d.nchunks;
+    a.chunk_off = d.ints;
+    a.nchunks = d.nchunks;
+    a.res_chunk = d.res_chunk;
+    a.hist = h->hist;
+    a.hist_cap = h->hist_cap;
+    a.k_done = h->k_done;
+    a.status = h->status;
+    a.stop_flag = h->stop_flag;
+    a.stop_pending = d.stop_pending;
+    a.check_stop = check_stop;
+    a.eps_abs = eps_abs;
+    a.eps_rel = eps_rel;
+    a.rho = static_cast<float>(h->rho);
+    a.rho_d = h->rho;
+    a.kappa = static_cast<float>(h->lambda / (h->M * h->rho));
+    a.inv_M = 1.0f / static_cast<float>(h->M);
+    return a;
+}
+
+void drop_direct_graphs(DirectState& d) {
+    if (d.g1) cudaGraphExecDestroy(d.g1);
+    if (d.g16) cudaGraphExecDestroy(d.g16);
+    d.g1 = d.g16 = nullptr;
+}
+
+// `iters` iterations of the direct form: per iteration the column pass (or,
+// with one column block, q = C + rho z), the factor pass with the update, and
+// with several column blocks the row pass.  Launched as captured graphs of
+// one and sixteen iterations, re-captured when a scalar argument changes.
+int run_direct(admm_t* h, int iters, int check_stop, double eps_abs, double eps_rel, cudaStream_t st) {
+    DirectState& d = h->dir;
+    const admm::DirectArgs a = direct_args(h, check_stop, eps_abs, eps_rel);
+    if (h->N == 1 && !d.c_valid) {
+        CK(h, admm::launch_dir_cols(a, 1, st));
+        d.c_valid = true;
+    }
+    const double key[6] = {h->rho, h->lambda, static_cast<double>(check_stop), eps_abs, eps_rel,
+                           static_cast<double>(h->hist_cap)};
+    if (!d.key_set || std::memcmp(key, d.key, sizeof key) != 0 || d.key_hist != h->hist) {
+        drop_direct_graphs(d);
+        std::memcpy(d.key, key, sizeof key);
+        d.key_hist = h->hist;
+        d.key_set = true;
+    }
+    auto capture = [&](int count, cudaGraphExec_t* out) -> cudaError_t {
+        cudaError_t e = cudaStreamBeginCapture(d.cap, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return e;
+        for (int q = 0; q < count && e == cudaSuccess; ++q) {
+            if (h->N == 1) {
+                e = admm::launch_dir_q(a, d.cap);
+                if (e == cudaSuccess) e = admm::launch_dir_factor(a, d.cap);
+            } else {
+                e = admm::launch_dir_cols(a, 0, d.cap);
+                if (e == cudaSuccess) e = admm::launch_dir_factor(a, d.cap);
+                if (e == cudaSuccess) e = admm::launch_dir_rows(a, d.cap);
+            }
+        }
+        cudaGraph_t graph = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(d.cap, &graph);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = cudaGraphInstantiate(out, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        return e;
+    };
+    int left = iters;
+    if (left >= 16) {
+        if (!d.g16) CK(h, capture(16, &d.g16));
+        for (; left >= 16; left -= 16) CK(h, cudaGraphLaunch(d.g16, st));
+    }
+    if (left > 0) {
+        if (!d.g1) CK(h, capture(1, &d.g1));
+        for (; left > 0; --left) CK(h, cudaGraphLaunch(d.g1, st));
+    }
+    h->k += iters;
+    h->pending = 0;   // the direct form writes each record inside the iteration
     return ADMM_OK;
 }
 
@@ -868,14 +1088,35 @@ int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks, int3
 int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
                int32_t row_blocks, int32_t col_blocks, double lambda, double rho,
                int32_t h_dtype, void* stream) {
+    return admm_setup_form(out, H, g, m, n, row_blocks, col_blocks, lambda, rho, h_dtype, ADMM_FORM_LEMMA,
+                           stream);
+}
+
+int admm_setup_form(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
+                    int32_t row_blocks, int32_t col_blocks, double lambda, double rho,
+                    int32_t h_dtype, int32_t form, void* stream) {
     if (!out) return fail(nullptr, ADMM_EINVAL, "out is NULL");
     *out = nullptr;
     if (!H || !g) return fail(nullptr, ADMM_EINVAL, "H and g must not be NULL");
     int code = validate(m, n, row_blocks, col_blocks, lambda, rho, h_dtype);
     if (code) return code;
+    if (form != ADMM_FORM_LEMMA && form != ADMM_FORM_DIRECT && form != ADMM_FORM_AUTO)
+        return fail(nullptr, ADMM_EINVAL, "form must be ADMM_FORM_LEMMA, ADMM_FORM_DIRECT or ADMM_FORM_AUTO");
     std::vector<int> ro, co;
     admm::balanced_offsets(m, row_blocks, ro);
     admm::balanced_offsets(n, col_blocks, co);
+    int mimin = static_cast<int>(m), mimax = 0, njmax = 0;
+    for (int i = 0; i < row_blocks; ++i) {
+        mimin = std::min(mimin, ro[i + 1] - ro[i]);
+        mimax = std::max(mimax, ro[i + 1] - ro[i]);
+    }
+    for (int j = 0; j < col_blocks; ++j) njmax = std::max(njmax, co[j + 1] - co[j]);
+    if (form == ADMM_FORM_AUTO)   // Section III-B: the lemma only when blocks have fewer rows than columns
+        form = (mimin >= njmax && njmax <= admm::kDirMaxCols) ? ADMM_FORM_DIRECT : ADMM_FORM_LEMMA;
+    if (form == ADMM_FORM_DIRECT && njmax > admm::kDirMaxCols)
+        return fail(nullptr, ADMM_EUNSUPPORTED, "the direct form takes column blocks of at most %d columns",
+                    admm::kDirMaxCols);
+    const bool direct = form == ADMM_FORM_DIRECT;
 
     admm_t* h = new admm_t();
     h->m = m;
@@ -886,6 +1127,7 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     h->rho = rho;
     h->row_off = ro;
     h->col_off = co;
+    h->form = form;
     cudaStream_t st = as_stream(stream);
     auto bail = [&](int c) {
         g_setup_error = h->err;
@@ -899,33 +1141,61 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, h->device);
     cudaDeviceGetAttribute(&h->smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
     cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
-    if (!coop) return bail(fail(h, ADMM_EUNSUPPORTED, "device has no cooperative launch"));
-    const char* why = "";
-    code = admm::make_plan(m, n, row_blocks, col_blocks, ro, co, h->num_sms, h->smem_optin, h->plan, &why);
-    if (code) return bail(fail(h, code, "%s", why));
+    const int P = row_blocks * col_blocks;
+    if (!direct) {
+        if (!coop) return bail(fail(h, ADMM_EUNSUPPORTED, "device has no cooperative launch"));
+        const char* why = "";
+        code = admm::make_plan(m, n, row_blocks, col_blocks, ro, co, h->num_sms, h->smem_optin, h->plan, &why);
+        if (code) return bail(fail(h, code, "%s", why));
+    } else {
+        // no persistent kernel: the plan only carries the pitch and the block sizes
+        h->plan = Plan();
+        h->plan.ld = round_up(n, 32);
+        h->plan.P = 1;
+        h->plan.mimax = mimax;
+        h->plan.kpmax = round_up(mimax, 4);
+    }
     const Plan& pl = h->plan;
 
-    // factor layout: block b = (i, j) holds m_i x kp_i complex64, kp_i = m_i rounded up to 4
-    h->kinv_off.resize(row_blocks * col_blocks);
-    h->kinv_pitch.resize(row_blocks * col_blocks);
+    // factor layout.  lemma: block b = (i, j) holds m_i x kp_i complex64,
+    // kp_i = m_i rounded up to 4.  direct: n_j x kp_j, stored in the order of
+    // the blocks of H^H (b' = j * M + i), which the factor kernels index
+    h->kinv_off.resize(P);
+    h->kinv_pitch.resize(P);
+    std::vector<long long> dir_off(P);
+    std::vector<int> dir_pitch(P);
     int64_t kel = 0;
-    for (int i = 0; i < row_blocks; ++i)
-        for (int j = 0; j < col_blocks; ++j) {
-            const int mi = ro[i + 1] - ro[i];
-            const int kp = round_up(mi, 4);
-            h->kinv_off[i * col_blocks + j] = kel;
-            h->kinv_pitch[i * col_blocks + j] = kp;
-            kel += static_cast<int64_t>(mi) * kp;
-        }
+    if (!direct) {
+        for (int i = 0; i < row_blocks; ++i)
+            for (int j = 0; j < col_blocks; ++j) {
+                const int mi = ro[i + 1] - ro[i];
+                const int kp = round_up(mi, 4);
+                h->kinv_off[i * col_blocks + j] = kel;
+                h->kinv_pitch[i * col_blocks + j] = kp;
+                kel += static_cast<int64_t>(mi) * kp;
+            }
+    } else {
+        for (int i = 0; i < row_blocks; ++i)
+            for (int j = 0; j < col_blocks; ++j) {
+                const int nj = co[j + 1] - co[j];
+                const int kp = round_up(nj, 4);
+                dir_off[i * col_blocks + j] = kel;
+                dir_pitch[i * col_blocks + j] = kp;
+                h->kinv_off[j * row_blocks + i] = kel;
+                h->kinv_pitch[j * row_blocks + i] = kp;
+                kel += static_cast<int64_t>(nj) * kp;
+            }
+    }
     h->kinv_elems = kel;
 
     const size_t ld = pl.ld;
     const size_t Nm = static_cast<size_t>(col_blocks) * m;
+    const size_t scratch = direct ? 1 : Nm;   // gt, r, w and the partials of the persistent kernel
     bool ok = dalloc(&h->H, ld * m) == cudaSuccess && dalloc(&h->g, m) == cudaSuccess &&
               dalloc(&h->v, ld) == cudaSuccess && dalloc(&h->s, ld * row_blocks) == cudaSuccess &&
               dalloc(&h->u, ld * row_blocks) == cudaSuccess && dalloc(&h->ghat, 2 * Nm) == cudaSuccess &&
-              dalloc(&h->gt, Nm) == cudaSuccess && dalloc(&h->r, Nm) == cudaSuccess &&
-              dalloc(&h->w, Nm) == cudaSuccess && dalloc(&h->part, Nm * pl.P) == cudaSuccess &&
+              dalloc(&h->gt, scratch) == cudaSuccess && dalloc(&h->r, scratch) == cudaSuccess &&
+              dalloc(&h->w, scratch) == cudaSuccess && dalloc(&h->part, scratch * pl.P) == cudaSuccess &&
               dalloc(&h->kinv, kel) == cudaSuccess &&
               dalloc(&h->kinv_off_d, h->kinv_off.size()) == cudaSuccess &&
               dalloc(&h->res_part, static_cast<size_t>(pl.P) * 8) == cudaSuccess &&
@@ -944,7 +1214,9 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
                  o_nj = put(pl.cta_nj), o_jl = put(pl.j_cta_lo), o_jh = put(pl.j_cta_hi),
                  o_sl = put(pl.solve_lo), o_kp = put(h->kinv_pitch);
     ok = ok && dalloc(&h->ints_d, ints.size()) == cudaSuccess;
-    if (!ok) return bail(fail(h, ADMM_ENOMEM, "device allocation failed (%.1f MB for H)", ld * m * 8 / 1e6));
+    if (ok && direct) ok = alloc_direct(h, dir_off, dir_pitch, njmax) == ADMM_OK;
+    if (!ok) return bail(fail(h, ADMM_ENOMEM, "device allocation failed (%.1f MB for H, %.1f MB of factors)",
+                              ld * m * 8 / 1e6, kel * 8 / 1e6));
     h->row_off_d = h->ints_d + o_row;
     h->col_off_d = h->ints_d + o_col;
     h->cta_col_d = h->ints_d + o_cta;
@@ -957,7 +1229,8 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     h->j_cta_hi_d = h->ints_d + o_jh;
     h->solve_lo_d = h->ints_d + o_sl;
     h->kinv_pitch_d = h->ints_d + o_kp;
-    h->state_bytes = static_cast<int64_t>((ld * (1 + 2 * row_blocks) + 5 * Nm + Nm * pl.P) * sizeof(float2));
+    h->state_bytes = static_cast<int64_t>((ld * (1 + 2 * row_blocks) + 2 * Nm + 3 * scratch + scratch * pl.P) *
+                                          sizeof(float2)) + h->dir.bytes;
 
 #define SETUP_CK(call)                                             \
     do {                                                           \
@@ -995,14 +1268,19 @@ int admm_setup(admm_t** out, const void* H, const void* g, int64_t m, int64_t n,
     if (flag) return bail(fail(h, ADMM_ENONFINITE, "H or g holds NaN or Inf"));
     code = build_factors(h, st, h->H, h->kinv, true);
     if (code) return bail(code);
-    code = encode_tensor_map(h);
-    if (code) return bail(code);
-    // opt into the device maximum: several handles share one kernel instance
-    SETUP_CK(admm::prepare_iterate(pl.chunks, h->smem_optin));
-    int per_sm = 0;
-    admm::max_coresident_iterate(pl.chunks, pl.smem, &per_sm);
-    if (per_sm * h->num_sms < pl.P)
-        return bail(fail(h, ADMM_EUNSUPPORTED, "iteration kernel cannot keep %d CTAs resident", pl.P));
+    if (!direct) {
+        code = encode_tensor_map(h);
+        if (code) return bail(code);
+        // opt into the device maximum: several handles share one kernel instance
+        SETUP_CK(admm::prepare_iterate(pl.chunks, h->smem_optin));
+        int per_sm = 0;
+        admm::max_coresident_iterate(pl.chunks, pl.smem, &per_sm);
+        if (per_sm * h->num_sms < pl.P)
+            return bail(fail(h, ADMM_EUNSUPPORTED, "iteration kernel cannot keep %d CTAs resident", pl.P));
+    } else {
+        SETUP_CK(admm::prepare_direct(h->smem_optin));
+        SETUP_CK(cudaStreamCreateWithFlags(&h->dir.cap, cudaStreamNonBlocking));
+    }
     code = zero_state(h, st);
     if (code) return bail(code);
     SETUP_CK(cudaStreamSynchronize(st));
@@ -1015,6 +1293,7 @@ int admm_iterate(admm_t* h, int32_t iters, void* stream) {
     if (!h || iters < 0) return h ? fail(h, ADMM_EINVAL, "iters must be >= 0") : ADMM_EINVAL;
     if (h->broken) return fail(h, ADMM_ECUDA, "handle is in an error state; call admm_reset");
     if (iters == 0) return ADMM_OK;
+    if (h->form == ADMM_FORM_DIRECT) return run_direct(h, iters, 0, 0.0, 0.0, as_stream(stream));
     return run_kernel(h, iters, 0, 0.0, 0.0, as_stream(stream));
 }
 
@@ -1027,6 +1306,25 @@ int admm_solve(admm_t* h, int32_t max_iter, double eps_abs, double eps_rel, int3
     if (iters_done) *iters_done = 0;
     if (max_iter == 0) return ADMM_OK;
     cudaStream_t st = as_stream(stream);
+    if (h->form == ADMM_FORM_DIRECT) {
+        // batches of 64 iterations; the kernels of iterations after the
+        // stopping test passed return at once
+        CK(h, cudaMemsetAsync(h->stop_flag, 0, sizeof(int), st));
+        CK(h, cudaMemsetAsync(h->dir.stop_pending, 0, sizeof(int), st));
+        for (int left = max_iter; left > 0;) {
+            const int batch = std::min(left, 64);
+            const int c = run_direct(h, batch, 1, eps_abs, eps_rel, st);
+            if (c) return c;
+            left -= batch;
+            int stop = 0;
+            CK(h, cudaMemcpyAsync(&stop, h->stop_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+            CK(h, cudaStreamSynchronize(st));
+            if (stop) break;
+        }
+        const int c = device_status(h, st);
+        if (iters_done) *iters_done = static_cast<int32_t>(h->k - k0);
+        return c;
+    }
     int code = run_kernel(h, max_iter, 1, eps_abs, eps_rel, st);
     if (code) return code;
     {
@@ -1075,6 +1373,7 @@ int admm_set_g(admm_t* h, const void* g, int32_t h_dtype, void* stream) {
     if (!h || !g) return h ? fail(h, ADMM_EINVAL, "g is NULL") : ADMM_EINVAL;
     if (h_dtype != ADMM_C64 && h_dtype != ADMM_C128) return fail(h, ADMM_EINVAL, "bad dtype");
     if (h->k > 0) h->rec_valid = false;
+    h->dir.c_valid = false;
     return copy_vector_in(h, h->g, g, h->m, h_dtype, as_stream(stream));
 }
 
@@ -1181,11 +1480,24 @@ int admm_get_info(const admm_t* h, admm_info_t* info) {
     info->h16_ready = h->H16 ? 1 : 0;
     info->h16_bytes = h->H16 ? h->m * h->n * 4 : 0;
     info->l2_keep_bytes = h->l2_keep_bytes;
+    info->factor_form = h->form;
+    info->reserved = 0;
+    if (h->form == ADMM_FORM_DIRECT) {
+        info->ctas = h->M * h->N * h->dir.fcn;
+        info->rows_per_stage = 0;
+        info->stages = 0;
+        info->slab_cols = 0;
+        info->smem_bytes = h->dir.njmax * static_cast<int32_t>(sizeof(float2));
+    }
     return ADMM_OK;
 }
 
 int admm_set_option(admm_t* h, int32_t option, int64_t value) {
     if (!h) return ADMM_EINVAL;
+    if (h->form == ADMM_FORM_DIRECT && value != 0 &&
+        (option == ADMM_OPT_H_FP16 || option == ADMM_OPT_RECORD_ITERS || option == ADMM_OPT_TRACE_ITERS ||
+         option == ADMM_OPT_BARRIER_EXTRA))
+        return fail(h, ADMM_EUNSUPPORTED, "option %d needs the lemma form (the persistent kernel)", option);
     switch (option) {
         case ADMM_OPT_TIMEOUT_NS:
             if (value < 1000) return fail(h, ADMM_EINVAL, "timeout must be >= 1000 ns");
@@ -1246,6 +1558,7 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
 int admm_tune(admm_t* h, void* stream) {
     if (!h) return ADMM_EINVAL;
     if (h->broken) return fail(h, ADMM_ECUDA, "handle is in an error state; call admm_reset");
+    if (h->form == ADMM_FORM_DIRECT) return ADMM_OK;   // nothing to tune: no L2 policy in the direct form
     cudaStream_t st = as_stream(stream);
     const int64_t mib = 1LL << 20;
     const int64_t cand[] = {0, 16 * mib, 32 * mib, 44 * mib, 52 * mib, 64 * mib, 80 * mib, 96 * mib};
@@ -1305,6 +1618,7 @@ int admm_backward(admm_t* h, const void* grad_v, void* grad_g, double* grad_lamb
                   void* stream) {
     if (!h || !grad_v || !grad_g || !grad_lambda || !grad_rho)
         return h ? fail(h, ADMM_EINVAL, "NULL argument") : ADMM_EINVAL;
+    if (h->form == ADMM_FORM_DIRECT) return fail(h, ADMM_EUNSUPPORTED, "the reverse sweep needs the lemma form");
     cudaStream_t st = as_stream(stream);
     int code = device_status(h, st);
     if (code) return code;
@@ -1493,8 +1807,11 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
     (void)stream;
     if (!out || !handles || count < 1) return gfail(nullptr, ADMM_EINVAL, "need out, handles and count >= 1");
     *out = nullptr;
-    for (int q = 0; q < count; ++q)
+    for (int q = 0; q < count; ++q) {
         if (!handles[q]) return gfail(nullptr, ADMM_EINVAL, "handle %d is NULL", q);
+        if (handles[q]->form == ADMM_FORM_DIRECT)
+            return gfail(nullptr, ADMM_EUNSUPPORTED, "handle %d has the direct form (no persistent kernel)", q);
+    }
     const int sms = handles[0]->num_sms, limit = handles[0]->smem_optin;
     admm_group_t* g = new admm_group_t();
     auto bail = [&](int c) {

@@ -224,6 +224,75 @@ struct FactorArgs {
 cudaError_t launch_gram(const FactorArgs& f, cudaStream_t s);
 cudaError_t launch_cholesky_inverse(const FactorArgs& f, cudaStream_t s);
 
+// ---- direct branch (admm_direct.cu) -------------------------------------------
+// Blocks with m_b >= n_b solved with the n_b x n_b factor of Section III-B,
+// L_b = (H_b^H H_b + rho I)^{-1}:
+//     q_b = H_b^H gt_b + rho z_b      (column pass over H_b; for one column
+//                                      block gt_b = g_i and H_b^H g_i is cached)
+//     u_b = L_b q_b                   (factor pass)
+//     v, s update                     (the last CTA of every column chunk)
+//     ghat_b = H_b u_b                (row pass; only with col_blocks > 1)
+// Every cross-CTA step is a last-arriver reduction on an atomic counter: no
+// CTA waits for another, and a launch sequence is stable under graph capture
+// (the estimated-data slot is taken from the device iteration count).
+
+constexpr int kDirThreads = 256;
+constexpr int kDirColTile = 256;     // columns per column-pass CTA (one per thread)
+constexpr int kDirChunk = 32;        // factor rows (= entries of u_b) per factor CTA
+constexpr int kDirRowTile = 64;      // rows of H_b per row-pass CTA
+constexpr int kDirMaxCols = 12288;   // widest block of the direct branch (q_b, u_b staged in shared memory)
+
+struct DirectArgs {
+    int m, n, ld, M, N, P;
+    int npitch;               // complex entries per block vector (Q, C, partial rows); multiple of 4
+    int njmax, mimax;
+    const int* row_off;
+    const int* col_off;
+    const float2* H;          // m x ld
+    const float2* g;          // m
+    float2* v;                // ld
+    float2* s;                // M x ld
+    float2* u;                // M x ld: u_j^i at u + i * ld + col_off[j]
+    float2* ghat;             // 2 x N x m, slot (iteration count) & 1
+    const float2* L;          // factors, block p = i * N + j at L + L_off[p], row pitch L_pitch[p]
+    const long long* L_off;
+    const int* L_pitch;
+    float2* C;                // P x npitch: H_i^H g_i (one column block)
+    float2* Q;                // P x npitch: q_b
+    float2* part;             // S x P x npitch: column-pass partial sums
+    int S;                    // row splits of the column pass
+    int ccn;                  // column tiles per block in the column pass
+    int fcn;                  // factor chunks per block (ceil(njmax / kDirChunk))
+    int rtn;                  // row tiles per block in the row pass
+    unsigned* cnt_cols;       // P x ccn
+    unsigned* cnt_upd;        // nchunks
+    unsigned* cnt_glob;       // [0] update chunks finished, [1] row-pass CTAs finished
+    const int* chunk_off;     // N + 1: first update chunk of each column block
+    int nchunks;
+    double* res_chunk;        // nchunks x 5
+    double* hist;
+    int hist_cap;
+    long long* k_done;
+    int* status;
+    int* stop_flag;           // set once the stopping test passed (with check_stop)
+    int* stop_pending;        // set by the update, turned into stop_flag after the row pass
+    int check_stop;
+    double eps_abs, eps_rel;
+    float rho, kappa, inv_M;
+    double rho_d;
+};
+
+// column pass: mode 0 writes Q = H^H gt + rho z, mode 1 writes C = H^H g (no z)
+cudaError_t launch_dir_cols(const DirectArgs& a, int mode, cudaStream_t s);
+// Q = C + rho z (one column block)
+cudaError_t launch_dir_q(const DirectArgs& a, cudaStream_t s);
+cudaError_t launch_dir_factor(const DirectArgs& a, cudaStream_t s);
+cudaError_t launch_dir_rows(const DirectArgs& a, cudaStream_t s);
+cudaError_t prepare_direct(int smem_optin);
+// HT (n x ldT) = H^H of the m x ld matrix H
+cudaError_t launch_conj_transpose(const float2* H, int64_t m, int64_t n, int64_t ld, float2* HT, int64_t ldT,
+                                  cudaStream_t s);
+
 // ---- small kernels (admm_misc.cu) ---------------------------------------------
 
 cudaError_t launch_pack_c128(const double2* src, int64_t m, int64_t n, float2* dst, int64_t ld,

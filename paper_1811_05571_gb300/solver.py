@@ -29,10 +29,14 @@ def _contig(x):
 
 
 class Solver:
-    """Norm-1 ADMM for g = Hu + w split into row_blocks x col_blocks (Sections III-A..C)."""
+    """Norm-1 ADMM for g = Hu + w split into row_blocks x col_blocks (Sections III-A..C).
+
+    form: "lemma" (m_b x m_b factors, every block shape), "direct" (n_b x n_b
+    factors of H_b^H H_b + rho I, Section III-B) or "auto" (direct when every
+    block has at least as many rows as columns)."""
 
     def __init__(self, H, g, row_blocks: int = 1, col_blocks: int = 1, lam: float = 0.0,
-                 rho: float = 1.0, stream=None):
+                 rho: float = 1.0, stream=None, form: str = "lemma"):
         import torch
         self._torch = torch
         H = _contig(H)
@@ -46,7 +50,10 @@ class Solver:
         self.m, self.n, self.M, self.N = m, n, int(row_blocks), int(col_blocks)
         self.stream = stream
         self._keep = (H, g)   # keep the sources alive until the synchronous setup returns
-        self.h = B.admm_setup(H, g, m, n, self.M, self.N, float(lam), float(rho), dt, stream)
+        codes = {"lemma": B.ADMM_FORM_LEMMA, "direct": B.ADMM_FORM_DIRECT, "auto": B.ADMM_FORM_AUTO}
+        if form not in codes:
+            raise ValueError("form must be 'lemma', 'direct' or 'auto'")
+        self.h = B.admm_setup_form(H, g, m, n, self.M, self.N, float(lam), float(rho), dt, codes[form], stream)
         self._keep = None
 
     # -- iteration ---------------------------------------------------------

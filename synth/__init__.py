@@ -20,6 +20,7 @@ from .workloads import (  # noqa: F401
     CONFIG1,
     CONFIG2,
     CONFIG3,
+    TALL,
     gaussian_problem_device,
     shared_h_scenes,
     uneven_problem_sizes,

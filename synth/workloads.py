@@ -264,6 +264,11 @@ CONFIG2 = dict(kind="cra", m=1440, n=32768, splits=((8, 1), (1, 8), (4, 4)),
 CONFIG3 = dict(kind="gaussian_device", m=8192, n=131072, nnz=400, seed=3, row_blocks=16,
                col_blocks=1, lam_frac=0.05, rho=1.0, fp16_iters=280, polish_iters=20)
 
+# an overdetermined Gaussian problem whose blocks all have m_b >= n_b in the
+# three splits (the direct factor form): 32768 x 2048 complex64 (537 MB, above L2)
+TALL = dict(kind="gaussian_device", m=32768, n=2048, nnz=64, seed=7, lam_frac=0.05, rho=1.0,
+            splits=((8, 1), (1, 8), (4, 4)))
+
 
 def gaussian_problem_device(m: int, n: int, nnz: int, seed: int, snr_db: float = 30.0,
                             lam_frac: float = 0.05, device="cuda"):

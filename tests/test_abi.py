@@ -33,7 +33,7 @@ def test_library_loads_and_exports_every_declared_symbol(cuda_lib):
 
 def test_abi_version_and_strerror(cuda_lib):
     import paper_1811_05571_gb300 as P
-    assert P.admm_abi_version() == P.ABI_VERSION == 3
+    assert P.admm_abi_version() == P.ABI_VERSION == 4
     for code in range(0, 9):
         assert P.admm_strerror(code)
     assert P.admm_strerror(99) == "unknown status"
@@ -123,6 +123,29 @@ def test_setup_argument_checks_need_no_gpu(cuda_lib, kw, code):
     with pytest.raises(P.AdmmError) as e:
         P.admm_setup(H, g, args["m"], args["n"], args["M"], args["N"], args["lam"], args["rho"],
                      args["dtype"])
+    assert e.value.status == code
+
+
+def test_form_constants_match_the_header(cuda_lib):
+    import paper_1811_05571_gb300 as P
+    found = dict(re.findall(r"#define (ADMM_FORM_[A-Z]+)\s+(\d+)", open(HEADER).read()))
+    assert {k: int(v) for k, v in found.items()} == {
+        "ADMM_FORM_LEMMA": P.ADMM_FORM_LEMMA, "ADMM_FORM_DIRECT": P.ADMM_FORM_DIRECT,
+        "ADMM_FORM_AUTO": P.ADMM_FORM_AUTO}
+
+
+@pytest.mark.parametrize("form,n,N,code", [
+    (3, 64, 1, 1), (-1, 64, 1, 1),
+    (1, 12289, 1, 7), (1, 2 * 12288 + 1, 2, 7),   # a column block wider than 12288 columns
+])
+def test_setup_form_checks_need_no_gpu(cuda_lib, form, n, N, code):
+    """An unknown factor form, and a direct form whose column blocks are too
+    wide for it, are rejected on the host before any CUDA call."""
+    import paper_1811_05571_gb300 as P
+    H = np.zeros((8, 1), np.complex64)   # never read: the checks come first
+    g = np.zeros(8, np.complex64)
+    with pytest.raises(P.AdmmError) as e:
+        P.admm_setup_form(H, g, 8, n, 1, N, 0.1, 1.0, P.ADMM_C64, form)
     assert e.value.status == code
 
 

@@ -1,0 +1,173 @@
+"""GPU parity of the direct factor form (ADMM_FORM_DIRECT: the n_b x n_b
+factor (H_b^H H_b + rho I)^{-1} of Section III-B) against the FP64 oracle,
+whose blocks with m_b >= n_b take the same direct branch.  Same bar as the
+lemma form: relative iterate error <= 1e-5, support identical outside the
+FP32 band of the threshold."""
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+from oracle import admm_fp64 as A
+from test_gpu_parity import _rho_cols, compare_all, oracle_run
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1811_05571_gb300 as P
+    P.load()
+
+
+def direct_run(p, M, N, iters, rho=None, form="direct", lam=None):
+    import paper_1811_05571_gb300 as P
+    H = torch.from_numpy(p.H_c64()).cuda()
+    g = torch.from_numpy(p.g_c64()).cuda()
+    s = P.Solver(H, g, M, N, p.lam if lam is None else lam, p.rho if rho is None else rho, form=form)
+    s.iterate(iters)
+    assert s.status() == 0
+    return s
+
+
+@pytest.mark.parametrize("m,n,M,N,iters", [
+    (1200, 512, 2, 1, 120),     # overdetermined consensus, 600 x 512 blocks: H is never read
+    (700, 203, 1, 4, 120),      # sectioning, ragged column blocks of 51 / 50
+    (703, 130, 3, 2, 100),      # C&S, ragged rows, 234 x 65 blocks
+    (300, 300, 1, 1, 100),      # square lasso (m_b = n_b)
+    (2000, 70, 1, 1, 100),      # tall lasso, a single partial factor chunk
+    (4100, 1030, 5, 3, 60),     # several column tiles, factor chunks and row tiles, ragged tails
+])
+def test_direct_form_matches_the_oracle(m, n, M, N, iters):
+    rows = A.balanced_blocks(m, M)
+    cols = A.balanced_blocks(n, N)
+    assert all(not A.lemma_applies(r1 - r0, c1 - c0) for r0, r1 in rows for c0, c1 in cols)
+    p = synth.gaussian_problem(m, n, max(2, n // 32), seed=m + n + M + N + 1)
+    rho = _rho_cols(p, N)
+    ref = oracle_run(p, M, N, iters, rho=rho)
+    s = direct_run(p, M, N, iters, rho=rho)
+    assert s.info()["factor_form"] == 1
+    compare_all(s, ref, M, N)
+
+
+def test_direct_form_on_wide_blocks_is_the_same_algorithm():
+    """The direct form is valid for any block shape (it is only costlier when
+    m_b < n_b): on wide blocks it matches the oracle's lemma branch."""
+    p = synth.gaussian_problem(96, 400, 6, seed=31)
+    rho = _rho_cols(p, 2)
+    ref = oracle_run(p, 2, 2, 80, rho=rho)
+    s = direct_run(p, 2, 2, 80, rho=rho)
+    compare_all(s, ref, 2, 2)
+
+
+def test_auto_form_follows_the_block_shape():
+    import paper_1811_05571_gb300 as P
+    tall = synth.gaussian_problem(512, 128, 4, seed=32)
+    wide = synth.gaussian_problem(64, 512, 4, seed=33)
+    for p, M, N, want in [(tall, 2, 1, 1), (tall, 1, 2, 1), (wide, 1, 1, 0), (wide, 2, 1, 0)]:
+        s = P.Solver(torch.from_numpy(p.H_c64()).cuda(), torch.from_numpy(p.g_c64()).cuda(), M, N,
+                     p.lam, 1.0, form="auto")
+        assert s.info()["factor_form"] == want, (p.m, p.n, M, N)
+
+
+def test_lemma_and_direct_forms_agree_on_a_large_tall_problem():
+    """8192 x 1024 in 4 x 2 blocks (2048 x 512): the two forms of the same
+    iteration against each other after 80 iterations, and the direct form
+    against the oracle."""
+    p = synth.gaussian_problem(8192, 1024, 32, seed=34)
+    rho = _rho_cols(p, 2)
+    ref = oracle_run(p, 4, 2, 80, rho=rho)
+    d = direct_run(p, 4, 2, 80, rho=rho)
+    compare_all(d, ref, 4, 2)
+    lem = direct_run(p, 4, 2, 80, rho=rho, form="lemma")
+    vd, vl = d.v().cpu().numpy(), lem.v().cpu().numpy()
+    assert np.linalg.norm(vd - vl) <= 2e-5 * np.linalg.norm(vl)
+
+
+def test_new_data_vector_recomputes_the_cached_product():
+    """With one column block the direct form caches H_i^H g_i; admm_set_g
+    must replace it (and reset restarts from zero)."""
+    p = synth.gaussian_problem(900, 200, 6, seed=35)
+    q = synth.gaussian_problem(900, 200, 6, seed=36)
+    s = direct_run(p, 3, 1, 20)
+    s.set_g(torch.from_numpy(q.g_c64()).cuda())
+    s.reset()
+    s.iterate(90)
+    assert s.status() == 0
+    ref = oracle.run_split(p.H, q.g, 3, 1, p.lam, p.rho, 90)
+    compare_all(s, ref, 3, 1)
+
+
+def test_set_rho_refactors_the_direct_factor():
+    p = synth.gaussian_problem(800, 160, 5, seed=37)
+    s = direct_run(p, 2, 2, 10, rho=1.0)
+    s.set_rho(3.0)
+    s.reset()
+    s.iterate(80)
+    ref = oracle_run(p, 2, 2, 80, rho=3.0)
+    compare_all(s, ref, 2, 2)
+
+
+@pytest.mark.parametrize("M,N", [(2, 1), (1, 3), (2, 2)])
+def test_checkpoint_restart_is_bit_exact(M, N):
+    """The direct form sums in a fixed order: a restart from a checkpoint
+    reproduces the uninterrupted iterates bit for bit."""
+    p = synth.gaussian_problem(600, 150, 5, seed=38 + M + N)
+    rho = _rho_cols(p, N)
+    s = direct_run(p, M, N, 17, rho=rho)
+    k, v, sd, gh = s.state()
+    s.iterate(23)
+    v_straight = s.v().cpu()
+    s.set_state(k, v, sd, gh if N > 1 else None)
+    s.iterate(23)
+    assert s.status() == 0
+    assert torch.equal(s.v().cpu(), v_straight)
+
+
+def test_solve_stops_where_the_oracle_stops():
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(1024, 256, 8, seed=41)
+    for M, N in [(4, 1), (2, 2)]:
+        rho = _rho_cols(p, N)
+        s = P.Solver(torch.from_numpy(p.H_c64()).cuda(), torch.from_numpy(p.g_c64()).cuda(), M, N,
+                     p.lam, rho, form="direct")
+        done = s.solve(3000, 1e-5, 1e-4)
+        ref = oracle.run_split(p.H, p.g, M, N, p.lam, rho, 3000, eps=(1e-5, 1e-4))
+        assert ref.stopped_at is not None
+        assert abs(done - ref.stopped_at) <= 2, (M, N, done, ref.stopped_at)
+        rec = s.residuals(1)[0]
+        assert A.stop_test(rec, M * p.n, rho, 1e-5, 1e-4)
+        # the state is that of the last iteration: continuing is a plain iterate
+        k0 = s.state()[0]
+        s.iterate(3)
+        assert s.state()[0] == k0 + 3
+
+
+def test_persistent_kernel_options_are_refused():
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(256, 64, 3, seed=42)
+    s = direct_run(p, 2, 1, 1)
+    for opt in (P.ADMM_OPT_H_FP16, P.ADMM_OPT_RECORD_ITERS, P.ADMM_OPT_TRACE_ITERS, P.ADMM_OPT_BARRIER_EXTRA):
+        with pytest.raises(P.AdmmError) as e:
+            s.set_option(opt, 1)
+        assert e.value.status == P.ADMM_EUNSUPPORTED
+    with pytest.raises(P.AdmmError) as e:
+        P.Group([s])
+    assert e.value.status == P.ADMM_EUNSUPPORTED
+    s.tune()                  # nothing to tune; the state is untouched
+    s.iterate(2)
+    assert s.status() == 0 and s.state()[0] == 3
+
+
+def test_lambda_zero_is_least_squares():
+    """lambda = 0 with one block: the fixed point is the least-squares
+    solution of the overdetermined system, reached by the direct form."""
+    p = synth.gaussian_problem(400, 100, 4, seed=43)
+    s = direct_run(p, 1, 1, 400, lam=0.0)
+    x_ls = np.linalg.lstsq(p.H, p.g, rcond=None)[0]
+    v = s.v().cpu().numpy().astype(np.complex128)
+    assert np.linalg.norm(v - x_ls) <= 1e-4 * np.linalg.norm(x_ls)
