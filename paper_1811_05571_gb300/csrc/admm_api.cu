@@ -28,16 +28,18 @@ int round_up(int64_t x, int64_t q) { return static_cast<int>((x + q - 1) / q * q
 struct DirectState {
     float2 *C = nullptr, *Q = nullptr, *part = nullptr;
     unsigned* cnt = nullptr;       // column tiles, update chunks, two global counters
-    int* ints = nullptr;           // chunk_off (N + 1), L_pitch (P)
+    int* ints = nullptr;           // chunk_off (N + 1), L_pitch (P), F_off (P + 1), R_off (P + 1)
     long long* L_off = nullptr;    // P
     double* res_chunk = nullptr;
     int* stop_pending = nullptr;
-    int npitch = 0, njmax = 0, S = 1, ccn = 1, fcn = 1, rtn = 1, nchunks = 0, ncnt = 0;
+    int npitch = 0, njmax = 0, S = 1, ccn = 1, ctas = 1, frows = 0, hrows = 0, nchunks = 0, ncnt = 0;
+    int fac_stream = 0, fac_ctas = 0, fac_ns = 0, fac_stage = 0;   // streamed factor pass
     int64_t bytes = 0;
     bool c_valid = false;          // C = H_i^H g_i matches g (one column block)
+    bool q_valid = false;          // Q of the current iteration matches C, v, s and rho
     cudaStream_t cap = nullptr;    // capture stream of the iteration graphs
     cudaGraphExec_t g1 = nullptr, g16 = nullptr;   // one and sixteen iterations
-    double key[6] = {0, 0, 0, 0, 0, 0};
+    double key[7] = {0, 0, 0, 0, 0, 0, 0};
     const void* key_hist = nullptr;
     bool key_set = false;
 };
@@ -624,6 +626,7 @@ int zero_state(admm_t* h, cudaStream_t st) {
     CK(h, cudaMemsetAsync(h->stop_flag, 0, sizeof(int), st));
     CK(h, cudaMemsetAsync(h->k_done, 0, sizeof(long long), st));
     CK(h, cudaMemsetAsync(h->hist, 0, static_cast<size_t>(h->hist_cap) * 5 * sizeof(double), st));
+    h->dir.q_valid = false;
     if (h->form == ADMM_FORM_DIRECT) {
         CK(h, cudaMemsetAsync(h->dir.cnt, 0, static_cast<size_t>(h->dir.ncnt) * sizeof(unsigned), st));
         CK(h, cudaMemsetAsync(h->dir.stop_pending, 0, sizeof(int), st));
@@ -643,26 +646,62 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
     const int mimax = h->plan.mimax;
     d.njmax = njmax;
     d.npitch = round_up(njmax, 4);
-    d.ccn = (njmax + admm::kDirColTile - 1) / admm::kDirColTile;
-    d.fcn = (njmax + admm::kDirChunk - 1) / admm::kDirChunk;
-    d.rtn = (mimax + admm::kDirRowTile - 1) / admm::kDirRowTile;
-    // row splits of the column pass: about four CTAs per SM, at least 64 rows
-    // per split where the blocks allow, at most 4096 (the staged gt_b)
-    int S = (4 * h->num_sms + P * d.ccn - 1) / (P * d.ccn);
-    S = std::min(S, std::max(1, mimax / 64));
-    S = std::max(S, (mimax + 4095) / 4096);
+    // column tiles: pairs from each block's first column rounded down to even
+    int pairs = 1;
+    for (int j = 0; j < h->N; ++j) {
+        const int c0 = h->col_off[j], c1 = h->col_off[j + 1];
+        pairs = std::max(pairs, (c1 - (c0 & ~1) + 1) / 2);
+    }
+    d.ccn = (pairs + admm::kDirColPairs - 1) / admm::kDirColPairs;
+    d.ctas = 2 * h->num_sms;   // factor and row passes: one wave of two CTAs per SM
+    // factor pass streamed through shared memory when the rows are short
+    // enough for a stage of four: a ring of up to eight stages, as many CTAs
+    // per SM (up to four) as the SM's shared memory holds
+    d.fac_stream = 0;
+    if (njmax <= admm::kDirBulkMaxCols) {
+        const int stage = round_up(static_cast<int64_t>(4) * round_up(njmax, 4) * 8, 128);
+        int ns = 8;
+        while (ns >= 2 && admm::stream_smem(ns, stage) > static_cast<size_t>(h->smem_optin)) --ns;
+        int per_sm = 0;
+        if (ns >= 2 && admm::prepare_direct(h->smem_optin) == cudaSuccess &&
+            admm::direct_stream_per_sm(static_cast<int>(admm::stream_smem(ns, stage)), &per_sm) == cudaSuccess &&
+            per_sm >= 1) {
+            d.fac_stream = 1;
+            d.fac_ns = ns;
+            d.fac_stage = stage;
+            d.fac_ctas = h->num_sms * std::min(4, per_sm);
+        }
+    }
+    // row splits of the column pass: at most one wave at two CTAs per SM, at
+    // least 32 rows per split where the blocks allow, at most kDirColRows (the
+    // staged gt_b)
+    int S = (2 * h->num_sms) / (P * d.ccn);
+    S = std::min(S, std::max(1, mimax / 32));
+    S = std::max(S, (mimax + admm::kDirColRows - 1) / admm::kDirColRows);
     d.S = std::max(S, 1);
     std::vector<int> ints(h->N + 1, 0);
     for (int j = 0; j < h->N; ++j)
         ints[j + 1] = ints[j] + (h->col_off[j + 1] - h->col_off[j] + admm::kDirChunk - 1) / admm::kDirChunk;
     d.nchunks = ints[h->N];
     ints.insert(ints.end(), pitch.begin(), pitch.end());
+    // factor rows and H rows of the blocks in order p = i * N + j, concatenated
+    std::vector<int> foff(P + 1, 0), roff(P + 1, 0);
+    for (int q = 0; q < P; ++q) {
+        const int i = q / h->N, j = q % h->N;
+        foff[q + 1] = foff[q] + (h->col_off[j + 1] - h->col_off[j]);
+        roff[q + 1] = roff[q] + (h->row_off[i + 1] - h->row_off[i]);
+    }
+    d.frows = foff[P];
+    d.hrows = roff[P];
+    ints.insert(ints.end(), foff.begin(), foff.end());
+    ints.insert(ints.end(), roff.begin(), roff.end());
     d.ncnt = P * d.ccn + d.nchunks + 2;
     const size_t vec = static_cast<size_t>(P) * d.npitch;
     // the column pass writes partials in both uses (q_b every iteration with
     // several column blocks, C = H_i^H g_i once per data vector with one)
     const size_t nc = h->N == 1 ? vec : 1, np = static_cast<size_t>(d.S) * vec;
-    const bool ok = dalloc(&d.C, nc) == cudaSuccess && dalloc(&d.Q, vec) == cudaSuccess &&
+    const size_t nq = h->N == 1 ? 2 * vec : vec;   // one column block: a slot per iteration parity
+    const bool ok = dalloc(&d.C, nc) == cudaSuccess && dalloc(&d.Q, nq) == cudaSuccess &&
                     dalloc(&d.part, np) == cudaSuccess && dalloc(&d.cnt, d.ncnt) == cudaSuccess &&
                     dalloc(&d.ints, ints.size()) == cudaSuccess && dalloc(&d.L_off, off.size()) == cudaSuccess &&
                     dalloc(&d.res_chunk, static_cast<size_t>(d.nchunks) * 5) == cudaSuccess &&
@@ -670,12 +709,12 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
     if (!ok) return ADMM_ENOMEM;
     // Q and C padding entries stay zero (the factor pass reads whole pairs)
     CK(h, cudaMemset(d.C, 0, nc * sizeof(float2)));
-    CK(h, cudaMemset(d.Q, 0, vec * sizeof(float2)));
+    CK(h, cudaMemset(d.Q, 0, nq * sizeof(float2)));
     CK(h, cudaMemset(d.cnt, 0, static_cast<size_t>(d.ncnt) * sizeof(unsigned)));
     CK(h, cudaMemset(d.stop_pending, 0, sizeof(int)));
     CK(h, cudaMemcpy(d.ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(d.L_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
-    d.bytes = static_cast<int64_t>((nc + vec + np) * sizeof(float2) + d.nchunks * 5 * sizeof(double));
+    d.bytes = static_cast<int64_t>((nc + nq + np) * sizeof(float2) + d.nchunks * 5 * sizeof(double));
     return ADMM_OK;
 }
 
@@ -708,8 +747,16 @@ admm::DirectArgs direct_args(admm_t* h, int check_stop, double eps_abs, double e
     a.part = d.part;
     a.S = d.S;
     a.ccn = d.ccn;
-    a.fcn = d.fcn;
-    a.rtn = d.rtn;
+    a.ctas = d.ctas;
+    a.fac_stream = d.fac_stream;
+    a.fac_ctas = d.fac_ctas;
+    a.fac_ns = d.fac_ns;
+    a.fac_stage = d.fac_stage;
+    a.timeout_ns = h->timeout_ns;
+    a.frows = d.frows;
+    a.hrows = d.hrows;
+    a.F_off = d.ints + (h->N + 1) + a.P;
+    a.R_off = d.ints + (h->N + 1) + a.P + (a.P + 1);
     a.cnt_cols = d.cnt;
     a.cnt_upd = d.cnt + a.P * d.ccn;
     a.cnt_glob = d.cnt + a.P * d.ccn + d.nchunks;
@@ -738,19 +785,28 @@ void drop_direct_graphs(DirectState& d) {
     d.g1 = d.g16 = nullptr;
 }
 
-// `iters` iterations of the direct form: per iteration the column pass (or,
-// with one column block, q = C + rho z), the factor pass with the update, and
-// with several column blocks the row pass.  Launched as captured graphs of
+// `iters` iterations of the direct form: per iteration the column pass, the
+// factor pass with the update and the row pass; with one column block the
+// factor pass alone (its update writes the next iteration's q).  Launched as captured graphs of
 // one and sixteen iterations, re-captured when a scalar argument changes.
 int run_direct(admm_t* h, int iters, int check_stop, double eps_abs, double eps_rel, cudaStream_t st) {
     DirectState& d = h->dir;
     const admm::DirectArgs a = direct_args(h, check_stop, eps_abs, eps_rel);
-    if (h->N == 1 && !d.c_valid) {
-        CK(h, admm::launch_dir_cols(a, 1, st));
-        d.c_valid = true;
+    if (h->N == 1) {
+        // one column block: C once per data vector, q of the current
+        // iteration once per state change (each update writes the next q)
+        if (!d.c_valid) {
+            CK(h, admm::launch_dir_cols(a, 1, st));
+            d.c_valid = true;
+            d.q_valid = false;
+        }
+        if (!d.q_valid) {
+            CK(h, admm::launch_dir_q(a, st));
+            d.q_valid = true;
+        }
     }
-    const double key[6] = {h->rho, h->lambda, static_cast<double>(check_stop), eps_abs, eps_rel,
-                           static_cast<double>(h->hist_cap)};
+    const double key[7] = {h->rho, h->lambda, static_cast<double>(check_stop), eps_abs, eps_rel,
+                           static_cast<double>(h->hist_cap), static_cast<double>(h->timeout_ns)};
     if (!d.key_set || std::memcmp(key, d.key, sizeof key) != 0 || d.key_hist != h->hist) {
         drop_direct_graphs(d);
         std::memcpy(d.key, key, sizeof key);
@@ -762,8 +818,7 @@ int run_direct(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
         if (e != cudaSuccess) return e;
         for (int q = 0; q < count && e == cudaSuccess; ++q) {
             if (h->N == 1) {
-                e = admm::launch_dir_q(a, d.cap);
-                if (e == cudaSuccess) e = admm::launch_dir_factor(a, d.cap);
+                e = admm::launch_dir_factor(a, d.cap);
             } else {
                 e = admm::launch_dir_cols(a, 0, d.cap);
                 if (e == cudaSuccess) e = admm::launch_dir_factor(a, d.cap);
@@ -1374,6 +1429,7 @@ int admm_set_g(admm_t* h, const void* g, int32_t h_dtype, void* stream) {
     if (h_dtype != ADMM_C64 && h_dtype != ADMM_C128) return fail(h, ADMM_EINVAL, "bad dtype");
     if (h->k > 0) h->rec_valid = false;
     h->dir.c_valid = false;
+    h->dir.q_valid = false;
     return copy_vector_in(h, h->g, g, h->m, h_dtype, as_stream(stream));
 }
 
@@ -1400,6 +1456,7 @@ int admm_set_rho(admm_t* h, double rho, void* stream) {
         return code;
     }
     h->rec_valid = false;
+    h->dir.q_valid = false;
     CK(h, admm::launch_scale(h->s, static_cast<int64_t>(h->plan.ld) * h->M, static_cast<float>(old / rho), st));
     CK(h, cudaStreamSynchronize(st));
     return ADMM_OK;
@@ -1450,6 +1507,7 @@ int admm_set_state(admm_t* h, int64_t k, const void* v, const void* s, const voi
     h->k = k;
     h->pending = 0;   // the restored state has no residual record of its own
     h->rec_valid = false;
+    h->dir.q_valid = false;
     return ADMM_OK;
 }
 
@@ -1483,7 +1541,7 @@ int admm_get_info(const admm_t* h, admm_info_t* info) {
     info->factor_form = h->form;
     info->reserved = 0;
     if (h->form == ADMM_FORM_DIRECT) {
-        info->ctas = h->M * h->N * h->dir.fcn;
+        info->ctas = h->dir.ctas;
         info->rows_per_stage = 0;
         info->stages = 0;
         info->slab_cols = 0;

@@ -21,8 +21,6 @@
 namespace admm {
 namespace {
 
-__device__ __forceinline__ float2 ldcg2(const float2* p) { return __ldcg(p); }
-__device__ __forceinline__ void stcg2(float2* p, float2 v) { __stcg(p, v); }
 __device__ __forceinline__ float sq2(float2 a) { return a.x * a.x + a.y * a.y; }
 
 // complex soft-threshold of Eq. (softhresholding)
@@ -35,14 +33,51 @@ __device__ __forceinline__ float2 shrink(float2 a, float kappa) {
     return make_float2(0.0f, 0.0f);
 }
 
+// Sum over the 32 lanes of x[0..7], leaving the sum of x[q] in lanes whose
+// bits 4..2 spell q (lane >> 2 == q): three exchange steps halve the values a
+// lane carries, two plain steps finish; 18 shuffles for eight complex values.
+__device__ __forceinline__ float2 lanes_sum8(const float2 (&x)[8], int lane) {
+    float2 y4[4];
+    const bool b16 = lane & 16;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 keep = b16 ? x[q + 4] : x[q], send = b16 ? x[q] : x[q + 4];
+        y4[q] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, send.x, 16),
+                            keep.y + __shfl_xor_sync(0xffffffffu, send.y, 16));
+    }
+    float2 y2[2];
+    const bool b8 = lane & 8;
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const float2 keep = b8 ? y4[q + 2] : y4[q], send = b8 ? y4[q] : y4[q + 2];
+        y2[q] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, send.x, 8),
+                            keep.y + __shfl_xor_sync(0xffffffffu, send.y, 8));
+    }
+    const bool b4 = lane & 4;
+    const float2 keep = b4 ? y2[1] : y2[0], send = b4 ? y2[0] : y2[1];
+    float2 y = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, send.x, 4),
+                           keep.y + __shfl_xor_sync(0xffffffffu, send.y, 4));
+    y.x += __shfl_xor_sync(0xffffffffu, y.x, 2);
+    y.y += __shfl_xor_sync(0xffffffffu, y.y, 2);
+    y.x += __shfl_xor_sync(0xffffffffu, y.x, 1);
+    y.y += __shfl_xor_sync(0xffffffffu, y.y, 1);
+    // lane bits: 16 -> q bit 2, 8 -> q bit 1, 4 -> q bit 0
+    return y;
+}
+
 __device__ __forceinline__ bool stopped(const DirectArgs& a) {
     return a.check_stop && ld_volatile(a.stop_flag) != 0;
 }
 
 // ---- column pass: partial[s][b][c] = sum over the rows of split s of
-// conj(H_b[r][c]) gt_b[r]; the last of the S splits of a column tile adds them
-__global__ void __launch_bounds__(kDirThreads) dir_cols_kernel(const DirectArgs a, int mode) {
-    extern __shared__ float2 gts[];
+// conj(H_b[r][c]) gt_b[r]; the last of the S splits of a column tile adds them.
+// A tile is kDirColPairs column pairs from the block's first column rounded
+// down to even (16-byte loads; columns outside the block are dropped).  Lane
+// l of every warp owns pairs l, l + 32, l + 64, l + 96 of the tile; warp w
+// takes rows w, w + 8, ... of the split, four at a time (16 loads in flight
+// per lane), and the eight warps' sums meet in shared memory.
+__global__ void __launch_bounds__(kDirColThreads, 2) dir_cols_kernel(const DirectArgs a, int mode) {
+    extern __shared__ float2 dsm[];
     __shared__ int last;
     if (mode == 0 && stopped(a)) return;
     const int sidx = blockIdx.x % a.S;
@@ -53,10 +88,13 @@ __global__ void __launch_bounds__(kDirThreads) dir_cols_kernel(const DirectArgs 
     const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
     const int rb = static_cast<int>(static_cast<long long>(mi) * sidx / a.S);
     const int nr = static_cast<int>(static_cast<long long>(mi) * (sidx + 1) / a.S) - rb;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    float2* gts = dsm;                                  // rows of the split
+    float2* red = dsm + ((a.mimax + a.S - 1) / a.S + 1); // 8 warps x 2 kDirColPairs
     const size_t Nm = static_cast<size_t>(a.N) * a.m;
     const float2* gh = a.ghat + static_cast<size_t>(__ldcg(a.k_done) & 1) * Nm;
     // gt_b = g_i - sum_{q != j} ghat_iq over the split's rows
-    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+    for (int r = tid; r < nr; r += blockDim.x) {
         const int row = r0 + rb + r;
         float2 x = a.g[row];
         if (mode == 0)
@@ -69,36 +107,82 @@ __global__ void __launch_bounds__(kDirThreads) dir_cols_kernel(const DirectArgs 
         gts[r] = x;
     }
     __syncthreads();
-    const int c = cc * kDirColTile + threadIdx.x;
-    float2 acc = make_float2(0.f, 0.f);
-    if (c < nj) {
-        const float2* hp = a.H + static_cast<size_t>(r0 + rb) * a.ld + c0 + c;
-        int r = 0;
-        for (; r + 8 <= nr; r += 8) {
-            float2 h[8];
+    const int cb = (c0 & ~1) + cc * 2 * kDirColPairs;  // first column of the tile (even)
+    const int cend = c0 + nj;
+    float2 acc[4][2];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) h[q] = __ldg(hp + static_cast<size_t>(r + q) * a.ld);
+    for (int t = 0; t < 4; ++t) acc[t][0] = acc[t][1] = make_float2(0.f, 0.f);
+    // pairs that hold a column of the block; the others load nothing
+    bool live[4];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) cfma_conj(acc, h[q], gts[r + q]);
+    for (int t = 0; t < 4; ++t) live[t] = cb + 2 * (lane + 32 * t) < cend;
+    const size_t step = static_cast<size_t>(a.ld) / 2;   // float4 per row
+    const float4* hp = reinterpret_cast<const float4*>(a.H + static_cast<size_t>(r0 + rb) * a.ld + cb) + lane;
+    int r = warp;
+    for (; r + 24 < nr; r += 32) {
+        float4 h[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int t = 0; t < 4; ++t)
+                h[q][t] = live[t] ? __ldg(hp + (r + 8 * q) * step + 32 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float2 x = gts[r + 8 * q];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                cfma_conj(acc[t][0], make_float2(h[q][t].x, h[q][t].y), x);
+                cfma_conj(acc[t][1], make_float2(h[q][t].z, h[q][t].w), x);
+            }
         }
-        for (; r < nr; ++r) cfma_conj(acc, __ldg(hp + static_cast<size_t>(r) * a.ld), gts[r]);
-        stcg2(a.part + (static_cast<size_t>(sidx) * a.P + p) * a.npitch + c, acc);
+    }
+    for (; r < nr; r += 8) {
+        const float2 x = gts[r];
+#pragma unroll
+        for (int t = 0; t < 4; ++t) {
+            const float4 h = live[t] ? __ldg(hp + r * step + 32 * t) : make_float4(0.f, 0.f, 0.f, 0.f);
+            cfma_conj(acc[t][0], make_float2(h.x, h.y), x);
+            cfma_conj(acc[t][1], make_float2(h.z, h.w), x);
+        }
+    }
+    // cross-warp sum: column c = 2 * pair + half of the tile
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+        const int pr = lane + 32 * t;
+        red[warp * 2 * kDirColPairs + 2 * pr] = acc[t][0];
+        red[warp * 2 * kDirColPairs + 2 * pr + 1] = acc[t][1];
+    }
+    __syncthreads();
+    float2* pp = a.part + (static_cast<size_t>(sidx) * a.P + p) * a.npitch;
+    for (int c = tid; c < 2 * kDirColPairs; c += blockDim.x) {
+        const int e = cb + c - c0;
+        if (e < 0 || e >= nj) continue;
+        float2 sum = red[c];
+#pragma unroll
+        for (int w = 1; w < kDirColThreads / 32; ++w) {
+            const float2 x = red[w * 2 * kDirColPairs + c];
+            sum.x += x.x;
+            sum.y += x.y;
+        }
+        stcg2(pp + e, sum);
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(a.cnt_cols + tile, 1u) == static_cast<unsigned>(a.S - 1);
+    if (tid == 0) last = atomicAdd(a.cnt_cols + tile, 1u) == static_cast<unsigned>(a.S - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    if (c < nj) {
+    const size_t sstep = static_cast<size_t>(a.P) * a.npitch;
+    for (int c = tid; c < 2 * kDirColPairs; c += blockDim.x) {
+        const int e = cb + c - c0;
+        if (e < 0 || e >= nj) continue;
         float2 sum = make_float2(0.f, 0.f);
-        const float2* pp = a.part + static_cast<size_t>(p) * a.npitch + c;
-        const size_t step = static_cast<size_t>(a.P) * a.npitch;
+        const float2* ps = a.part + static_cast<size_t>(p) * a.npitch + e;
         int q = 0;
         for (; q + 4 <= a.S; q += 4) {
             float2 x[4];
 #pragma unroll
-            for (int t = 0; t < 4; ++t) x[t] = ldcg2(pp + (q + t) * step);
+            for (int t = 0; t < 4; ++t) x[t] = ldcg2(ps + (q + t) * sstep);
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 sum.x += x[t].x;
@@ -106,151 +190,111 @@ __global__ void __launch_bounds__(kDirThreads) dir_cols_kernel(const DirectArgs 
             }
         }
         for (; q < a.S; ++q) {
-            const float2 x = ldcg2(pp + q * step);
+            const float2 x = ldcg2(ps + q * sstep);
             sum.x += x.x;
             sum.y += x.y;
         }
         if (mode == 0) {
-            const float2 vv = ldcg2(a.v + c0 + c), ss = ldcg2(a.s + static_cast<size_t>(i) * a.ld + c0 + c);
+            const float2 vv = ldcg2(a.v + c0 + e), ss = ldcg2(a.s + static_cast<size_t>(i) * a.ld + c0 + e);
             sum.x += a.rho * (vv.x - ss.x);
             sum.y += a.rho * (vv.y - ss.y);
-            stcg2(a.Q + static_cast<size_t>(p) * a.npitch + c, sum);
+            stcg2(a.Q + static_cast<size_t>(p) * a.npitch + e, sum);
         } else {
-            stcg2(a.C + static_cast<size_t>(p) * a.npitch + c, sum);
+            stcg2(a.C + static_cast<size_t>(p) * a.npitch + e, sum);
         }
     }
-    if (threadIdx.x == 0) a.cnt_cols[tile] = 0u;
+    if (tid == 0) a.cnt_cols[tile] = 0u;
 }
 
-// ---- one column block: q_i = C_i + rho (v - s_i) ---------------------------
-__global__ void __launch_bounds__(kDirThreads) dir_q_kernel(const DirectArgs a) {
+// ---- one column block: q_i = C_i + rho (v - s_i) into the slot of the current
+// iteration (later iterations get theirs from the update) ---------------------
+__global__ void __launch_bounds__(kDirFacThreads) dir_q_kernel(const DirectArgs a) {
     if (stopped(a)) return;
     const long long total = static_cast<long long>(a.M) * a.n;
+    float2* Q = a.Q + static_cast<size_t>(__ldcg(a.k_done) & 1) * a.P * a.npitch;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
         const int i = static_cast<int>(e / a.n), c = static_cast<int>(e - static_cast<long long>(i) * a.n);
         const float2 cv = a.C[static_cast<size_t>(i) * a.npitch + c];
         const float2 vv = ldcg2(a.v + c), ss = ldcg2(a.s + static_cast<size_t>(i) * a.ld + c);
-        stcg2(a.Q + static_cast<size_t>(i) * a.npitch + c,
+        stcg2(Q + static_cast<size_t>(i) * a.npitch + c,
               make_float2(cv.x + a.rho * (vv.x - ss.x), cv.y + a.rho * (vv.y - ss.y)));
     }
 }
 
-// ---- factor pass + update ----------------------------------------------------
-// CTA (b, chunk): u_b[row0 .. row0 + 32) = L_b[rows] q_b, four rows per warp.
-// The last of the M CTAs holding chunk `chunk` of column block j updates v_j,
-// s_j^i over those 32 columns and writes the chunk's residual partials; the
-// last chunk of all writes the iteration's residual record.
-__global__ void __launch_bounds__(kDirThreads) dir_factor_kernel(const DirectArgs a) {
-    extern __shared__ float4 qs4[];
-    __shared__ int last;
-    if (stopped(a)) return;
-    const int chunk_in = blockIdx.x % a.fcn, p = blockIdx.x / a.fcn;
-    const int i = p / a.N, j = p - i * a.N;
-    const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
-    const int row0 = chunk_in * kDirChunk;
-    if (row0 >= nj) return;   // whole CTA: this chunk does not exist for the block
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int npairs = (nj + 1) >> 1;
-    const float4* q4 = reinterpret_cast<const float4*>(a.Q + static_cast<size_t>(p) * a.npitch);
-    for (int e = tid; e < npairs; e += blockDim.x) qs4[e] = __ldcg(q4 + e);
-    __syncthreads();
-    {
-        const float2* Lp = a.L + a.L_off[p];
-        const int pitch = a.L_pitch[p];
-        const int rbase = row0 + warp * 4;
-        const float4* lr[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const int rq = min(rbase + q, nj - 1);   // clamped rows are computed and dropped
-            lr[q] = reinterpret_cast<const float4*>(Lp + static_cast<size_t>(rq) * pitch);
-        }
-        float2 acc[4];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
-        int e = lane;
-        for (; e + 32 < npairs; e += 64) {
-            const float4 x0 = qs4[e], x1 = qs4[e + 32];
-            float4 l0[4], l1[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                l0[q] = __ldg(lr[q] + e);
-                l1[q] = __ldg(lr[q] + e + 32);
-            }
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                cfma(acc[q], make_float2(l0[q].x, l0[q].y), make_float2(x0.x, x0.y));
-                cfma(acc[q], make_float2(l0[q].z, l0[q].w), make_float2(x0.z, x0.w));
-                cfma(acc[q], make_float2(l1[q].x, l1[q].y), make_float2(x1.x, x1.y));
-                cfma(acc[q], make_float2(l1[q].z, l1[q].w), make_float2(x1.z, x1.w));
-            }
-        }
-        for (; e < npairs; e += 32) {
-            const float4 x0 = qs4[e];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float4 l = __ldg(lr[q] + e);
-                cfma(acc[q], make_float2(l.x, l.y), make_float2(x0.x, x0.y));
-                cfma(acc[q], make_float2(l.z, l.w), make_float2(x0.z, x0.w));
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
-        if (lane == 0) {
-            float2* up = a.u + static_cast<size_t>(i) * a.ld + c0;
-#pragma unroll
-            for (int q = 0; q < 4; ++q)
-                if (rbase + q < nj) stcg2(up + rbase + q, acc[q]);
-        }
-    }
+// Consensus update of update chunk `chunk` (entries row0 .. row0 + 16 of
+// column block j), run by the warp that completed the chunk: v_j, s_j^i over
+// those columns (with one column block also the next iteration's q_i there),
+// the chunk's residual partials, and, by the warp that completes the last
+// chunk of all, the iteration's residual record.
+__device__ void update_chunk(const DirectArgs& a, int j, int c0, int nj, int row0, int chunk, long long k,
+                             int lane) {
     __threadfence();
-    __syncthreads();
-    const int chunk = a.chunk_off[j] + chunk_in;
-    if (tid == 0) last = atomicAdd(a.cnt_upd + chunk, 1u) == static_cast<unsigned>(a.M - 1);
-    __syncthreads();
-    if (!last || warp != 0) return;
-    __threadfence();
-    // consensus update of columns c0 + row0 + lane
     float d[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
     const int cl = row0 + lane;
-    if (cl < nj) {
+    if (lane < kDirChunk && cl < nj) {
+        // replicas eight at a time, every load of a group issued before its use
         const int col = c0 + cl;
         const float2 vv = ldcg2(a.v + col);
         float2 sum = make_float2(0.f, 0.f);
-        for (int r = 0; r < a.M; ++r) {
-            const float2 uu = ldcg2(a.u + static_cast<size_t>(r) * a.ld + col);
-            const float2 ss = ldcg2(a.s + static_cast<size_t>(r) * a.ld + col);
-            sum.x += uu.x + ss.x;
-            sum.y += uu.y + ss.y;
+        for (int rg = 0; rg < a.M; rg += 8) {
+            float2 uu[8], ss[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const bool in = rg + q < a.M;
+                const size_t o = static_cast<size_t>(rg + q) * a.ld + col;
+                uu[q] = in ? ldcg2(a.u + o) : make_float2(0.f, 0.f);
+                ss[q] = in ? ldcg2(a.s + o) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                sum.x += uu[q].x + ss[q].x;
+                sum.y += uu[q].y + ss[q].y;
+            }
         }
         const float2 av = make_float2(sum.x * a.inv_M, sum.y * a.inv_M);
         const float2 vn = shrink(av, a.kappa);
         d[1] = sq2(make_float2(vn.x - vv.x, vn.y - vv.y));
         d[3] = sq2(vn);
-        for (int r = 0; r < a.M; ++r) {
-            float2* sp = a.s + static_cast<size_t>(r) * a.ld + col;
-            const float2 uu = ldcg2(a.u + static_cast<size_t>(r) * a.ld + col);
-            const float2 ss = ldcg2(sp);
-            const float2 sn = make_float2(ss.x + uu.x - vn.x, ss.y + uu.y - vn.y);
-            d[0] += sq2(make_float2(uu.x - vn.x, uu.y - vn.y));
-            d[2] += sq2(uu);
-            d[4] += sq2(sn);
-            stcg2(sp, sn);
+        float2* qn = a.Q + (a.N == 1 ? static_cast<size_t>((k + 1) & 1) * a.P * a.npitch : 0);
+        for (int rg = 0; rg < a.M; rg += 8) {
+            float2 uu[8], ss[8], cv[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                const bool in = rg + q < a.M;
+                const size_t o = static_cast<size_t>(rg + q) * a.ld + col;
+                uu[q] = in ? ldcg2(a.u + o) : make_float2(0.f, 0.f);
+                ss[q] = in ? ldcg2(a.s + o) : make_float2(0.f, 0.f);
+                cv[q] = (in && a.N == 1) ? ldcg2(a.C + static_cast<size_t>(rg + q) * a.npitch + col)
+                                         : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                if (rg + q >= a.M) continue;
+                const float2 sn = make_float2(ss[q].x + uu[q].x - vn.x, ss[q].y + uu[q].y - vn.y);
+                d[0] += sq2(make_float2(uu[q].x - vn.x, uu[q].y - vn.y));
+                d[2] += sq2(uu[q]);
+                d[4] += sq2(sn);
+                stcg2(a.s + static_cast<size_t>(rg + q) * a.ld + col, sn);
+                if (a.N == 1)   // q_i of the next iteration: H_i^H g_i + rho (v - s_i)
+                    stcg2(qn + static_cast<size_t>(rg + q) * a.npitch + col,
+                          make_float2(cv[q].x + a.rho * (vn.x - sn.x), cv[q].y + a.rho * (vn.y - sn.y)));
+            }
         }
         stcg2(a.v + col, vn);
     }
 #pragma unroll
     for (int q = 0; q < 5; ++q)
         for (int o = 16; o > 0; o >>= 1) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+    int fin = 0;
     if (lane == 0) {
 #pragma unroll
         for (int q = 0; q < 5; ++q) __stcg(a.res_chunk + static_cast<size_t>(chunk) * 5 + q, static_cast<double>(d[q]));
         a.cnt_upd[chunk] = 0u;
         __threadfence();
-        last = atomicAdd(a.cnt_glob, 1u) == static_cast<unsigned>(a.nchunks - 1);
+        fin = atomicAdd(a.cnt_glob, 1u) == static_cast<unsigned>(a.nchunks - 1);
     }
-    __syncwarp();
-    if (!__shfl_sync(0xffffffffu, last, 0)) return;
+    if (!__shfl_sync(0xffffffffu, fin, 0)) return;
     __threadfence();
     // residual record of the iteration (the same five norms as the persistent kernel)
     double acc[5] = {0, 0, 0, 0, 0};
@@ -262,7 +306,6 @@ __global__ void __launch_bounds__(kDirThreads) dir_factor_kernel(const DirectArg
     for (int q = 0; q < 5; ++q) acc[q] = warp_sum_d(acc[q]);
     if (lane == 0) {
         a.cnt_glob[0] = 0u;
-        const long long k = __ldcg(a.k_done);
         const double Md = static_cast<double>(a.M);
         double rec[5];
         rec[0] = acc[0];
@@ -291,55 +334,352 @@ __global__ void __launch_bounds__(kDirThreads) dir_factor_kernel(const DirectArg
     }
 }
 
-// ---- row pass: ghat_b = H_b u_b, eight rows per warp --------------------------
-__global__ void __launch_bounds__(kDirThreads) dir_rows_kernel(const DirectArgs a) {
-    extern __shared__ float2 us[];
-    __shared__ int last;
+// ---- factor pass + update ----------------------------------------------------
+// The factor rows of all blocks, concatenated, are cut into one contiguous
+// range per warp (two CTAs of eight warps per SM, one wave).  A warp takes its
+// rows up to four at a time (never across a block or an update chunk), with
+// four 16-byte loads per row in flight per lane, and q_b through the
+// read-only cache.  Each update chunk counts the rows done for it over the M
+// replicas; the warp whose rows complete it runs update_chunk.
+__global__ void __launch_bounds__(kDirFacThreads, 2) dir_factor_kernel(const DirectArgs a) {
     if (stopped(a)) return;
-    const int bt = blockIdx.x % a.rtn, p = blockIdx.x / a.rtn;
-    const int i = p / a.N, j = p - i * a.N;
-    const int r0 = a.row_off[i], mi = a.row_off[i + 1] - r0;
-    const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int rt0 = bt * kDirRowTile;
-    if (rt0 < mi) {
-        const float2* up = a.u + static_cast<size_t>(i) * a.ld + c0;
-        for (int c = tid; c < nj; c += blockDim.x) us[c] = ldcg2(up + c);
-        __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpc = blockDim.x >> 5;
+    const long long W = static_cast<long long>(gridDim.x) * wpc;
+    const long long gw = static_cast<long long>(blockIdx.x) * wpc + (threadIdx.x >> 5);
+    int r = static_cast<int>(gw * a.frows / W);
+    const int rend = static_cast<int>((gw + 1) * a.frows / W);
+    if (r >= rend) return;
+    const long long k = __ldcg(a.k_done);
+    const size_t qslot = a.N == 1 ? static_cast<size_t>(k & 1) * a.P * a.npitch : 0;
+    int p = 0;
+    while (a.F_off[p + 1] <= r) ++p;
+    while (r < rend) {
+        while (a.F_off[p + 1] <= r) ++p;
+        const int i = p / a.N, j = p - i * a.N;
+        const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
+        const int row = r - a.F_off[p];
+        const int row0 = row - row % kDirChunk;
+        const int cend = min(row0 + kDirChunk, nj);
+        const int g = min(min(4, cend - row), rend - r);
+        const int npairs = (nj + 1) >> 1;
+        const float4* q4 = reinterpret_cast<const float4*>(a.Q + qslot + static_cast<size_t>(p) * a.npitch);
+        const float2* Lp = a.L + a.L_off[p];
+        const int pitch = a.L_pitch[p];
+        const float4* lr[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)   // rows past the group repeat its last row and are dropped
+            lr[q] = reinterpret_cast<const float4*>(Lp + static_cast<size_t>(row + min(q, g - 1)) * pitch);
+        float2 acc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+        int e = lane;
+        for (; e + 96 < npairs; e += 128) {
+            float4 x[4], l[4][4];
+#pragma unroll
+            for (int t = 0; t < 4; ++t) x[t] = __ldg(q4 + e + 32 * t);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) l[q][t] = __ldg(lr[q] + e + 32 * t);
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+#pragma unroll
+                for (int t = 0; t < 4; ++t) {
+                    cfma(acc[q], make_float2(l[q][t].x, l[q][t].y), make_float2(x[t].x, x[t].y));
+                    cfma(acc[q], make_float2(l[q][t].z, l[q][t].w), make_float2(x[t].z, x[t].w));
+                }
+        }
+        for (; e < npairs; e += 32) {
+            const float4 x = __ldg(q4 + e);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float4 l = __ldg(lr[q] + e);
+                cfma(acc[q], make_float2(l.x, l.y), make_float2(x.x, x.y));
+                cfma(acc[q], make_float2(l.z, l.w), make_float2(x.z, x.w));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
+        int last = 0;
+        const int chunk = a.chunk_off[j] + row0 / kDirChunk;
+        if (lane == 0) {
+            float2* up = a.u + static_cast<size_t>(i) * a.ld + c0 + row;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+                if (q < g) stcg2(up + q, acc[q]);
+            __threadfence();
+            const unsigned need = static_cast<unsigned>(a.M * (cend - row0));
+            last = atomicAdd(a.cnt_upd + chunk, static_cast<unsigned>(g)) + g == need;
+        }
+        if (__shfl_sync(0xffffffffu, last, 0)) update_chunk(a, j, c0, nj, row0, chunk, k, lane);
+        r += g;
+    }
+}
+
+// ---- streamed factor pass + update -------------------------------------------
+// The same work as dir_factor_kernel for blocks up to kDirBulkMaxCols wide:
+// CTA c takes the c-th balanced range of the concatenated factor rows; one
+// producer lane streams it stage by stage (up to four consecutive rows of one
+// block and one update chunk, contiguous in memory) with one 1-D bulk copy
+// per row into a ring of shared-memory slots.  Every consumer warp takes one
+// eighth of the columns of all rows of a stage (each q_b load serves the four
+// rows); the warp that adds its partial sums last (a shared-memory counter per
+// slot, no barrier) sums the eight in warp order, writes u and adds the rows to
+// the CTA's table of update chunks in shared memory.  After the last stage the
+// table's counts go to the global chunk counters and the warps that complete a
+// chunk run its update, so no stage waits for a global atomic or an update.
+// Every wait is bounded (ADMM_ETIMEOUT), and the producer waits for all its
+// copies before the CTA ends.
+__global__ void __launch_bounds__((kDirBulkWarps + 1) * 32, 1) dir_factor_stream_kernel(const DirectArgs a) {
+    extern __shared__ __align__(128) unsigned char fsm[];
+    if (stopped(a)) return;
+    const int NS = a.fac_ns;
+    unsigned char* ring = fsm;
+    uint64_t* full = reinterpret_cast<uint64_t*>(fsm + static_cast<size_t>(NS) * a.fac_stage);
+    uint64_t* empty = full + NS;
+    float2* red = reinterpret_cast<float2*>(empty + NS);              // NS x kDirBulkWarps x 4
+    int* red_cnt = reinterpret_cast<int*>(red + NS * kDirBulkWarps * 4);  // NS
+    int* tab_chunk = red_cnt + NS;                                    // kDirDeferred chunks of this CTA
+    int* tab_cnt = tab_chunk + kDirDeferred;                          // rows counted for each
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ra = static_cast<int>(static_cast<long long>(blockIdx.x) * a.frows / gridDim.x);
+    const int rb = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * a.frows / gridDim.x);
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < NS; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], kDirBulkWarps);
+            red_cnt[q] = 0;
+        }
+        for (int q = 0; q < kDirDeferred; ++q) tab_cnt[q] = 0;
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+    const long long k = __ldcg(a.k_done);
+    if (warp == kDirBulkWarps) {
+        if (lane != 0) return;
+        int issued = 0, slot = 0, p = 0;
+        uint32_t ph = 0;
+        for (int r = ra; r < rb;) {
+            while (a.F_off[p + 1] <= r) ++p;
+            const int j = p % a.N;
+            const int nj = a.col_off[j + 1] - a.col_off[j];
+            const int row = r - a.F_off[p];
+            const int row0 = row - row % kDirChunk;
+            const int g = min(min(4, min(row0 + kDirChunk, nj) - row), rb - r);
+            if (!mbar_wait_bounded(&empty[slot], ph ^ 1u, a.status, a.timeout_ns)) break;
+            const int pitch = a.L_pitch[p];
+            const uint32_t rbytes = static_cast<uint32_t>(pitch) * sizeof(float2);
+            mbar_arrive_expect_tx(&full[slot], rbytes * g);
+            const float2* src = a.L + a.L_off[p] + static_cast<size_t>(row) * pitch;
+            for (int q = 0; q < g; ++q)   // one copy per factor row
+                bulk_load(ring + static_cast<size_t>(slot) * a.fac_stage + static_cast<size_t>(q) * rbytes,
+                          src + static_cast<size_t>(q) * pitch, rbytes, &full[slot]);
+            ++issued;
+            if (++slot == NS) {
+                slot = 0;
+                ph ^= 1u;
+            }
+            r += g;
+        }
+        // no copy into this CTA's shared memory may outlive it
+        for (int q = 0; q < NS && q < issued; ++q) {
+            const int lastq = q + ((issued - 1 - q) / NS) * NS;
+            mbar_wait_bounded(&full[q], static_cast<uint32_t>((lastq / NS) & 1), a.status, a.timeout_ns);
+        }
+        return;
+    }
+    const size_t qslot = a.N == 1 ? static_cast<size_t>(k & 1) * a.P * a.npitch : 0;
+    int slot = 0, p = 0, qp = -1, lc = -1, prev_chunk = -1;
+    uint32_t ph = 0;
+    float4 qr[4];
+    for (int r = ra; r < rb;) {
+        while (a.F_off[p + 1] <= r) ++p;
+        const int i = p / a.N, j = p - i * a.N;
+        const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
+        const int row = r - a.F_off[p];
+        const int row0 = row - row % kDirChunk;
+        const int cend = min(row0 + kDirChunk, nj);
+        const int g = min(min(4, cend - row), rb - r);
+        const int chunk = a.chunk_off[j] + row0 / kDirChunk;
+        if (chunk != prev_chunk) {   // every consumer warp numbers the CTA's chunks alike
+            ++lc;
+            prev_chunk = chunk;
+        }
+        if (!mbar_wait_bounded(&full[slot], ph, a.status, a.timeout_ns)) break;
+        const int pitch = a.L_pitch[p];
+        const int npairs = (nj + 1) >> 1;
+        const int seg = (npairs + kDirBulkWarps - 1) / kDirBulkWarps;
+        const int e_beg = warp * seg, e_end = min(npairs, e_beg + seg);
+        const float4* l4 = reinterpret_cast<const float4*>(ring + static_cast<size_t>(slot) * a.fac_stage);
+        if (p != qp) {   // this warp's segment of q_b, kept in registers while the block lasts
+            const float4* q4 = reinterpret_cast<const float4*>(a.Q + qslot + static_cast<size_t>(p) * a.npitch);
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int e = e_beg + lane + 32 * t;
+                qr[t] = e < e_end ? __ldg(q4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            qp = p;
+        }
+        const int rstep = pitch / 2;   // float4 per factor row
+        float2 acc[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+        float4 l[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const int e = e_beg + lane + 32 * t;
+                l[q][t] = (q < g && e < e_end) ? l4[q * rstep + e] : make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                cfma(acc[q], make_float2(l[q][t].x, l[q][t].y), make_float2(qr[t].x, qr[t].y));
+                cfma(acc[q], make_float2(l[q][t].z, l[q][t].w), make_float2(qr[t].z, qr[t].w));
+            }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
+        float2* rs = red + static_cast<size_t>(slot) * kDirBulkWarps * 4;
+        int last = 0;
+        if (lane == 0) {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) rs[warp * 4 + q] = acc[q];
+            __threadfence_block();
+            last = atomicAdd(&red_cnt[slot], 1) == kDirBulkWarps - 1;
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        int now = 0;   // the chunk table is full: count this stage's rows at once
+        if (last) {
+            __threadfence_block();
+            if (lane < g) {
+                float2 t = make_float2(0.f, 0.f);
+                for (int w = 0; w < kDirBulkWarps; ++w) {
+                    const volatile float* x = reinterpret_cast<volatile float*>(&rs[w * 4 + lane]);
+                    t.x += x[0];
+                    t.y += x[1];
+                }
+                stcg2(a.u + static_cast<size_t>(i) * a.ld + c0 + row + lane, t);
+            }
+            if (lane == 0) {
+                red_cnt[slot] = 0;
+                if (lc < kDirDeferred) {
+                    tab_chunk[lc] = chunk;
+                    atomicAdd(&tab_cnt[lc], g);
+                } else {
+                    now = 1;
+                }
+            }
+            now = __shfl_sync(0xffffffffu, now, 0);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[slot]);
+        if (now) {
+            __threadfence();
+            int done = 0;
+            if (lane == 0)
+                done = atomicAdd(a.cnt_upd + chunk, static_cast<unsigned>(g)) + g ==
+                       static_cast<unsigned>(a.M * (cend - row0));
+            if (__shfl_sync(0xffffffffu, done, 0)) update_chunk(a, j, c0, nj, row0, chunk, k, lane);
+        }
+        if (++slot == NS) {
+            slot = 0;
+            ph ^= 1u;
+        }
+        r += g;
+    }
+    // the chunks counted in the table: one global count each, then the updates
+    // (every consumer warp reaches this barrier, also after a failed wait)
+    __threadfence();
+    asm volatile("bar.sync 1, %0;" ::"r"(kDirBulkWarps * 32) : "memory");
+    const int nlc = min(lc + 1, kDirDeferred);
+    for (int e = warp; e < nlc; e += kDirBulkWarps) {
+        const int chunk = tab_chunk[e], cnt = tab_cnt[e];
+        if (cnt == 0) continue;
+        int j = 0;
+        while (a.chunk_off[j + 1] <= chunk) ++j;
+        const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
+        const int row0 = (chunk - a.chunk_off[j]) * kDirChunk;
+        int done = 0;
+        if (lane == 0)
+            done = atomicAdd(a.cnt_upd + chunk, static_cast<unsigned>(cnt)) + cnt ==
+                   static_cast<unsigned>(a.M * (min(row0 + kDirChunk, nj) - row0));
+        if (__shfl_sync(0xffffffffu, done, 0)) update_chunk(a, j, c0, nj, row0, chunk, k, lane);
+    }
+}
+
+// ---- row pass: ghat_b = H_b u_b -----------------------------------------------
+// The rows of H of all blocks, concatenated, are cut into one contiguous range
+// per warp (two CTAs of eight warps per SM, one wave).  A warp takes its rows
+// up to eight at a time within one block, reading 16-byte column pairs from the
+// block's first column rounded down to even; u_b comes through the read-only
+// cache with the halves outside the block zeroed.
+__global__ void __launch_bounds__(kDirRowThreads, 2) dir_rows_kernel(const DirectArgs a) {
+    __shared__ int last;
+    if (!stopped(a)) {
+        const int lane = threadIdx.x & 31;
+        const int wpc = blockDim.x >> 5;
+        const long long W = static_cast<long long>(gridDim.x) * wpc;
+        const long long gw = static_cast<long long>(blockIdx.x) * wpc + (threadIdx.x >> 5);
+        int x = static_cast<int>(gw * a.hrows / W);
+        const int xend = static_cast<int>((gw + 1) * a.hrows / W);
         // after this iteration's update the device count is k + 1: its slot
         const size_t Nm = static_cast<size_t>(a.N) * a.m;
-        float2* out = a.ghat + static_cast<size_t>(__ldcg(a.k_done) & 1) * Nm + static_cast<size_t>(j) * a.m + r0;
-        const int rw = rt0 + warp * 8;
-        if (rw < mi) {
-            const float2* hr[8];
+        float2* outb = a.ghat + static_cast<size_t>(__ldcg(a.k_done) & 1) * Nm;
+        int p = 0;
+        while (x < xend) {
+            while (a.R_off[p + 1] <= x) ++p;
+            const int i = p / a.N, j = p - i * a.N;
+            const int r0 = a.row_off[i], mi = a.row_off[i + 1] - r0;
+            const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
+            const int row = x - a.R_off[p];
+            const int g = min(min(8, mi - row), xend - x);
+            const int cb = c0 & ~1;
+            const int npairs = (c0 + nj - cb + 1) >> 1;
+            const float4* u4 = reinterpret_cast<const float4*>(a.u + static_cast<size_t>(i) * a.ld + cb);
+            const float4* hr[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q)
-                hr[q] = a.H + static_cast<size_t>(r0 + min(rw + q, mi - 1)) * a.ld + c0;
+                hr[q] = reinterpret_cast<const float4*>(a.H + static_cast<size_t>(r0 + row + min(q, g - 1)) * a.ld + cb);
             float2 acc[8];
 #pragma unroll
             for (int q = 0; q < 8; ++q) acc[q] = make_float2(0.f, 0.f);
-            for (int c = lane; c < nj; c += 32) {
-                const float2 x = us[c];
-                float2 h[8];
+            for (int e = lane; e < npairs; e += 64) {
+                const bool two = e + 32 < npairs;
+                float4 u[2];
+                u[0] = __ldg(u4 + e);
+                u[1] = two ? __ldg(u4 + e + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-                for (int q = 0; q < 8; ++q) h[q] = __ldg(hr[q] + c);
+                for (int t = 0; t < 2; ++t) {
+                    const int col = cb + 2 * (e + 32 * t);
+                    if (col < c0) u[t].x = u[t].y = 0.f;
+                    if (col + 1 >= c0 + nj) u[t].z = u[t].w = 0.f;
+                }
+                float4 h[2][8];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) cfma(acc[q], h[q], x);
+                for (int q = 0; q < 8; ++q) {
+                    h[0][q] = __ldg(hr[q] + e);
+                    h[1][q] = two ? __ldg(hr[q] + e + 32) : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+#pragma unroll
+                for (int t = 0; t < 2; ++t)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        cfma(acc[q], make_float2(h[t][q].x, h[t][q].y), make_float2(u[t].x, u[t].y));
+                        cfma(acc[q], make_float2(h[t][q].z, h[t][q].w), make_float2(u[t].z, u[t].w));
+                    }
             }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) acc[q] = warp_sum(acc[q]);
-            if (lane < 8) {
-                float2 mine = acc[0];
-#pragma unroll
-                for (int q = 1; q < 8; ++q)
-                    if (lane == q) mine = acc[q];
-                if (rw + lane < mi) stcg2(out + rw + lane, mine);
-            }
+            const float2 tot = lanes_sum8(acc, lane);
+            const int q = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+            if ((lane & 3) == 0 && q < g) stcg2(outb + static_cast<size_t>(j) * a.m + r0 + row + q, tot);
+            x += g;
         }
+        __threadfence();
     }
-    __threadfence();
     __syncthreads();
-    if (tid == 0) {
+    if (threadIdx.x == 0) {
         last = atomicAdd(a.cnt_glob + 1, 1u) == gridDim.x - 1;
         if (last) {
             a.cnt_glob[1] = 0u;
@@ -375,35 +715,50 @@ __global__ void conj_transpose_kernel(const float2* __restrict__ H, int64_t m, i
 }  // namespace
 
 cudaError_t prepare_direct(int smem_optin) {
-    const int lim = std::min(smem_optin, kDirMaxCols * 8);
-    cudaError_t e = cudaFuncSetAttribute(dir_factor_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(dir_rows_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, lim);
+    const int cols = (kDirColRows + 1 + (kDirColThreads / 32) * 2 * kDirColPairs) * 8;
+    cudaError_t e =
+        cudaFuncSetAttribute(dir_cols_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, std::min(smem_optin, cols));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(dir_factor_stream_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin);
     return e;
+}
+
+size_t stream_smem(int ns, int stage) {
+    return static_cast<size_t>(ns) * stage + 2 * ns * sizeof(uint64_t) + ns * kDirBulkWarps * 4 * sizeof(float2) +
+           ns * sizeof(int) + 2 * kDirDeferred * sizeof(int);
+}
+
+cudaError_t direct_stream_per_sm(int smem, int* per_sm) {
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, dir_factor_stream_kernel, (kDirBulkWarps + 1) * 32,
+                                                         static_cast<size_t>(smem));
 }
 
 cudaError_t launch_dir_cols(const DirectArgs& a, int mode, cudaStream_t s) {
     const int rows = (a.mimax + a.S - 1) / a.S + 1;
-    const size_t smem = static_cast<size_t>(rows) * sizeof(float2);
-    dir_cols_kernel<<<a.P * a.ccn * a.S, kDirThreads, smem, s>>>(a, mode);
+    const size_t smem = (static_cast<size_t>(rows) + (kDirColThreads / 32) * 2 * kDirColPairs) * sizeof(float2);
+    dir_cols_kernel<<<a.P * a.ccn * a.S, kDirColThreads, smem, s>>>(a, mode);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dir_q(const DirectArgs& a, cudaStream_t s) {
     const long long total = static_cast<long long>(a.M) * a.n;
-    const int blocks = static_cast<int>(std::min<long long>((total + kDirThreads - 1) / kDirThreads, 4096));
-    dir_q_kernel<<<blocks, kDirThreads, 0, s>>>(a);
+    const int blocks = static_cast<int>(std::min<long long>((total + kDirFacThreads - 1) / kDirFacThreads, 4096));
+    dir_q_kernel<<<blocks, kDirFacThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_dir_factor(const DirectArgs& a, cudaStream_t s) {
-    const size_t smem = static_cast<size_t>((a.njmax + 1) / 2) * sizeof(float4);
-    dir_factor_kernel<<<a.P * a.fcn, kDirThreads, smem, s>>>(a);
+    if (a.fac_stream) {
+        const size_t smem = stream_smem(a.fac_ns, a.fac_stage);
+        dir_factor_stream_kernel<<<a.fac_ctas, (kDirBulkWarps + 1) * 32, smem, s>>>(a);
+    } else {
+        dir_factor_kernel<<<a.ctas, kDirFacThreads, 0, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_dir_rows(const DirectArgs& a, cudaStream_t s) {
-    const size_t smem = static_cast<size_t>(a.njmax) * sizeof(float2);
-    dir_rows_kernel<<<a.P * a.rtn, kDirThreads, smem, s>>>(a);
+    dir_rows_kernel<<<a.ctas, kDirRowThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -236,11 +236,16 @@ cudaError_t launch_cholesky_inverse(const FactorArgs& f, cudaStream_t s);
 // CTA waits for another, and a launch sequence is stable under graph capture
 // (the estimated-data slot is taken from the device iteration count).
 
-constexpr int kDirThreads = 256;
-constexpr int kDirColTile = 256;     // columns per column-pass CTA (one per thread)
-constexpr int kDirChunk = 32;        // factor rows (= entries of u_b) per factor CTA
-constexpr int kDirRowTile = 64;      // rows of H_b per row-pass CTA
-constexpr int kDirMaxCols = 12288;   // widest block of the direct branch (q_b, u_b staged in shared memory)
+constexpr int kDirColThreads = 256;  // column pass: eight warps splitting the rows
+constexpr int kDirColPairs = 128;    // column pairs per column-pass CTA (four per lane)
+constexpr int kDirColRows = 4096;    // most rows per column-pass split (gt_b staged in shared memory)
+constexpr int kDirFacThreads = 256;  // factor pass: eight warps, up to four rows at a time each
+constexpr int kDirChunk = 16;        // entries of u_b per update chunk
+constexpr int kDirRowThreads = 256;  // row pass: eight warps, up to eight rows at a time each
+constexpr int kDirBulkWarps = 8;     // streamed factor pass: consumer warps (an eighth of the columns each)
+constexpr int kDirDeferred = 32;     // update chunks a streamed factor CTA counts in shared memory
+constexpr int kDirBulkMaxCols = 2048;  // widest block the streamed factor pass takes (16 KB rows)
+constexpr int kDirMaxCols = 12288;   // widest block of the direct branch (u_b staged in shared memory)
 
 struct DirectArgs {
     int m, n, ld, M, N, P;
@@ -258,12 +263,21 @@ struct DirectArgs {
     const long long* L_off;
     const int* L_pitch;
     float2* C;                // P x npitch: H_i^H g_i (one column block)
-    float2* Q;                // P x npitch: q_b
+    float2* Q;                // q_b, P x npitch; with one column block two slots by
+                              // iteration parity (the update writes the next q)
     float2* part;             // S x P x npitch: column-pass partial sums
     int S;                    // row splits of the column pass
     int ccn;                  // column tiles per block in the column pass
-    int fcn;                  // factor chunks per block (ceil(njmax / kDirChunk))
-    int rtn;                  // row tiles per block in the row pass
+    int ctas;                 // CTAs of the factor and row passes (two per SM)
+    int frows;                // factor rows of all blocks (sum of n_j over the blocks)
+    int hrows;                // rows of H of all blocks (sum of m_i over the blocks)
+    int fac_stream;           // factor pass: 1 = bulk copies into a shared-memory ring
+    int fac_ctas;             // CTAs of the streamed factor pass
+    int fac_ns;               // its ring stages
+    int fac_stage;            // its stage bytes (four factor rows of the widest block)
+    long long timeout_ns;     // bound of every wait of the streamed factor pass
+    const int* F_off;         // P + 1: first factor row of block p in the concatenation
+    const int* R_off;         // P + 1: first H row of block p in the concatenation
     unsigned* cnt_cols;       // P x ccn
     unsigned* cnt_upd;        // nchunks
     unsigned* cnt_glob;       // [0] update chunks finished, [1] row-pass CTAs finished
@@ -284,11 +298,15 @@ struct DirectArgs {
 
 // column pass: mode 0 writes Q = H^H gt + rho z, mode 1 writes C = H^H g (no z)
 cudaError_t launch_dir_cols(const DirectArgs& a, int mode, cudaStream_t s);
-// Q = C + rho z (one column block)
+// Q[slot of the device iteration count] = C + rho z (one column block)
 cudaError_t launch_dir_q(const DirectArgs& a, cudaStream_t s);
 cudaError_t launch_dir_factor(const DirectArgs& a, cudaStream_t s);
 cudaError_t launch_dir_rows(const DirectArgs& a, cudaStream_t s);
 cudaError_t prepare_direct(int smem_optin);
+// shared memory of the streamed factor pass with `ns` stages of `stage` bytes,
+// and its resident CTAs per SM with `smem` bytes
+size_t stream_smem(int ns, int stage);
+cudaError_t direct_stream_per_sm(int smem, int* per_sm);
 // HT (n x ldT) = H^H of the m x ld matrix H
 cudaError_t launch_conj_transpose(const float2* H, int64_t m, int64_t n, int64_t ld, float2* HT, int64_t ldT,
                                   cudaStream_t s);
