@@ -28,12 +28,12 @@ int round_up(int64_t x, int64_t q) { return static_cast<int>((x + q - 1) / q * q
 struct DirectState {
     float2 *C = nullptr, *Q = nullptr, *part = nullptr;
     unsigned* cnt = nullptr;       // column tiles, update chunks, two global counters
-    int* ints = nullptr;           // chunk_off (N + 1), L_pitch (P), F_off (P + 1), R_off (P + 1)
+    int* ints = nullptr;           // chunk_off (N + 1), L_pitch (P), F_off, R_off, I_off (P + 1 each)
     long long* L_off = nullptr;    // P
     double* res_chunk = nullptr;
     int* stop_pending = nullptr;
     int npitch = 0, njmax = 0, S = 1, ccn = 1, ctas = 1, frows = 0, hrows = 0, nchunks = 0, ncnt = 0;
-    int fac_stream = 0, fac_ctas = 0, fac_ns = 0, fac_stage = 0;   // streamed factor pass
+    int fac_stream = 0, fac_ctas = 0, fac_ns = 0, fac_stage = 0, fitems = 0;   // streamed factor pass
     int64_t bytes = 0;
     bool c_valid = false;          // C = H_i^H g_i matches g (one column block)
     bool q_valid = false;          // Q of the current iteration matches C, v, s and rho
@@ -695,7 +695,15 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
     d.hrows = roff[P];
     ints.insert(ints.end(), foff.begin(), foff.end());
     ints.insert(ints.end(), roff.begin(), roff.end());
-    d.ncnt = P * d.ccn + d.nchunks + 2;
+    // items of the streamed factor pass: the update chunks of each block
+    std::vector<int> ioff(P + 1, 0);
+    for (int q = 0; q < P; ++q) {
+        const int j = q % h->N;
+        ioff[q + 1] = ioff[q] + (h->col_off[j + 1] - h->col_off[j] + admm::kDirChunk - 1) / admm::kDirChunk;
+    }
+    d.fitems = ioff[P];
+    ints.insert(ints.end(), ioff.begin(), ioff.end());
+    d.ncnt = P * d.ccn + d.nchunks + 4;
     const size_t vec = static_cast<size_t>(P) * d.npitch;
     // the column pass writes partials in both uses (q_b every iteration with
     // several column blocks, C = H_i^H g_i once per data vector with one)
@@ -757,6 +765,8 @@ admm::DirectArgs direct_args(admm_t* h, int check_stop, double eps_abs, double e
     a.hrows = d.hrows;
     a.F_off = d.ints + (h->N + 1) + a.P;
     a.R_off = d.ints + (h->N + 1) + a.P + (a.P + 1);
+    a.I_off = d.ints + (h->N + 1) + a.P + 2 * (a.P + 1);
+    a.fitems = d.fitems;
     a.cnt_cols = d.cnt;
     a.cnt_upd = d.cnt + a.P * d.ccn;
     a.cnt_glob = d.cnt + a.P * d.ccn + d.nchunks;

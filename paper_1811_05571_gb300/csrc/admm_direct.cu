@@ -418,19 +418,22 @@ __global__ void __launch_bounds__(kDirFacThreads, 2) dir_factor_kernel(const Dir
 }
 
 // ---- streamed factor pass + update -------------------------------------------
-// The same work as dir_factor_kernel for blocks up to kDirBulkMaxCols wide:
-// CTA c takes the c-th balanced range of the concatenated factor rows; one
-// producer lane streams it stage by stage (up to four consecutive rows of one
-// block and one update chunk, contiguous in memory) with one 1-D bulk copy
-// per row into a ring of shared-memory slots.  Every consumer warp takes one
-// eighth of the columns of all rows of a stage (each q_b load serves the four
-// rows); the warp that adds its partial sums last (a shared-memory counter per
-// slot, no barrier) sums the eight in warp order, writes u and adds the rows to
-// the CTA's table of update chunks in shared memory.  After the last stage the
-// table's counts go to the global chunk counters and the warps that complete a
-// chunk run its update, so no stage waits for a global atomic or an update.
-// Every wait is bounded (ADMM_ETIMEOUT), and the producer waits for all its
-// copies before the CTA ends.
+// The same work as dir_factor_kernel for blocks up to kDirBulkMaxCols wide.
+// Work items are the update chunks of every block (16 factor rows of block p,
+// contiguous in memory), handed out by a global counter: one producer lane per
+// CTA takes an item (fetching the next one while it streams the current), and
+// streams it in stages of up to four rows with one 1-D bulk copy per row into
+// a ring of shared-memory slots, each slot carrying its stage's description;
+// a slot with no rows ends the CTA's work.  Every consumer warp takes one
+// eighth of the columns of all rows of a stage (its segment of q_b stays in
+// registers while the block lasts); the warp that adds its partial sums last
+// (a shared-memory counter per slot, no barrier) sums the eight in warp order,
+// writes u and adds the rows to the CTA's table of chunks in shared memory.
+// After the last stage the table's counts go to the global chunk counters and
+// the warps that complete a chunk run its update, so no stage waits for a
+// global atomic or an update.  The last CTA to run out of items resets the
+// item counter.  Every wait is bounded (ADMM_ETIMEOUT), and the producer waits
+// for all its copies before the CTA ends.
 __global__ void __launch_bounds__((kDirBulkWarps + 1) * 32, 1) dir_factor_stream_kernel(const DirectArgs a) {
     extern __shared__ __align__(128) unsigned char fsm[];
     if (stopped(a)) return;
@@ -438,13 +441,12 @@ __global__ void __launch_bounds__((kDirBulkWarps + 1) * 32, 1) dir_factor_stream
     unsigned char* ring = fsm;
     uint64_t* full = reinterpret_cast<uint64_t*>(fsm + static_cast<size_t>(NS) * a.fac_stage);
     uint64_t* empty = full + NS;
-    float2* red = reinterpret_cast<float2*>(empty + NS);              // NS x kDirBulkWarps x 4
+    float2* red = reinterpret_cast<float2*>(empty + NS);                  // NS x kDirBulkWarps x 4
     int* red_cnt = reinterpret_cast<int*>(red + NS * kDirBulkWarps * 4);  // NS
-    int* tab_chunk = red_cnt + NS;                                    // kDirDeferred chunks of this CTA
-    int* tab_cnt = tab_chunk + kDirDeferred;                          // rows counted for each
+    int* tab_chunk = red_cnt + NS;                                        // kDirDeferred chunks of this CTA
+    int* tab_cnt = tab_chunk + kDirDeferred;                              // rows counted for each
+    int* meta = tab_cnt + kDirDeferred;                                   // NS x 4: p, row, g, table index
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int ra = static_cast<int>(static_cast<long long>(blockIdx.x) * a.frows / gridDim.x);
-    const int rb = static_cast<int>(static_cast<long long>(blockIdx.x + 1) * a.frows / gridDim.x);
     if (threadIdx.x == 0) {
         for (int q = 0; q < NS; ++q) {
             mbar_init(&full[q], 1);
@@ -456,75 +458,110 @@ __global__ void __launch_bounds__((kDirBulkWarps + 1) * 32, 1) dir_factor_stream
     }
     __syncthreads();
     const long long k = __ldcg(a.k_done);
+    unsigned* items = a.cnt_glob + 2;   // [0] next item, [1] CTAs out of items
     if (warp == kDirBulkWarps) {
         if (lane != 0) return;
-        int issued = 0, slot = 0, p = 0;
+        int issued = 0, slot = 0, p = 0, nitem = 0;
         uint32_t ph = 0;
-        for (int r = ra; r < rb;) {
-            while (a.F_off[p + 1] <= r) ++p;
+        bool ok = true;
+        int it = static_cast<int>(atomicAdd(items, 1u));
+        while (ok && it < a.fitems) {
+            const int nxt = static_cast<int>(atomicAdd(items, 1u));   // fetched while this item streams
+            while (a.I_off[p + 1] <= it) ++p;
             const int j = p % a.N;
             const int nj = a.col_off[j + 1] - a.col_off[j];
-            const int row = r - a.F_off[p];
-            const int row0 = row - row % kDirChunk;
-            const int g = min(min(4, min(row0 + kDirChunk, nj) - row), rb - r);
-            if (!mbar_wait_bounded(&empty[slot], ph ^ 1u, a.status, a.timeout_ns)) break;
             const int pitch = a.L_pitch[p];
             const uint32_t rbytes = static_cast<uint32_t>(pitch) * sizeof(float2);
-            mbar_arrive_expect_tx(&full[slot], rbytes * g);
-            const float2* src = a.L + a.L_off[p] + static_cast<size_t>(row) * pitch;
-            for (int q = 0; q < g; ++q)   // one copy per factor row
-                bulk_load(ring + static_cast<size_t>(slot) * a.fac_stage + static_cast<size_t>(q) * rbytes,
-                          src + static_cast<size_t>(q) * pitch, rbytes, &full[slot]);
-            ++issued;
-            if (++slot == NS) {
-                slot = 0;
-                ph ^= 1u;
+            const int row_end = min((it - a.I_off[p] + 1) * kDirChunk, nj);
+            for (int row = (it - a.I_off[p]) * kDirChunk; row < row_end;) {
+                const int g = min(4, row_end - row);
+                if (!mbar_wait_bounded(&empty[slot], ph ^ 1u, a.status, a.timeout_ns)) {
+                    ok = false;
+                    break;
+                }
+                int* m = meta + slot * 4;
+                m[0] = p;
+                m[1] = row;
+                m[2] = g;
+                m[3] = nitem;
+                mbar_arrive_expect_tx(&full[slot], rbytes * g);
+                const float2* src = a.L + a.L_off[p] + static_cast<size_t>(row) * pitch;
+                for (int q = 0; q < g; ++q)   // one copy per factor row
+                    bulk_load(ring + static_cast<size_t>(slot) * a.fac_stage + static_cast<size_t>(q) * rbytes,
+                              src + static_cast<size_t>(q) * pitch, rbytes, &full[slot]);
+                ++issued;
+                if (++slot == NS) {
+                    slot = 0;
+                    ph ^= 1u;
+                }
+                row += g;
             }
-            r += g;
+            ++nitem;
+            it = nxt;
         }
-        // no copy into this CTA's shared memory may outlive it
+        // the last CTA out of items resets the item counter for the next launch
+        if (atomicAdd(items + 1, 1u) == gridDim.x - 1) {
+            items[0] = 0u;
+            items[1] = 0u;
+        }
+        // every copy into this CTA's shared memory lands before the closing slot
+        // (which completes one more phase of its slot) and before the CTA ends
         for (int q = 0; q < NS && q < issued; ++q) {
             const int lastq = q + ((issued - 1 - q) / NS) * NS;
             mbar_wait_bounded(&full[q], static_cast<uint32_t>((lastq / NS) & 1), a.status, a.timeout_ns);
         }
+        // closing slot: no rows, no copy
+        if (ok && mbar_wait_bounded(&empty[slot], ph ^ 1u, a.status, a.timeout_ns)) {
+            int* m = meta + slot * 4;
+            m[0] = p;
+            m[1] = 0;
+            m[2] = 0;
+            m[3] = nitem;
+            mbar_arrive(&full[slot]);
+        }
         return;
     }
     const size_t qslot = a.N == 1 ? static_cast<size_t>(k & 1) * a.P * a.npitch : 0;
-    int slot = 0, p = 0, qp = -1, lc = -1, prev_chunk = -1;
+    int slot = 0, qp = -1, nlc = 0;
     uint32_t ph = 0;
-    float4 qr[4];
-    for (int r = ra; r < rb;) {
-        while (a.F_off[p + 1] <= r) ++p;
+    float2 qre[8], qim[8];
+    for (;;) {
+        if (!mbar_wait_bounded(&full[slot], ph, a.status, a.timeout_ns)) break;
+        const int* m = meta + slot * 4;
+        const int p = m[0], row = m[1], g = m[2], lc = m[3];
+        if (g == 0) break;   // closing slot
+        nlc = lc + 1;
         const int i = p / a.N, j = p - i * a.N;
         const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
-        const int row = r - a.F_off[p];
         const int row0 = row - row % kDirChunk;
         const int cend = min(row0 + kDirChunk, nj);
-        const int g = min(min(4, cend - row), rb - r);
         const int chunk = a.chunk_off[j] + row0 / kDirChunk;
-        if (chunk != prev_chunk) {   // every consumer warp numbers the CTA's chunks alike
-            ++lc;
-            prev_chunk = chunk;
-        }
-        if (!mbar_wait_bounded(&full[slot], ph, a.status, a.timeout_ns)) break;
         const int pitch = a.L_pitch[p];
         const int npairs = (nj + 1) >> 1;
         const int seg = (npairs + kDirBulkWarps - 1) / kDirBulkWarps;
         const int e_beg = warp * seg, e_end = min(npairs, e_beg + seg);
         const float4* l4 = reinterpret_cast<const float4*>(ring + static_cast<size_t>(slot) * a.fac_stage);
-        if (p != qp) {   // this warp's segment of q_b, kept in registers while the block lasts
+        if (p != qp) {
+            // this warp's segment of q_b, kept in registers while the block lasts,
+            // as (re, re) and (im, im) pairs for the paired FMAs
             const float4* q4 = reinterpret_cast<const float4*>(a.Q + qslot + static_cast<size_t>(p) * a.npitch);
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
                 const int e = e_beg + lane + 32 * t;
-                qr[t] = e < e_end ? __ldg(q4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                const float4 x = e < e_end ? __ldg(q4 + e) : make_float4(0.f, 0.f, 0.f, 0.f);
+                qre[2 * t] = make_float2(x.x, x.x);
+                qim[2 * t] = make_float2(x.y, x.y);
+                qre[2 * t + 1] = make_float2(x.z, x.z);
+                qim[2 * t + 1] = make_float2(x.w, x.w);
             }
             qp = p;
         }
         const int rstep = pitch / 2;   // float4 per factor row
-        float2 acc[4];
+        // row q: A = sum (L.re q.re, L.im q.re), B = sum (L.re q.im, L.im q.im);
+        // L q = (A.x - B.y, A.y + B.x)
+        float2 A[4], Bv[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < 4; ++q) A[q] = Bv[q] = make_float2(0.f, 0.f);
         float4 l[4][4];
 #pragma unroll
         for (int q = 0; q < 4; ++q)
@@ -537,16 +574,41 @@ __global__ void __launch_bounds__((kDirBulkWarps + 1) * 32, 1) dir_factor_stream
         for (int q = 0; q < 4; ++q)
 #pragma unroll
             for (int t = 0; t < 4; ++t) {
-                cfma(acc[q], make_float2(l[q][t].x, l[q][t].y), make_float2(qr[t].x, qr[t].y));
-                cfma(acc[q], make_float2(l[q][t].z, l[q][t].w), make_float2(qr[t].z, qr[t].w));
+                const float2 lo = make_float2(l[q][t].x, l[q][t].y), hi = make_float2(l[q][t].z, l[q][t].w);
+                A[q] = __ffma2_rn(lo, qre[2 * t], A[q]);
+                Bv[q] = __ffma2_rn(lo, qim[2 * t], Bv[q]);
+                A[q] = __ffma2_rn(hi, qre[2 * t + 1], A[q]);
+                Bv[q] = __ffma2_rn(hi, qim[2 * t + 1], Bv[q]);
             }
+        float2 acc[4];
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[q] = warp_sum(acc[q]);
+        for (int q = 0; q < 4; ++q) acc[q] = make_float2(A[q].x - Bv[q].y, A[q].y + Bv[q].x);
+        // lane sums of the four rows: two halving exchanges, then three plain
+        // steps; row q's sum ends in the lanes whose bits 4..3 spell q
+        {
+            const bool b16 = lane & 16, b8 = lane & 8;
+            float2 h2[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                const float2 keep = b16 ? acc[q + 2] : acc[q], send = b16 ? acc[q] : acc[q + 2];
+                h2[q] = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, send.x, 16),
+                                    keep.y + __shfl_xor_sync(0xffffffffu, send.y, 16));
+            }
+            const float2 keep = b8 ? h2[1] : h2[0], send = b8 ? h2[0] : h2[1];
+            float2 y = make_float2(keep.x + __shfl_xor_sync(0xffffffffu, send.x, 8),
+                                   keep.y + __shfl_xor_sync(0xffffffffu, send.y, 8));
+#pragma unroll
+            for (int o = 4; o > 0; o >>= 1) {
+                y.x += __shfl_xor_sync(0xffffffffu, y.x, o);
+                y.y += __shfl_xor_sync(0xffffffffu, y.y, o);
+            }
+            acc[0] = y;   // row 2 * b16 + b8
+        }
         float2* rs = red + static_cast<size_t>(slot) * kDirBulkWarps * 4;
         int last = 0;
+        if ((lane & 7) == 0) rs[warp * 4 + (lane >> 3)] = acc[0];   // lanes 0, 8, 16, 24: rows 0..3
+        __syncwarp();
         if (lane == 0) {
-#pragma unroll
-            for (int q = 0; q < 4; ++q) rs[warp * 4 + q] = acc[q];
             __threadfence_block();
             last = atomicAdd(&red_cnt[slot], 1) == kDirBulkWarps - 1;
         }
@@ -588,13 +650,12 @@ __global__ void __launch_bounds__((kDirBulkWarps + 1) * 32, 1) dir_factor_stream
             slot = 0;
             ph ^= 1u;
         }
-        r += g;
     }
     // the chunks counted in the table: one global count each, then the updates
     // (every consumer warp reaches this barrier, also after a failed wait)
     __threadfence();
     asm volatile("bar.sync 1, %0;" ::"r"(kDirBulkWarps * 32) : "memory");
-    const int nlc = min(lc + 1, kDirDeferred);
+    nlc = min(nlc, kDirDeferred);
     for (int e = warp; e < nlc; e += kDirBulkWarps) {
         const int chunk = tab_chunk[e], cnt = tab_cnt[e];
         if (cnt == 0) continue;
@@ -725,7 +786,7 @@ cudaError_t prepare_direct(int smem_optin) {
 
 size_t stream_smem(int ns, int stage) {
     return static_cast<size_t>(ns) * stage + 2 * ns * sizeof(uint64_t) + ns * kDirBulkWarps * 4 * sizeof(float2) +
-           ns * sizeof(int) + 2 * kDirDeferred * sizeof(int);
+           ns * sizeof(int) + 2 * kDirDeferred * sizeof(int) + ns * 4 * sizeof(int);
 }
 
 cudaError_t direct_stream_per_sm(int smem, int* per_sm) {

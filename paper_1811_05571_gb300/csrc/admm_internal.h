@@ -276,11 +276,14 @@ struct DirectArgs {
     int fac_ns;               // its ring stages
     int fac_stage;            // its stage bytes (four factor rows of the widest block)
     long long timeout_ns;     // bound of every wait of the streamed factor pass
+    int fitems;               // work items of the streamed factor pass (update chunks of all blocks)
+    const int* I_off;         // P + 1: first item of block p
     const int* F_off;         // P + 1: first factor row of block p in the concatenation
     const int* R_off;         // P + 1: first H row of block p in the concatenation
     unsigned* cnt_cols;       // P x ccn
     unsigned* cnt_upd;        // nchunks
-    unsigned* cnt_glob;       // [0] update chunks finished, [1] row-pass CTAs finished
+    unsigned* cnt_glob;       // [0] update chunks finished, [1] row-pass CTAs finished,
+                              // [2] next streamed factor item, [3] CTAs out of items
     const int* chunk_off;     // N + 1: first update chunk of each column block
     int nchunks;
     double* res_chunk;        // nchunks x 5
