@@ -654,11 +654,12 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
     }
     d.ccn = (pairs + admm::kDirColPairs - 1) / admm::kDirColPairs;
     d.ctas = 2 * h->num_sms;   // factor and row passes: one wave of two CTAs per SM
-    // factor pass streamed through shared memory when the rows are short
-    // enough for a stage of four: a ring of up to eight stages, as many CTAs
-    // per SM (up to four) as the SM's shared memory holds
+    // factor pass streamed through shared memory for blocks of 1024 to 2048
+    // columns (a stage of four rows fits three times): a ring of up to eight
+    // stages, as many CTAs per SM (up to four) as its registers and shared
+    // memory hold
     d.fac_stream = 0;
-    if (njmax <= admm::kDirBulkMaxCols) {
+    if (njmax >= admm::kDirBulkMinCols && njmax <= admm::kDirBulkMaxCols) {
         const int stage = round_up(static_cast<int64_t>(4) * round_up(njmax, 4) * 8, 128);
         int ns = 8;
         while (ns >= 2 && admm::stream_smem(ns, stage) > static_cast<size_t>(h->smem_optin)) --ns;

@@ -244,7 +244,9 @@ constexpr int kDirChunk = 16;        // entries of u_b per update chunk
 constexpr int kDirRowThreads = 256;  // row pass: eight warps, up to eight rows at a time each
 constexpr int kDirBulkWarps = 8;     // streamed factor pass: consumer warps (an eighth of the columns each)
 constexpr int kDirDeferred = 32;     // update chunks a streamed factor CTA counts in shared memory
-constexpr int kDirBulkMaxCols = 2048;  // widest block the streamed factor pass takes (16 KB rows)
+constexpr int kDirBulkMinCols = 1024;  // blocks the streamed factor pass takes: 1024 to 2048 columns
+constexpr int kDirBulkMaxCols = 2048;  // (8 to 16 KB rows; narrower factors are latency-bound and
+                                       // measured faster with the plain-load pass)
 constexpr int kDirMaxCols = 12288;   // widest block of the direct branch (u_b staged in shared memory)
 
 struct DirectArgs {

@@ -41,7 +41,9 @@ def direct_run(p, M, N, iters, rho=None, form="direct", lam=None):
     (300, 300, 1, 1, 100),      # square lasso (m_b = n_b)
     (2000, 70, 1, 1, 100),      # tall lasso, a single partial factor chunk
     (4100, 1030, 5, 3, 60),     # several column tiles, factor chunks and row tiles, ragged tails
-    (5000, 2100, 2, 1, 40),     # blocks wider than 2048 columns: the factor pass without the ring
+    (5000, 2100, 2, 1, 40),     # blocks wider than 2048 columns: the plain-load factor pass
+    (3000, 1500, 2, 1, 40),     # 1500-column blocks: the streamed factor pass, several items per CTA
+    (4000, 2400, 2, 2, 30),     # the streamed factor pass with two column blocks (q from the column pass)
 ])
 def test_direct_form_matches_the_oracle(m, n, M, N, iters):
     rows = A.balanced_blocks(m, M)
