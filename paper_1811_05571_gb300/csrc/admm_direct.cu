@@ -485,10 +485,13 @@ __global__ void __launch_bounds__((kDirBulkWarps + 1) * 32, 1) dir_factor_stream
                 m[2] = g;
                 m[3] = nitem;
                 mbar_arrive_expect_tx(&full[slot], rbytes * g);
-                const float2* src = a.L + a.L_off[p] + static_cast<size_t>(row) * pitch;
-                for (int q = 0; q < g; ++q)   // one copy per factor row
-                    bulk_load(ring + static_cast<size_t>(slot) * a.fac_stage + static_cast<size_t>(q) * rbytes,
-                              src + static_cast<size_t>(q) * pitch, rbytes, &full[slot]);
+                // the stage's rows are contiguous: copies of at most 4 KB each
+                const unsigned char* src = reinterpret_cast<const unsigned char*>(
+                    a.L + a.L_off[p] + static_cast<size_t>(row) * pitch);
+                unsigned char* dst = ring + static_cast<size_t>(slot) * a.fac_stage;
+                const uint32_t total = rbytes * g;
+                for (uint32_t off = 0; off < total; off += 4096u)
+                    bulk_load(dst + off, src + off, min(4096u, total - off), &full[slot]);
                 ++issued;
                 if (++slot == NS) {
                     slot = 0;
