@@ -114,11 +114,14 @@ typedef struct admm_info {
     int32_t row_blocks, col_blocks;
     double lambda, rho, kappa;  /* kappa = lambda / (row_blocks * rho), the shrinkage threshold */
     int64_t iterations;       /* iterations completed since setup / reset */
-    int32_t ctas;             /* CTAs of the persistent iteration kernel (one per SM at most) */
-    int32_t rows_per_stage;   /* rows of H per pipeline stage */
-    int32_t stages;           /* depth of the TMA pipeline */
-    int32_t slab_cols;        /* widest column slab owned by one CTA */
-    int32_t smem_bytes;       /* dynamic shared memory of the iteration kernel */
+    int32_t ctas;             /* CTAs of the persistent iteration kernel (one per SM at most);
+                                 direct form: CTAs of the factor pass */
+    int32_t rows_per_stage;   /* rows of H per pipeline stage; direct form: factor rows per
+                                 stage of the streamed factor pass (0: plain loads) */
+    int32_t stages;           /* depth of the TMA pipeline (direct form: of the factor ring) */
+    int32_t slab_cols;        /* widest column slab owned by one CTA (0 in the direct form) */
+    int32_t smem_bytes;       /* dynamic shared memory of the iteration kernel (direct form:
+                                 of the streamed factor pass, 0 with plain loads) */
     int32_t num_sms;
     int64_t h_bytes;          /* bytes of H streamed by one pass (m * n * 8) */
     int64_t factor_bytes;     /* bytes of all cached factors (complex64) */

@@ -1552,11 +1552,13 @@ int admm_get_info(const admm_t* h, admm_info_t* info) {
     info->factor_form = h->form;
     info->reserved = 0;
     if (h->form == ADMM_FORM_DIRECT) {
-        info->ctas = h->dir.ctas;
-        info->rows_per_stage = 0;
-        info->stages = 0;
+        // the factor pass: streamed (a ring of stages of four factor rows) or plain loads
+        const DirectState& d = h->dir;
+        info->ctas = d.fac_stream ? d.fac_ctas : d.ctas;
+        info->rows_per_stage = d.fac_stream ? 4 : 0;
+        info->stages = d.fac_stream ? d.fac_ns : 0;
         info->slab_cols = 0;
-        info->smem_bytes = h->dir.njmax * static_cast<int32_t>(sizeof(float2));
+        info->smem_bytes = d.fac_stream ? static_cast<int32_t>(admm::stream_smem(d.fac_ns, d.fac_stage)) : 0;
     }
     return ADMM_OK;
 }

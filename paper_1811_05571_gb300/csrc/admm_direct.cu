@@ -14,7 +14,9 @@
 // kernel the step that needs every CTA's result (the sum of the column-pass
 // partials, the consensus update of a column chunk, the residual record) is
 // done by whichever CTA increments the step's counter last; that CTA also
-// resets the counter.  No CTA waits for another.
+// resets the counter.  No CTA waits for another; the only waits are those
+// between the producer lane and the consumer warps of one CTA of the streamed
+// factor pass (mbarriers, each bounded by the handle's timeout).
 #include "admm_internal.h"
 #include "ptx.cuh"
 
