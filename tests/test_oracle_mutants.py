@@ -34,29 +34,32 @@ MUTANTS = [
     # (id, old, new, pin to run, pin kwargs)
     ("consensus_kappa_drops_M", "kappa = lam / (M * rho)\n    hist, a, stopped",
      "kappa = lam / rho\n    hist, a, stopped",
-     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=0)),
+     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=0, mn=(20, 48))),
     ("consensus_dual_sign", "s = s + u - v_new\n        rp2 = sum(_sq(u[i]",
      "s = s - u + v_new\n        rp2 = sum(_sq(u[i]",
-     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=1)),
+     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=1, mn=(20, 48))),
     ("lemma_transpose_without_conjugate", "adjoint(self.H, t)", "(self.H.T @ t)",
      pins.test_block_solver_matches_dense_solve, dict(rows=8, cols=64, rho=1.0)),
     ("lemma_rho_power", "/ (self.rho * self.rho)", "/ self.rho",
      pins.test_block_solver_matches_dense_solve, dict(rows=30, cols=200, rho=0.05)),
     ("direct_branch_missing_conjugate", "big = self.H.conj().T @ self.H", "big = self.H.T @ self.H",
      pins.test_block_solver_matches_dense_solve, dict(rows=40, cols=16, rho=0.5)),
+    ("direct_branch_drops_rho", "big = self.H.conj().T @ self.H + self.rho * np.eye(cols",
+     "big = self.H.conj().T @ self.H + np.eye(cols",
+     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=1, mn=(60, 12))),
     ("sectioning_wrong_exclusion", "if q != j:\n                    gj = gj - ghat[q]",
      "if q == j:\n                    gj = gj - ghat[q]",
-     pins.test_one_iteration_matches_least_squares_step, dict(M=1, N=3, k=1)),
+     pins.test_one_iteration_matches_least_squares_step, dict(M=1, N=3, k=1, mn=(20, 48))),
     ("sectioning_gauss_seidel_order", "gj = gj - ghat[q]",
      "gj = gj - solvers[q].H @ (u_new[q] if q < j else u[q])",
-     pins.test_one_iteration_matches_least_squares_step, dict(M=1, N=3, k=1)),
+     pins.test_one_iteration_matches_least_squares_step, dict(M=1, N=3, k=1, mn=(20, 48))),
     ("cs_wrong_replica_index", "gij = gij - ghat[i][q]", "gij = gij - ghat[0][q]",
-     pins.test_one_iteration_matches_least_squares_step, dict(M=3, N=2, k=1)),
+     pins.test_one_iteration_matches_least_squares_step, dict(M=3, N=2, k=1, mn=(20, 48))),
     ("consensus_rd_drops_M", "rd2 = rho * rho * M * _sq(v_new - v)", "rd2 = rho * rho * _sq(v_new - v)",
-     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=1)),
+     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=1, mn=(20, 48))),
     ("consensus_sum_not_mean", "a = u.mean(axis=0) + s.mean(axis=0)",
      "a = u.sum(axis=0) + s.mean(axis=0)",
-     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=1)),
+     pins.test_one_iteration_matches_least_squares_step, dict(M=2, N=1, k=1, mn=(20, 48))),
     ("threshold_tie_kept", "keep = mag > kappa", "keep = mag >= kappa",
      pins.test_soft_threshold_golden_values, dict()),
     ("threshold_real_sign", "out[keep] = a[keep] - kappa * (a[keep] / mag[keep])",
