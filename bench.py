@@ -103,9 +103,28 @@ def load_traffic() -> dict | None:
 
 
 def make_problem(rank: int):
+    """Rank r's replica: the shared CRA-shaped matrix with its own scene (seed 2 + r)."""
     import synth
     H = synth.cra_matrix(seed=1)
     return synth.cra_problem(H=H, scene_seed=2 + rank)
+
+
+def max_over_ranks(seconds: float, world: int, device=None) -> float:
+    """The largest of the ranks' timings (the whole job lasts as long as the
+    slowest rank).  The tensor lives on `device` for NCCL, on the host for gloo."""
+    if world <= 1:
+        return seconds
+    import torch
+    import torch.distributed as dist
+    on = device if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([seconds], device=on, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, splits: int, steps: int, seconds: float) -> float:
+    """Whole-job throughput: iterations of every split on every rank per second."""
+    return world * splits * steps / seconds
 
 
 # ---------------------------------------------------------------------------
@@ -729,10 +748,7 @@ def run_ours(args) -> None:
         st = s.status()
         if st != 0:
             raise RuntimeError(f"device status {st} after the timed region")
-    if world > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
+    total_s = max_over_ranks(total_s, world, dev)
 
     # end to end through the public API with host buffers: per step and split,
     # set_g from pinned host memory, one iteration, the image back to pinned
@@ -761,10 +777,7 @@ def run_ours(args) -> None:
     for s in solvers:
         s.stream = stream
     e2e_s = e0.elapsed_time(e1) / 1e3
-    if world > 1:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(e2e_s, world, dev)
 
     # the same three handles streaming the FP16 copy of H (built here, untimed)
     fp16_split_s = []
@@ -861,7 +874,7 @@ def run_ours(args) -> None:
         for name in per_split:
             per_split[name]["dram_bytes_per_launch"] = traffic.get(name)
             per_split[name]["fp16_h"]["dram_bytes_per_launch"] = traffic.get(name + "_fp16")
-    value = world * len(SPLITS) * K / total_s
+    value = job_value(world, len(SPLITS), K, total_s)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_s / K * 1e3, "higher_is_better": True,
@@ -880,7 +893,7 @@ def run_ours(args) -> None:
                      "per": "iteration (achieved and traffic per iteration; one launch runs K iterations)",
                      "dram_achieved": dram_achieved,
                      "dram_frac": dram_achieved / peaks["hbm_gbs"] if dram_achieved else None},
-        "e2e": {"value": world * len(SPLITS) * K / e2e_s, "unit": UNIT,
+        "e2e": {"value": job_value(world, len(SPLITS), K, e2e_s), "unit": UNIT,
                 "h2d_bytes_per_step": len(SPLITS) * M_ROWS * 8,
                 "d2h_bytes_per_step": len(SPLITS) * N_COLS * 8},
         "gpu_launches": len(SPLITS),
