@@ -57,6 +57,18 @@ def test_direct_form_matches_the_oracle(m, n, M, N, iters):
     compare_all(s, ref, M, N)
 
 
+def test_streamed_factor_pass_with_more_items_than_its_chunk_table():
+    """80 row blocks of 1024 x 1024: 5120 factor items over the CTAs, more than
+    the 32 a CTA counts in shared memory, so the later items of a CTA count
+    their rows in the global chunk counters at once."""
+    p = synth.gaussian_problem(80 * 1024, 1024, 16, seed=44)
+    ref = oracle_run(p, 80, 1, 3)
+    s = direct_run(p, 80, 1, 3)
+    info = s.info()
+    assert info["rows_per_stage"] == 4 and 5120 > 32 * info["ctas"]
+    compare_all(s, ref, 80, 1)
+
+
 def test_direct_form_on_wide_blocks_is_the_same_algorithm():
     """The direct form is valid for any block shape (it is only costlier when
     m_b < n_b): on wide blocks it matches the oracle's lemma branch."""
