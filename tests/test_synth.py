@@ -65,3 +65,16 @@ def test_plate_scene_is_axis_aligned_plates():
     nz = np.count_nonzero(u)
     assert 100 <= nz <= 300
     assert np.array_equal(synth.plate_scene(seed=2), synth.plate_scene(seed=2))
+
+
+def test_tall_workload_has_only_tall_blocks():
+    """The overdetermined workload of the direct-form measurement: every block
+    of every one of its splits has at least as many rows as columns, so the
+    paper's rule picks the direct branch throughout."""
+    from oracle import admm_fp64 as A
+    c = synth.TALL
+    assert c["m"] > c["n"]
+    for M, N in c["splits"]:
+        for r0, r1 in A.balanced_blocks(c["m"], M):
+            for c0, c1 in A.balanced_blocks(c["n"], N):
+                assert not A.lemma_applies(r1 - r0, c1 - c0), (M, N)
