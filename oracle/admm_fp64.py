@@ -35,7 +35,7 @@ The estimated data of the column splits is formed from explicit products
 H_q u_q of the *previous* iterate (Eq. g_columns, g_rows_columns), never from
 an algebraic shortcut.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
 * initial state v = s = u = 0 (so every estimated datum starts at 0);
 * complex sign(a) = a/|a| in the soft-threshold; |a| == kappa maps to 0;
 * blocks are contiguous and balanced, the first (total mod parts) blocks one

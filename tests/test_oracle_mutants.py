@@ -68,6 +68,22 @@ MUTANTS = [
     ("cs_kappa_drops_M", "kappa = lam / (M * rho)\n    hist, a_parts, stopped",
      "kappa = lam / rho\n    hist, a_parts, stopped",
      pins.test_every_split_converges_to_the_lasso_minimiser, dict(M=3, N=2)),
+    # the stopping rule (Boyd et al. Section 3.3.1)
+    ("stop_dual_tolerance_drops_rho",
+     "eps_dual = np.sqrt(p) * eps_abs + eps_rel * rho * np.sqrt(rec[4])",
+     "eps_dual = np.sqrt(p) * eps_abs + eps_rel * np.sqrt(rec[4])",
+     pins.test_stop_rule_hand_worked_records, dict()),
+    ("stop_primal_tolerance_ignores_u",
+     "eps_rel * max(np.sqrt(rec[2]), np.sqrt(rec[3]))", "eps_rel * np.sqrt(rec[3])",
+     pins.test_stop_rule_hand_worked_records, dict()),
+    ("consensus_stop_length_is_n", "stop_test(np.array(hist[-1]), M * n, rho, *eps)",
+     "stop_test(np.array(hist[-1]), n, rho, *eps)",
+     pins.test_stopping_iteration_follows_boyd, dict(M=4, N=1)),
+    ("consensus_v_norm_not_stacked", "M * _sq(v_new),\n", "_sq(v_new),\n",
+     pins.test_recorded_norms_follow_the_stacked_definitions, dict(M=3, N=1, k=4)),
+    ("cs_dual_record_drops_M", "rd2 = rho * rho * M * sum(_sq(v_new[j] - v[j]) for j in range(N))",
+     "rd2 = rho * rho * sum(_sq(v_new[j] - v[j]) for j in range(N))",
+     pins.test_recorded_norms_follow_the_stacked_definitions, dict(M=2, N=2, k=4)),
 ]
 
 

@@ -425,15 +425,117 @@ def test_efficiency_inequalities_agree_with_table1():
 # stopping rule
 # ----------------------------------------------------------------------------
 
-def test_stop_rule_and_residual_decay():
-    p = small_problem()
-    r = oracle.run_split(p.H, p.g, 2, 1, p.lam, p.rho, 5000, eps=(1e-8, 1e-6))
-    assert r.stopped_at is not None and r.stopped_at == r.iters
-    rec = r.hist[-1]
-    nstack = 2 * p.n
-    assert np.sqrt(rec[0]) <= np.sqrt(nstack) * 1e-8 + 1e-6 * max(np.sqrt(rec[2]), np.sqrt(rec[3]))
-    prev = r.hist[-2]
-    assert not A.stop_test(prev, nstack, p.rho, 1e-8, 1e-6)
+def test_stop_rule_hand_worked_records():
+    """Boyd et al. Section 3.3.1 (the residuals the paper cites): stop when
+    ||r_p|| <= sqrt(p) eps_abs + eps_rel max(||Ax||, ||Bz||) and
+    ||r_d|| <= sqrt(p) eps_abs + eps_rel ||A^T y||, with y = rho s the unscaled
+    dual.  Records are (||r_p||^2, ||r_d||^2, ||u||^2, ||v||^2, ||s||^2); every
+    number below is a power of two or a short sum of them, so the boundary
+    cases are exact.  With p = 4, eps_abs = 1/8, eps_rel = 1/2, rho = 2:
+    sqrt(p) eps_abs = 1/4; ||u|| = 2, ||v|| = 4 gives eps_pri = 1/4 + 2 = 9/4;
+    ||s|| = 1 gives eps_dual = 1/4 + (1/2)(2)(1) = 5/4."""
+    p, ea, er, rho = 4, 0.125, 0.5, 2.0
+    # both norms exactly on their tolerance: stop (the test is "<=")
+    assert A.stop_test(np.array([2.25 ** 2, 1.25 ** 2, 4.0, 16.0, 1.0]), p, rho, ea, er) is True
+    # only the primal test fails: ||r_p|| = 5/2 > 9/4, ||r_d|| = 1 <= 5/4
+    assert A.stop_test(np.array([2.5 ** 2, 1.0, 4.0, 16.0, 1.0]), p, rho, ea, er) is False
+    # only the dual test fails: ||r_p|| = 2 <= 9/4, ||r_d|| = 3/2 > 5/4
+    assert A.stop_test(np.array([4.0, 1.5 ** 2, 4.0, 16.0, 1.0]), p, rho, ea, er) is False
+    # the larger of ||u|| and ||v|| sets eps_pri: ||u|| = 6 gives 1/4 + 3 = 13/4
+    assert A.stop_test(np.array([3.25 ** 2, 1.0, 36.0, 16.0, 1.0]), p, rho, ea, er) is True
+    assert A.stop_test(np.array([3.5 ** 2, 1.0, 36.0, 16.0, 1.0]), p, rho, ea, er) is False
+    # rho scales the dual tolerance: rho = 4 gives eps_dual = 1/4 + 2 = 9/4
+    assert A.stop_test(np.array([1.0, 2.25 ** 2, 4.0, 16.0, 1.0]), p, 4.0, ea, er) is True
+    assert A.stop_test(np.array([1.0, 2.25 ** 2, 4.0, 16.0, 1.0]), p, rho, ea, er) is False
+    # sqrt(p) scales the absolute part of both: p = 64 gives 1 + 2 = 3 and 1 + 1 = 2
+    assert A.stop_test(np.array([9.0, 4.0, 4.0, 16.0, 1.0]), 64, rho, ea, er) is True
+    assert A.stop_test(np.array([9.0, 4.0, 4.0, 16.0, 1.0]), 16, rho, ea, er) is False
+
+
+def test_threshold_margin_hand_values():
+    """min_k | |a_k| - kappa | / kappa: |3+4j| = 5, |1| = 1, |0| = 0 against kappa = 2
+    give 3/2, 1/2 and 1, so 1/2; a tie gives 0; kappa = 0 (no shrinkage) gives inf."""
+    a = np.array([3 + 4j, 1.0, 0.0])
+    assert A.threshold_margin(a, 2.0) == 0.5
+    assert A.threshold_margin(np.array([2j, 7.0]), 2.0) == 0.0
+    assert A.threshold_margin(a, 0.0) == float("inf")
+
+
+def _stacked_state(res, M, n):
+    """(u, v, s) of an oracle result as (M, n) replicas, the image and the duals."""
+    return res.u.reshape(M, n), res.v.copy(), res.s.reshape(M, n)
+
+
+@pytest.mark.parametrize("M,N", [(1, 1), (3, 1), (1, 3), (2, 2)])
+@pytest.mark.parametrize("k", [0, 4])
+def test_recorded_norms_follow_the_stacked_definitions(M, N, k):
+    """The norms the stopping rule reads, rebuilt from the state alone.
+
+    Boyd's stacked form of the split: x = (u^1, ..., u^M) (one replica per
+    row block; the column segments of a replica side by side), z = v,
+    constraint x - [v; ...; v] = 0, so ||Ax|| = ||x||, ||Bz|| = ||[v; ...; v]||
+    and ||A^T y|| = rho ||s|| over the stacked duals.  The primal residual is
+    x - [v; ...; v].  The dual residual is taken from its definition as the
+    defect of dual feasibility after the step: block b's gradient of
+    1/2||H_b u_b - gt_b||^2 (gt_b the data the block fits, with the previous
+    iterate's estimated data of the other column blocks) plus its unscaled
+    dual rho s_b; stacked over all blocks its squared norm is ||r_d||^2."""
+    p = small_problem(m=20, n=48, nnz=3, rho=3.0 * N)
+    H, g, n = p.H, p.g, p.n
+    before = oracle.run_split(H, g, M, N, p.lam, p.rho, k)
+    after = oracle.run_split(H, g, M, N, p.lam, p.rho, k + 1)
+    rows = A.balanced_blocks(p.m, M)
+    cols = A.balanced_blocks(n, N)
+    if k == 0:
+        u0 = np.zeros((M, n), complex)
+    else:
+        u0 = before.u.reshape(M, n)
+    u1, v1, s1 = _stacked_state(after, M, n)
+    x = u1.reshape(-1)
+    bz = np.tile(v1, M)
+    defect = []
+    for i, (r0, r1) in enumerate(rows):
+        for j, (c0, c1) in enumerate(cols):
+            gt = g[r0:r1].copy()
+            for q, (d0, d1) in enumerate(cols):
+                if q != j:
+                    gt -= H[r0:r1, d0:d1] @ u0[i, d0:d1]
+            Hb = H[r0:r1, c0:c1]
+            defect.append(Hb.conj().T @ (Hb @ u1[i, c0:c1] - gt) + p.rho * s1[i, c0:c1])
+    defect = np.concatenate(defect)
+    rec = after.hist[-1]
+    want = [np.linalg.norm(x - bz) ** 2, np.linalg.norm(defect) ** 2, np.linalg.norm(x) ** 2,
+            np.linalg.norm(bz) ** 2, np.linalg.norm(s1.reshape(-1)) ** 2]
+    for got, ref in zip(rec, want):
+        assert abs(got - ref) <= 1e-9 * max(1.0, ref), (rec, want)
+
+
+@pytest.mark.parametrize("M,N", [(1, 1), (4, 1), (1, 3), (2, 2)])
+def test_stopping_iteration_follows_boyd(M, N):
+    """The oracle stops at the first iteration whose state meets Boyd's test
+    with p = the length of the stacked constraint (M n entries), the norms
+    taken from the state as in the previous test.  The tolerances are chosen
+    so that p = n instead would stop at another iteration."""
+    p = small_problem(m=20, n=48, nnz=3, rho=3.0 * N)
+    H, g, n = p.H, p.g, p.n
+    eps_abs, eps_rel = 2e-4, 0.0
+    K = 120
+    stop = oracle.run_split(H, g, M, N, p.lam, p.rho, K, eps=(eps_abs, eps_rel))
+    full = oracle.run_split(H, g, M, N, p.lam, p.rho, K)
+    first = {}
+    for plen in (M * n, n):
+        for k in range(K):
+            rp, rd = np.sqrt(full.hist[k, 0]), np.sqrt(full.hist[k, 1])
+            if rp <= np.sqrt(plen) * eps_abs and rd <= np.sqrt(plen) * eps_abs:
+                first[plen] = k + 1
+                break
+    assert M * n in first, "the tolerance is never met within the run"
+    assert stop.stopped_at == first[M * n] == stop.iters
+    if M > 1:
+        assert first.get(n) != first[M * n]
+    # and the recorded norms of the stopping iteration are those of the state
+    u1, v1, s1 = _stacked_state(stop, M, n)
+    assert abs(stop.hist[-1, 0] - np.linalg.norm(u1.reshape(-1) - np.tile(v1, M)) ** 2) <= 1e-12
 
 
 # ----------------------------------------------------------------------------
