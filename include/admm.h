@@ -354,11 +354,9 @@ void admm_destroy(admm_t* h);
 
 /* Allocation-free solve of a small problem.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
- * a framework whose own pool allocator owns all of the GPU's memory, a
- * real-time loop that must not pay for (or risk failing) an allocation, or
- * code recording work into a CUDA graph, where an allocation would be an
- * illegal or unwanted side effect.  admm_setup allocates, so such callers
- * use this call instead.
+ * a framework whose own pool allocator owns all of the GPU's memory, or a
+ * real-time loop that must not pay for (or risk failing) an allocation.
+ * admm_setup allocates, so such callers use this call instead.
  * It computes what admm_setup + admm_iterate(iters) + admm_get_v compute
  * from the zero initial state (same kernels, same results), but takes all of
  * its working memory -- factors, FP64 factor workspace, iteration state and
@@ -366,18 +364,24 @@ void admm_destroy(admm_t* h);
  * GPU that loads the library holds until the process exits.  It calls no
  * cudaMalloc, cudaFree or other allocating routine.
  *   H      device pointer: m x n complex64, row-major, 16-byte aligned, with n
- *          a positive multiple of 32 (used in place, not copied);
+ *          a multiple of 32 in [32, 2^24] and 1 <= m <= 2^20 (used in place,
+ *          not copied);
  *   g      device pointer: m complex64;
  *   v_out  device pointer: n complex64, receives the image v.
- * Every block must have fewer rows than columns.  A problem whose working
+ * H, g and v_out must be memory of the current device (cudaMalloc'd on it,
+ * or managed); host memory, pinned or not, returns ADMM_EINVAL before any
+ * kernel runs.  Every block shape is accepted: like admm_setup, blocks with
+ * m_b >= n_b use the m_b x m_b factor.  NaN or Inf in H or g returns
+ * ADMM_ENONFINITE before any factor is formed.  A problem whose working
  * memory exceeds the 8 MiB (for example, 256 x 4096 with 4 row blocks needs
- * about 1.1 MiB) returns ADMM_EINVAL, with the reason in
- * admm_last_error(NULL), as do other invalid arguments.
+ * about 1.1 MiB) returns ADMM_EINVAL, as do other invalid arguments; the
+ * reason is in admm_last_error(NULL).
  * The first call on a device looks up that device's address of the array
  * (cudaGetSymbolAddress) and keeps it; make that first call before any stream
  * capture.  Every call reuses the same array and clears what must start at
  * zero itself, so calls that overlap on the GPU (other streams, other host
- * threads) race and must be serialised by the caller.  Synchronises `stream`. */
+ * threads) race and must be serialised by the caller.  Synchronises `stream`
+ * (after the input check and at the end). */
 int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
                              int32_t row_blocks, int32_t col_blocks, double lambda, double rho,
                              int32_t iters, void* v_out, void* stream);

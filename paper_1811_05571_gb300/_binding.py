@@ -328,7 +328,13 @@ def admm_destroy(h: int) -> None:
 
 def admm_solve_small_noalloc(H, g, m: int, n: int, row_blocks: int, col_blocks: int, lam: float,
                              rho: float, iters: int, v_out, stream=None) -> None:
-    """Allocation-free solve of a small problem into the caller's v_out (see include/admm.h)."""
+    """Allocation-free solve of a small problem into the caller's v_out (see include/admm.h).
+
+    H, g and v_out must be CUDA tensors: the call uses them in place."""
+    import torch
+    for name, t in (("H", H), ("g", g), ("v_out", v_out)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda):
+            raise TypeError(f"admm_solve_small_noalloc: {name} must be a CUDA tensor")
     _check(load().admm_solve_small_noalloc(_ptr(H), _ptr(g), m, n, row_blocks, col_blocks, lam, rho,
                                            iters, _ptr(v_out), _stream(stream)))
 

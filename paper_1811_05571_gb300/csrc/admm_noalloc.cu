@@ -3,12 +3,11 @@
 // memory carved out of one file-scope device array instead of cudaMalloc.
 //
 // Who needs this: code that may not allocate device memory itself -- a
-// framework whose own pool allocator owns all of the GPU's memory, a
-// real-time loop that must not pay (or risk failing) an allocation, or a
-// caller recording work into a CUDA graph, where a cudaMalloc would be an
-// illegal or unwanted side effect.  They pass their own input and output
-// buffers; the library's scratch is reserved once per device when the
-// library loads.
+// framework whose own pool allocator owns all of the GPU's memory, or a
+// real-time loop that must not pay (or risk failing) an allocation.  They
+// pass their own input and output buffers; the library's scratch is reserved
+// once per device when the library loads.
+#include <cmath>
 #include <cstring>
 #include <mutex>
 #include <vector>
@@ -60,6 +59,32 @@ int noalloc_fail(int code, const char* msg) {
     return code;
 }
 
+// H, g and v_out are used in place by the kernels, so each must be device
+// memory this device can address (cudaMalloc'd on it, or managed memory).
+bool on_this_device(const void* p, int dev) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();   // clear the error an unregistered host pointer may leave
+        return false;
+    }
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
+}
+
+// the driver's tensor-map encoder, looked up once for every thread
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn_ptr = nullptr;
+    std::call_once(once, [] {
+        cudaDriverEntryPointQueryResult q;
+        void* fn = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess && fn)
+            fn_ptr = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    });
+    return fn_ptr;
+}
+
 }  // namespace
 
 extern "C" {
@@ -68,15 +93,22 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
                              int32_t col_blocks, double lambda, double rho, int32_t iters,
                              void* v_out, void* stream) {
     if (!H || !g || !v_out) return noalloc_fail(ADMM_EINVAL, "H, g and v_out must not be NULL");
-    if (m < 1 || n < 1 || n % 32 != 0 || m > (1 << 20) || n > (1 << 24))
-        return noalloc_fail(ADMM_EINVAL, "need m >= 1 and n a positive multiple of 32");
+    if (m < 1 || m > (1 << 20)) return noalloc_fail(ADMM_EINVAL, "need 1 <= m <= 2^20");
+    if (n < 32 || n > (1 << 24) || n % 32 != 0)
+        return noalloc_fail(ADMM_EINVAL, "need n a multiple of 32 in [32, 2^24]");
     if (reinterpret_cast<uintptr_t>(H) % 16 != 0)
         return noalloc_fail(ADMM_EINVAL, "H must be 16-byte aligned");
     if (row_blocks < 1 || row_blocks > m || col_blocks < 1 || col_blocks > n ||
         static_cast<int64_t>(row_blocks) * col_blocks > admm::kMaxBlocks)
         return noalloc_fail(ADMM_EINVAL, "bad row_blocks / col_blocks");
-    if (!(lambda >= 0.0) || !(rho > 0.0) || iters < 0)
-        return noalloc_fail(ADMM_EINVAL, "need lambda >= 0, rho > 0, iters >= 0");
+    if (!(lambda >= 0.0) || !std::isfinite(lambda) || !(rho > 0.0) || !std::isfinite(rho) || iters < 0)
+        return noalloc_fail(ADMM_EINVAL, "need finite lambda >= 0, finite rho > 0, iters >= 0");
+    {
+        int cur = 0;
+        if (cudaGetDevice(&cur) != cudaSuccess) return noalloc_fail(ADMM_ECUDA, "cudaGetDevice failed");
+        if (!on_this_device(H, cur) || !on_this_device(g, cur) || !on_this_device(v_out, cur))
+            return noalloc_fail(ADMM_EINVAL, "H, g and v_out must be device memory of the current device");
+    }
     std::vector<int> ro, co;
     admm::balanced_offsets(m, row_blocks, ro);
     admm::balanced_offsets(n, col_blocks, co);
@@ -168,6 +200,16 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
     NA_CK(cudaMemsetAsync(at(x_v), 0, x_part - x_v, st));          // v, s, u, ghat, gt, r, w
     NA_CK(cudaMemsetAsync(at(x_hist), 0, cv.used - x_hist, st));   // history, counters, flags
 
+    // non-finite inputs: checked before any factor or iteration kernel runs
+    {
+        int flag = 0;
+        NA_CK(admm::launch_finite_check(static_cast<const float2*>(H), m * n, status, st));
+        NA_CK(admm::launch_finite_check(static_cast<const float2*>(g), m, status, st));
+        NA_CK(cudaMemcpyAsync(&flag, status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        NA_CK(cudaStreamSynchronize(st));
+        if (flag) return noalloc_fail(ADMM_ENONFINITE, "H or g holds NaN or Inf");
+    }
+
     admm::FactorArgs f;
     f.m = static_cast<int>(m);
     f.ld = static_cast<int>(ld);
@@ -187,15 +229,8 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
     NA_CK(admm::launch_gram(f, st));
     NA_CK(admm::launch_cholesky_inverse(f, st));
 
-    static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
-    if (!encode) {
-        cudaDriverEntryPointQueryResult q;
-        void* fn = nullptr;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess || q != cudaDriverEntryPointSuccess || !fn)
-            return noalloc_fail(ADMM_ECUDA, "cuTensorMapEncodeTiled is not available");
-        encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    }
+    PFN_cuTensorMapEncodeTiled_v12000 encode = tensor_map_encoder();
+    if (!encode) return noalloc_fail(ADMM_ECUDA, "cuTensorMapEncodeTiled is not available");
     CUtensorMap tmap;
     cuuint64_t dims[2] = {static_cast<cuuint64_t>(ld), static_cast<cuuint64_t>(m)};
     cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * sizeof(float2)};
