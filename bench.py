@@ -1,13 +1,17 @@
 #!/usr/bin/env python3
-"""Throughput of the GB300 norm-1 ADMM on the CRA-shaped imaging workload.
+"""Throughput of the GB300 norm-1 ADMM on the 8192 x 131072 mixed-precision workload.
 
-Workload: H = 1440 x 32768 complex64 (40 frequencies x 36 receivers, 32^3
-voxels), a three-plate scene at 30 dB, lambda = 0.05 max|H^H g|, rho = 8 max_j
-||H_j||^2 (the column-split rule), solved in all three splits of the paper:
-consensus 8x1, sectioning 1x8, consensus-and-sectioning 4x4.  One step = one
-ADMM iteration of each split; the timed region runs each split's K iterations
-as one launch of the persistent iteration kernel (three launches).  H (377 MB
-per split) is larger than L2, so no flush is needed between steps.
+Headline workload: H 8192 x 131072 complex64, i.i.d. CN(0, 1/8192) drawn on the
+host in seeded row chunks (synth.chunked_gaussian_problem, seed 3), 400 planted
+nonzeros, 30 dB, lambda = 0.05 max|H^H g|, rho = 1, consensus over 16 row blocks
+of 512 rows.  One step = one ADMM iteration with the complex64 H; the timed
+region runs the K steps as one launch of the persistent iteration kernel
+(admm_iterate(h, K)).  H (8.6 GB) is far larger than L2, so no flush is needed.
+Beside it: the FP16-H mode, the 280 FP16 + 20 complex64 schedule against 300
+complex64 iterations and the time to 1e-4 relative error of both, each with its
+error against the stored FP64 oracle solution of this exact problem; then the
+CRA-shaped 1440 x 32768 workload in the paper's three splits, the 256 x 4096
+workload, and the batched, differentiable, uneven-problem and direct-form legs.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -37,8 +41,16 @@ METRIC = "ADMM iters/s & HBM GB/s vs roofline; time to 1e-4 rel. err, chosen vs 
 UNIT = "iters/s"
 SPLITS = ((8, 1), (1, 8), (4, 4))
 M_ROWS, N_COLS = 1440, 32768
-WORKLOAD = ("CRA-shaped imaging, H 1440x32768 complex64 (40 freqs x 36 rx, 32^3 voxels), "
-            "one iteration of each split 8x1 / 1x8 / 4x4 per step")
+C3_M, C3_N, C3_NNZ, C3_SEED, C3_BLOCKS = 8192, 131072, 400, 3, 16
+C3_FP16, C3_POLISH = 280, 20
+C3_VSTAR = os.path.join(ROOT, "tests", "golden", "vstar_gaussian_8192x131072_c16.txt")
+WORKLOAD = ("Gaussian 8192x131072 complex64 CN(0,1/8192), 400 nonzeros, 30 dB, consensus 16x1 "
+            "(512-row blocks), lambda 0.05 max|H^H g|, rho 1; one complex64 iteration per step")
+CONFIG = {"workload": WORKLOAD, "m": C3_M, "n": C3_N, "row_blocks": C3_BLOCKS, "col_blocks": 1,
+          "inputs": "host generator synth.chunked_gaussian_problem(8192, 131072, 400, seed 3)",
+          "l2": "inputs larger than L2 (H 8.6 GB vs 129 MB L2), no flush"}
+# the CPU oracle sample: the same recipe at a quarter of the rows
+CPU_M, CPU_NNZ = 2048, 100
 
 
 def parse_args(argv=None):
@@ -47,7 +59,7 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--cpu-iters", type=int, default=12,
+    ap.add_argument("--cpu-iters", type=int, default=30,
                     help="iterations per split in the bounded CPU-oracle sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-direct", action="store_true",
@@ -59,13 +71,11 @@ def parse_args(argv=None):
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched shared-H workload (tensor-core GEMMs)")
     ap.add_argument("--batch", type=int, default=256, help="scenes of the batched workload")
-    ap.add_argument("--no-large", action="store_true",
-                    help="skip the 8192x131072 mixed-precision workload")
+    ap.add_argument("--no-cra", action="store_true",
+                    help="skip the CRA-shaped 1440x32768 workload in the three splits")
+    ap.add_argument("--no-small", action="store_true", help="skip the 256x4096 workload")
     ap.add_argument("--no-time-to-tol", action="store_true",
                     help="skip the time-to-1e-4 comparison of FP16+polish against plain complex64")
-    ap.add_argument("--trace", type=int, default=0,
-                    help="after the timed region, run this many traced iterations per split and "
-                         "report the median time of each phase")
     ap.add_argument("--l2-keep-mb", type=float, default=None,
                     help="MiB of H per pass kept in L2 for the reversed next pass "
                          "(ADMM_OPT_L2_KEEP_BYTES; default: the library's)")
@@ -83,23 +93,31 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback"}
 
 
+TRAFFIC_FILES = ("iterate_kernel_gaussian8192x131072_dram.txt", "iterate_kernel_cra1440x32768_dram.txt")
+
+
 def load_traffic() -> dict | None:
-    """DRAM bytes per launch per split from the committed ncu summary, or None
-    when the iteration kernel's source changed since it was captured."""
+    """DRAM bytes per iteration of the iteration kernel from the committed ncu
+    summaries (keys: workload or split names), each file used only while the
+    kernel's source hash matches the one it was captured with."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "iterate_kernel_cra1440x32768_dram.txt")
     src = os.path.join(ROOT, "paper_1811_05571_gb300", "csrc", "admm_iterate.cu")
-    if not os.path.exists(path):
-        return None
-    want, out = None, {}
-    for line in open(path):
-        parts = line.split()
-        if len(parts) == 2 and parts[0] == "source_sha256":
-            want = parts[1]
-        elif len(parts) == 3 and parts[0] == "traffic_bytes":
-            out[parts[1]] = float(parts[2])
     have = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    return out if want == have and out else None
+    out = {}
+    for name in TRAFFIC_FILES:
+        path = os.path.join(ROOT, "profiles", name)
+        if not os.path.exists(path):
+            continue
+        want, vals = None, {}
+        for line in open(path):
+            parts = line.split()
+            if len(parts) == 2 and parts[0] == "source_sha256":
+                want = parts[1]
+            elif len(parts) == 3 and parts[0] == "traffic_bytes":
+                vals[parts[1]] = float(parts[2])
+        if want == have:
+            out.update(vals)
+    return out or None
 
 
 def make_problem(rank: int):
@@ -185,32 +203,42 @@ class ClockSampler:
 # the oracle on the host cores (CPU baseline and the reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_iteration_seconds(p, iters: dict, warmup: int) -> dict:
-    """Per-split seconds per oracle iteration from two runs of the oracle as it
-    stands: (T(warmup + k) - T(warmup)) / k, so its one-time factorisation and
-    the warm-up iterations cancel.  `iters` maps a split name to k."""
+def quarter_problem():
+    """The CPU-oracle sample: the headline recipe at a quarter of the rows
+    (2048 x 131072, 100 nonzeros), as complex128 for the oracle."""
+    import numpy as np
+    import synth
+    H, g, _, lam = synth.chunked_gaussian_problem(CPU_M, C3_N, CPU_NNZ, C3_SEED)
+    return H.astype(np.complex128), g, lam
+
+
+def oracle_seconds_per_iteration(H, g, lam, k: int, warmup: int) -> float:
+    """Seconds per iteration of the oracle as it stands (consensus, 16 row
+    blocks): one run of warmup + k iterations, timed from the end of the last
+    warm-up iteration to the end of the last one (at least one warm-up
+    iteration, so the one-time factorisation is excluded)."""
     import oracle
-    out = {}
-    for M, N in SPLITS:
-        name = f"{M}x{N}"
-        k = max(int(iters[name]), 1)
-        t0 = time.perf_counter()
-        oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, warmup)
-        t1 = time.perf_counter()
-        oracle.run_split(p.H, p.g, M, N, p.lam, p.rho, warmup + k)
-        t2 = time.perf_counter()
-        out[name] = max((t2 - t1) - (t1 - t0), 1e-9) / k
-    return out
+    k, warmup = max(int(k), 1), max(int(warmup), 1)
+    stamps = []
+    oracle.run_split(H, g, C3_BLOCKS, 1, lam, 1.0, warmup + k,
+                     on_iter=lambda it: stamps.append(time.perf_counter()))
+    return (stamps[warmup + k - 1] - stamps[warmup - 1]) / k
 
 
-def sample_iters(base: int) -> dict:
-    # the consensus oracle iteration is ~10x cheaper than the column splits'
-    return {"8x1": 8 * base, "1x8": base, "4x4": base}
+# per-iteration cost of the oracle is two passes over H: proportional to the rows at fixed n
+CPU_SCALE = C3_M / CPU_M
+
+
+def cpu_sample_text(iters: int, warmup: int, cores: int) -> str:
+    return (f"FP64 oracle (numpy/OpenBLAS, {cores} threads) on the headline recipe at a quarter of the "
+            f"rows (2048x131072, 100 nonzeros, 16 row blocks of 128): {iters} iterations after "
+            f"{max(warmup, 1)} warm-up, factorisation excluded; seconds per iteration x4 for "
+            f"8192 rows (two passes over H per iteration)")
 
 
 def cpu_sample_worker(args) -> None:
-    p = make_problem(0)
-    per = oracle_iteration_seconds(p, sample_iters(args.cpu_iters), 2)
+    H, g, lam = quarter_problem()
+    per = oracle_seconds_per_iteration(H, g, lam, args.cpu_iters, 2)
     print(json.dumps({"per_iter_s": per, "cores": int(os.environ.get("OPENBLAS_NUM_THREADS", "1"))}))
 
 
@@ -227,37 +255,28 @@ def cpu_baseline(iters: int) -> dict:
         return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
                 "sample": f"failed: {res.stderr.strip()[-200:]}"}
     d = json.loads(res.stdout.strip().splitlines()[-1])
-    total = sum(d["per_iter_s"].values())
-    return {"value": len(SPLITS) / total, "unit": UNIT, "cores": d["cores"], "kind": "oracle",
-            "sample": (f"FP64 oracle on the full 1440x32768 CRA workload: {sample_iters(iters)} "
-                       f"iterations per split after 2 warm-up, factorisation excluded "
-                       f"(difference of two runs); numpy/OpenBLAS with {d['cores']} threads"),
-            "per_iter_s": d["per_iter_s"]}
+    return {"value": 1.0 / (d["per_iter_s"] * CPU_SCALE), "unit": UNIT, "cores": d["cores"],
+            "kind": "oracle", "sample": cpu_sample_text(iters, 2, d["cores"]),
+            "quarter_scale_s_per_iter": d["per_iter_s"]}
 
 
 def run_reference(args) -> None:
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    p = make_problem(0)
+    H, g, lam = quarter_problem()
     k = max(args.steps, 1)
-    per = oracle_iteration_seconds(p, {f"{M}x{N}": k for M, N in SPLITS}, args.warmup)
-    step_s = sum(per.values())
-    value = len(SPLITS) / step_s
+    per = oracle_seconds_per_iteration(H, g, lam, k, max(args.warmup, 0)) * CPU_SCALE
+    value = 1.0 / per
     cores = int(os.environ.get("OPENBLAS_NUM_THREADS", os.cpu_count() or 1))
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": step_s * 1e3,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": per * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-        "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS,
-                   "splits": [f"{M}x{N}" for M, N in SPLITS], "parallelism": "host cores"},
+        "data": "synthetic", "config": CONFIG,
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": (f"{args.steps} FP64 oracle iterations of each split after "
-                                    f"{args.warmup} warm-up, factorisation excluded "
-                                    f"(difference of two runs)")},
+                         "sample": cpu_sample_text(k, max(args.warmup, 0), cores)},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
-        "splits": {k: {"iters_per_s": 1.0 / v} for k, v in per.items()},
     }
     print(json.dumps(line))
 
@@ -266,170 +285,75 @@ def run_reference(args) -> None:
 # our arm
 # ---------------------------------------------------------------------------
 
-TT_M, TT_N, TT_NNZ, TT_SEED, TT_BLOCKS = 2048, 16384, 128, 5, 8
-TT_TOL, TT_POLISH, TT_MAX = 1e-4, 20, 600
-TT_VSTAR = os.path.join(ROOT, "tests", "golden", "vstar_gaussian_2048x16384_c8.txt")
+TT_TOL, TT_MAX = 1e-4, 600
 
 
-def load_vstar():
-    """Stored FP64 solution of the time-to-tolerance workload (nonzeros only)."""
+def load_vstar_file(path: str, n: int):
+    """(header, v*) of a stored FP64 oracle solution (nonzeros only)."""
     import numpy as np
-    v = np.zeros(TT_N, dtype=np.complex128)
-    with open(TT_VSTAR) as f:
+    head, v = {}, np.zeros(n, dtype=np.complex128)
+    with open(path) as f:
         for line in f:
-            if not line.startswith("#"):
-                k, re, im = line.split()
-                v[int(k)] = float(re) + 1j * float(im)
-    return v
+            if line.startswith("#"):
+                parts = line[1:].split()
+                if len(parts) >= 2 and parts[0] in ("lambda", "rho", "iterations", "nonzeros", "norm"):
+                    head[parts[0]] = float(parts[1])
+                continue
+            k, re, im = line.split()
+            v[int(k)] = float(re) + 1j * float(im)
+    return head, v
 
 
-def time_to_tolerance(pkg, stream, dev, barrier) -> dict:
-    """Time to relative error ||v - v*|| / ||v*|| <= 1e-4, v* the stored FP64
-    solution: plain complex64 iterations against the chosen schedule, FP16-H
-    iterations followed by 20 complex64 polish iterations.
-
-    Calibration (untimed) reads v every 5 iterations and finds, for each
-    schedule, the fewest iterations that meet the tolerance; the timed runs then
-    execute exactly those iterations from the zero state, with CUDA events on the
-    launching stream (median of 5).  Setup is timed on the host around the
-    handle creation (Gram products and FP64 factorisation included) and, for the
-    chosen schedule, around building the FP16 copy and its factors."""
+def config3_solver(pkg, stream, dev, rank: int):
+    """The headline problem on the device.  Rank 0 draws the host recipe whose
+    FP64 oracle solution is stored (so its error can be stated); further ranks
+    solve a device-generated instance of the same shape (seed 3 + rank).
+    Returns (solver, g, v* or None, timings)."""
     import numpy as np
     import torch
     import synth
-    p = synth.gaussian_problem(TT_M, TT_N, TT_NNZ, seed=TT_SEED)
-    vstar = load_vstar()
-    nv = np.linalg.norm(vstar)
-    H_d = torch.from_numpy(p.H_c64()).to(dev)
-    g_d = torch.from_numpy(p.g_c64()).to(dev)
+    t0 = time.perf_counter()
+    vstar = None
+    if rank == 0 and os.path.exists(C3_VSTAR):
+        head, vstar = load_vstar_file(C3_VSTAR, C3_N)
+        lam = head["lambda"]
+        H_d = torch.empty((C3_M, C3_N), dtype=torch.complex64, device=dev)
+
+        def sink(r0, rows):
+            with torch.cuda.device(dev):
+                H_d[r0:r0 + rows.shape[0]].copy_(torch.from_numpy(rows))
+
+        _, g, _, _ = synth.chunked_gaussian_problem(C3_M, C3_N, C3_NNZ, C3_SEED, sink=sink, lam=lam)
+        g_d = torch.from_numpy(g.astype(np.complex64)).to(dev)
+    else:
+        H_d, g_d, _, lam = synth.gaussian_problem_device(C3_M, C3_N, C3_NNZ, C3_SEED + rank, device=dev)
+        g = g_d.cpu().numpy().astype(np.complex128)
     torch.cuda.synchronize()
+    gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     with torch.cuda.stream(stream):
-        s = pkg.Solver(H_d, g_d, TT_BLOCKS, 1, p.lam, p.rho, stream=stream)
+        s = pkg.Solver(H_d, g_d, C3_BLOCKS, 1, lam, 1.0, stream=stream)
     torch.cuda.synchronize()
-    setup_plain = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    s.use_fp16(True)
-    torch.cuda.synchronize()
-    setup_fp16 = time.perf_counter() - t0
-    s.use_fp16(False)
-    del H_d
-
-    def err() -> float:
-        return float(np.linalg.norm(s.v().cpu().numpy().astype(np.complex128) - vstar) / nv)
-
-    def run(fp16_iters: int, plain_iters: int) -> None:
-        if fp16_iters:
-            s.use_fp16(True)
-            s.iterate(fp16_iters)
-            s.use_fp16(False)
-        if plain_iters:
-            s.iterate(plain_iters)
-
-    # plain: first multiple of 5 within the tolerance
-    s.reset()
-    k_plain, e_plain = None, None
-    for k in range(5, TT_MAX + 1, 5):
-        s.iterate(5)
-        e = err()
-        if e <= TT_TOL:
-            k_plain, e_plain = k, e
-            break
-    # chosen: fewest FP16 iterations that reach the tolerance after the polish
-    k16, e_chosen = None, None
-    for k in range(0, TT_MAX + 1, 5):
-        s.reset()
-        run(k, TT_POLISH)
-        e = err()
-        if e <= TT_TOL:
-            k16, e_chosen = k, e
-            break
-    out = {"workload": f"gaussian {TT_M}x{TT_N} CN(0,1/{TT_M}), {TT_NNZ} nonzeros, 30 dB, seed {TT_SEED}, "
-                       f"consensus {TT_BLOCKS}x1, lambda 0.05 max|H^H g|, rho 1",
-           "tol": TT_TOL, "vstar": "FP64 oracle, 800 iterations (stored), residuals < 1e-13"}
-    if k_plain is None or k16 is None:
-        out["unavailable"] = "a schedule did not reach the tolerance within 600 iterations"
-        s.close()
-        return out
-
-    def timed(fp16_iters: int, plain_iters: int) -> float:
-        ts = []
-        for _ in range(5):
-            s.reset()
-            barrier()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            run(fp16_iters, plain_iters)
-            b.record(stream)
-            barrier()
-            ts.append(a.elapsed_time(b))
-        if s.status() != 0:
-            raise RuntimeError("device status after the time-to-tolerance runs")
-        return statistics.median(ts)
-
-    ms_plain = timed(0, k_plain)
-    ms_chosen = timed(k16, TT_POLISH)
-    s.close()
-    out.update({
-        "plain": {"iters": k_plain, "ms": ms_plain, "ms_with_setup": ms_plain + setup_plain * 1e3,
-                  "setup_ms": setup_plain * 1e3, "rel_err": e_plain},
-        "chosen": {"fp16_iters": k16, "polish_iters": TT_POLISH, "ms": ms_chosen,
-                   "ms_with_setup": ms_chosen + (setup_plain + setup_fp16) * 1e3,
-                   "setup_ms": (setup_plain + setup_fp16) * 1e3, "rel_err": e_chosen},
-        "speedup": ms_plain / ms_chosen,
-        "speedup_with_setup": (ms_plain + setup_plain * 1e3) / (ms_chosen + (setup_plain + setup_fp16) * 1e3),
-    })
-    return out
-
-
-def mixed_precision_large(pkg, stream, dev, barrier, peaks) -> dict:
-    """The 8192 x 131072 workload (16 row blocks of 512 rows, consensus): per
-    iteration in complex64 and in FP16 H, and 300 iterations as 280 FP16 + 20
-    complex64 polish against 300 complex64, each timed with CUDA events on the
-    launching stream.  H (8.6 GB complex64) is far larger than L2."""
-    import torch
-    import synth
-    c = synth.CONFIG3
-    H, g, _, lam = synth.gaussian_problem_device(c["m"], c["n"], c["nnz"], c["seed"], device=dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    with torch.cuda.stream(stream):
-        s = pkg.Solver(H, g, c["row_blocks"], 1, lam, c["rho"], stream=stream)
-    torch.cuda.synchronize()
-    setup_s = time.perf_counter() - t0
-    del H, g
+    setup_ms = (time.perf_counter() - t0) * 1e3
+    del H_d, g_d
     torch.cuda.empty_cache()
-    t0 = time.perf_counter()
-    s.use_fp16(True)
-    torch.cuda.synchronize()
-    setup16_s = time.perf_counter() - t0
-    out = {"workload": f"gaussian {c['m']}x{c['n']} CN(0,1/{c['m']}), {c['nnz']} nonzeros, 30 dB, "
-                       f"seed {c['seed']} (device generator), consensus {c['row_blocks']}x1, "
-                       f"lambda 0.05 max|H^H g|, rho 1",
-           "setup_ms": setup_s * 1e3, "fp16_setup_ms": setup16_s * 1e3}
+    return s, g, lam, vstar, {"inputs_s": gen_s, "setup_ms": setup_ms}
 
-    def per_iter(fp16: bool, k: int = 20) -> float:
-        s.use_fp16(fp16)
-        for _ in range(3):
-            s.iterate(1)
-        barrier()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(k):
-            s.iterate(1)
-        b.record(stream)
-        barrier()
-        return a.elapsed_time(b) / k * 1e3
 
-    info = s.info()
-    state = (2 * c["row_blocks"] + 2) * c["n"] * 8
-    for name, fp16, hb in (("c64", False, info["h_bytes"]), ("fp16_h", True, info["h16_bytes"])):
-        us = per_iter(fp16)
-        alg = 2 * hb + info["factor_bytes"] + state
-        out[name] = {"us_per_iter": us, "alg_bytes_per_iter": alg, "gbs": alg / us / 1e3,
-                     "frac": alg / us / 1e3 / peaks["hbm_gbs"]}
+def rel_err(s, vstar) -> float:
+    import numpy as np
+    v = s.v().cpu().numpy().astype(np.complex128)
+    return float(np.linalg.norm(v - vstar) / np.linalg.norm(vstar))
 
-    def schedule(k16: int, k32: int) -> float:
+
+def config3_schedules(s, stream, barrier, vstar) -> dict:
+    """The workload's 300-iteration schedules from the zero state: 280 FP16-H
+    iterations then 20 complex64 polish iterations ("chosen") against 300
+    complex64 iterations ("plain"); CUDA events on the launching stream, and
+    each result's relative error against the FP64 oracle solution."""
+    import torch
+
+    def schedule(k16: int, k32: int):
         s.reset()
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -437,24 +361,96 @@ def mixed_precision_large(pkg, stream, dev, barrier, peaks) -> dict:
         if k16:
             s.use_fp16(True)
             s.iterate(k16)
-        s.use_fp16(False)
+            s.use_fp16(False)
         s.iterate(k32)
         b.record(stream)
         barrier()
-        return a.elapsed_time(b)
+        rec = s.residuals(1)[0].tolist()
+        out = {"ms": a.elapsed_time(b), "final_rp2_rd2": rec[:2]}
+        if vstar is not None:
+            out["rel_err_vs_fp64_oracle"] = rel_err(s, vstar)
+        return out
 
-    ms_chosen = schedule(c["fp16_iters"], c["polish_iters"])
-    rec_chosen = s.residuals(1)[0].tolist()
-    ms_plain = schedule(0, c["fp16_iters"] + c["polish_iters"])
-    rec_plain = s.residuals(1)[0].tolist()
+    chosen = schedule(C3_FP16, C3_POLISH)
+    chosen.update({"fp16_iters": C3_FP16, "polish_iters": C3_POLISH})
+    plain = schedule(0, C3_FP16 + C3_POLISH)
+    plain.update({"iters": C3_FP16 + C3_POLISH})
     if s.status() != 0:
-        raise RuntimeError("device status after the mixed-precision runs")
-    s.close()
-    out["schedule"] = {"chosen": {"fp16_iters": c["fp16_iters"], "polish_iters": c["polish_iters"],
-                                  "ms": ms_chosen, "final_rp2_rd2": rec_chosen[:2]},
-                       "plain": {"iters": c["fp16_iters"] + c["polish_iters"], "ms": ms_plain,
-                                 "final_rp2_rd2": rec_plain[:2]},
-                       "speedup": ms_plain / ms_chosen}
+        raise RuntimeError("device status after the schedules")
+    return {"chosen": chosen, "plain": plain, "speedup": plain["ms"] / chosen["ms"]}
+
+
+def config3_time_to_tol(s, stream, barrier, vstar, setup_ms: float, setup16_ms: float) -> dict:
+    """Time to ||v - v*|| / ||v*|| <= 1e-4 on the headline problem, v* the stored
+    FP64 oracle solution: plain complex64 iterations against the chosen schedule
+    (FP16-H iterations, then 20 complex64 polish iterations).
+
+    Calibration (untimed) finds the fewest iterations, in steps of 5, that meet
+    the tolerance: for plain by reading v every 5 iterations; for chosen by
+    checkpointing the FP16 run every 5 iterations, polishing a copy and
+    restoring the checkpoint.  The timed runs then execute exactly those
+    iterations from the zero state (CUDA events on the launching stream, median
+    of 3).  "with setup" adds the handle creation (Gram products and FP64
+    factorisation) and, for chosen, building the FP16 copy and its factors."""
+    import torch
+    out = {"tol": TT_TOL, "vstar": "FP64 oracle (stored), residuals at the Boyd tolerances 1e-14 / 1e-12"}
+    s.reset()
+    k_plain = None
+    for k in range(5, TT_MAX + 1, 5):
+        s.iterate(5)
+        if rel_err(s, vstar) <= TT_TOL:
+            k_plain = k
+            break
+    s.reset()
+    s.use_fp16(True)
+    k16 = None
+    for k in range(0, TT_MAX + 1, 5):
+        if k:
+            s.iterate(5)
+        ck = s.state()
+        s.use_fp16(False)
+        s.iterate(C3_POLISH)
+        e = rel_err(s, vstar)
+        if e <= TT_TOL:
+            k16 = k
+            break
+        s.set_state(*ck)
+        s.use_fp16(True)
+    s.use_fp16(False)
+    if k_plain is None or k16 is None:
+        out["unavailable"] = f"a schedule did not reach the tolerance within {TT_MAX} iterations"
+        return out
+
+    def timed(fp16_iters: int, plain_iters: int):
+        ts = []
+        for _ in range(3):
+            s.reset()
+            barrier()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            if fp16_iters:
+                s.use_fp16(True)
+                s.iterate(fp16_iters)
+                s.use_fp16(False)
+            s.iterate(plain_iters)
+            b.record(stream)
+            barrier()
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts), rel_err(s, vstar)
+
+    ms_plain, e_plain = timed(0, k_plain)
+    ms_chosen, e_chosen = timed(k16, C3_POLISH)
+    if s.status() != 0:
+        raise RuntimeError("device status after the time-to-tolerance runs")
+    out.update({
+        "plain": {"iters": k_plain, "ms": ms_plain, "setup_ms": setup_ms,
+                  "ms_with_setup": ms_plain + setup_ms, "rel_err": e_plain},
+        "chosen": {"fp16_iters": k16, "polish_iters": C3_POLISH, "ms": ms_chosen,
+                   "setup_ms": setup_ms + setup16_ms, "ms_with_setup": ms_chosen + setup_ms + setup16_ms,
+                   "rel_err": e_chosen},
+        "speedup": ms_plain / ms_chosen,
+        "speedup_with_setup": (ms_plain + setup_ms) / (ms_chosen + setup_ms + setup16_ms),
+    })
     return out
 
 
@@ -521,7 +517,7 @@ def uneven_problems(pkg, stream, dev, barrier, peaks, iters: int = 300) -> dict:
             H, g, _, lam = synth.gaussian_problem_device(m, n, nnz, seed, device=dev)
             s = pkg.Solver(H, g, M, 1, lam, 1.0, stream=stream)
             info = s.info()
-            alg += 2 * info["h_bytes"] + info["factor_bytes"] + (2 * M + 2) * n * 8
+            alg += 2 * info["h_bytes"] + info["factor_bytes"] + state_bytes(M, n)
             solvers.append(s)
             del H, g
     torch.cuda.synchronize()
@@ -570,17 +566,59 @@ def uneven_problems(pkg, stream, dev, barrier, peaks, iters: int = 300) -> dict:
 def differentiable(pkg, stream, dev, barrier, K: int = 100) -> dict:
     """The differentiable workload: H 2048 x 16384, 16 scenes of 64 nonzeros
     (seeds 500-515), consensus over 8 row blocks, loss sum_b ||v_K - u_b||^2.
-    Times K recorded forward iterations and the reverse sweep (CUDA events on
-    the launching stream; the loss gradient dL/dv is formed on the device)."""
+    (a) complex64 H: UnrolledADMM over 16 single-scene handles (K recorded
+    iterations each, then each handle's reverse sweep) -- gradients in G,
+    lambda and rho through loss.backward(); (b) the FP16-encoded H: all 16
+    scenes together on the tensor cores (BatchSolver).  Forward and reverse
+    times with CUDA events on the launching stream (median of 3)."""
     import numpy as np
     import torch
     import synth
     p = synth.gaussian_problem(2048, 16384, 64, seed=5)
     G, U, lam = synth.shared_h_scenes(p.H, 16, seed0=500, nnz=64)
+    Hd = torch.from_numpy(p.H_c64()).to(dev)
+    G_d = torch.from_numpy(G.astype(np.complex64)).to(dev)
+    U_d = torch.from_numpy(U.astype(np.complex64)).to(dev)
+    out = {"workload": "gaussian 2048x16384 CN(0,1/2048), 16 scenes x 64 nonzeros (seeds 500-515), "
+                       "consensus 8x1, K = 100, loss sum ||v_K - u||^2"}
+
+    # (a) complex64, one handle per scene, through torch.autograd
     with torch.cuda.stream(stream):
-        bs = pkg.BatchSolver(torch.from_numpy(p.H_c64()).to(dev), 8, 1, lam, 1.0, stream=stream)
-        G_d = torch.from_numpy(G.astype(np.complex64)).to(dev)
-        U_d = torch.from_numpy(U.astype(np.complex64)).to(dev)
+        solvers = [pkg.Solver(Hd, G_d[b], 8, 1, lam[b], 1.0, stream=stream) for b in range(16)]
+    torch.cuda.synchronize()
+
+    def once_c64():
+        Gt = G_d.clone().requires_grad_(True)
+        lam_t = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+        rho_t = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+        a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        barrier()
+        a.record(stream)
+        with torch.cuda.stream(stream):
+            V = pkg.UnrolledADMM.apply(Gt, lam_t, rho_t, solvers, K)
+            loss = ((V - U_d).abs() ** 2).sum()
+        b.record(stream)
+        with torch.cuda.stream(stream):
+            loss.backward()
+        c.record(stream)
+        barrier()
+        return a.elapsed_time(b), b.elapsed_time(c)
+
+    once_c64()
+    fw, bw = zip(*[once_c64() for _ in range(3)])
+    for sv in solvers:
+        if sv.status() != 0:
+            raise RuntimeError("device status after the complex64 differentiable workload")
+        sv.close()
+    fwd, bwd = statistics.median(fw), statistics.median(bw)
+    out["complex64_per_scene"] = {"forward_ms": fwd, "backward_ms": bwd,
+                                  "gradients_per_s": 16 / ((fwd + bwd) / 1e3),
+                                  "backward_over_forward": bwd / fwd,
+                                  "path": "UnrolledADMM over 16 Solver handles (admm_backward)"}
+
+    # (b) FP16-encoded H, all scenes on the tensor cores
+    with torch.cuda.stream(stream):
+        bs = pkg.BatchSolver(Hd, 8, 1, lam, 1.0, stream=stream)
 
     def once():
         a, b, c = (torch.cuda.Event(enable_timing=True) for _ in range(3))
@@ -604,10 +642,9 @@ def differentiable(pkg, stream, dev, barrier, K: int = 100) -> dict:
     info = bs.info()
     bs.close()
     fwd, bwd = statistics.median(fw), statistics.median(bw)
-    return {"workload": "gaussian 2048x16384 CN(0,1/2048), 16 scenes x 64 nonzeros (seeds 500-515), "
-                        "consensus 8x1, K = 100, loss sum ||v_K - u||^2, FP16 H",
-            "forward_ms": fwd, "backward_ms": bwd, "gradients_per_s": 16 / ((fwd + bwd) / 1e3),
-            "backward_over_forward": bwd / fwd, "tensor_flops_per_iter": info["tensor_flops"]}
+    out["fp16_batched"] = {"forward_ms": fwd, "backward_ms": bwd, "gradients_per_s": 16 / ((fwd + bwd) / 1e3),
+                           "backward_over_forward": bwd / fwd, "tensor_flops_per_iter": info["tensor_flops"]}
+    return out
 
 
 def direct_form(pkg, stream, dev, barrier, peaks, iters: int = 64) -> dict:
@@ -645,7 +682,7 @@ def direct_form(pkg, stream, dev, barrier, peaks, iters: int = 64) -> dict:
         if s.status() != 0:
             raise RuntimeError(f"device status after the {form} {M}x{N} run")
         us = a.elapsed_time(b) / iters * 1e3
-        state = (2 * M + 2) * c["n"] * 8
+        state = state_bytes(M, c["n"])
         if form == "direct":
             passes = 0 if N == 1 else 2
             alg = passes * info["h_bytes"] + info["factor_bytes"] + state + (M * c["n"] * 8 if N == 1 else 0)
@@ -665,6 +702,108 @@ def direct_form(pkg, stream, dev, barrier, peaks, iters: int = 64) -> dict:
     del H, g
     torch.cuda.empty_cache()
     return out
+
+
+def state_bytes(M: int, n: int) -> int:
+    """Algorithmic state bytes of one iteration: v and the M duals read by the
+    first product and again by the update, and written once, complex64."""
+    return (3 * M + 3) * n * 8
+
+
+def cra_three_splits(pkg, stream, dev, barrier, peaks, K: int, warmup: int, rank: int) -> dict:
+    """The CRA-shaped 1440 x 32768 workload in the paper's three splits (8x1,
+    1x8, 4x4), K iterations per split as one persistent launch, complex64 and
+    FP16 H, with each split's algorithmic bytes per iteration."""
+    import torch
+    p = make_problem(rank)
+    H_d = torch.from_numpy(p.H_c64()).to(dev)
+    g_d = torch.from_numpy(p.g_c64()).to(dev)
+    torch.cuda.synchronize()
+    solvers = []
+    with torch.cuda.stream(stream):
+        for M, N in SPLITS:
+            solvers.append(pkg.Solver(H_d, g_d, M, N, p.lam, p.rho, stream=stream))
+    del H_d, g_d
+    torch.cuda.synchronize()
+    out = {"workload": ("CRA-shaped imaging, H 1440x32768 complex64 (40 freqs x 36 rx, 32^3 voxels), "
+                        "three-plate scene, 30 dB"), "lambda": p.lam, "rho": p.rho, "splits": {}}
+
+    def timed(s, fp16: bool):
+        s.use_fp16(fp16)
+        for _ in range(max(warmup, 0)):
+            s.iterate(1)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.iterate(K)
+        b.record(stream)
+        barrier()
+        info = s.info()
+        hb = info["h16_bytes"] if fp16 else info["h_bytes"]
+        alg = 2 * hb + info["factor_bytes"] + state_bytes(s.M, s.n)
+        us = a.elapsed_time(b) / K * 1e3
+        return {"us_per_iter": us, "iters_per_s": 1e6 / us, "alg_bytes_per_iter": alg,
+                "gbs": alg / us / 1e3, "frac": alg / us / 1e3 / peaks["hbm_gbs"]}, info
+
+    traffic = load_traffic()
+    for (M, N), s in zip(SPLITS, solvers):
+        c64, info = timed(s, False)
+        f16, _ = timed(s, True)
+        s.use_fp16(False)
+        name = f"{M}x{N}"
+        c64.update({"ctas": info["ctas"], "rows_per_stage": info["rows_per_stage"], "stages": info["stages"],
+                    "setup_ms": {"gram": info["setup_gram_ms"], "cholesky_inverse": info["setup_factor_ms"]},
+                    "fp16_h": f16})
+        if traffic:
+            c64["dram_bytes_per_launch"] = traffic.get(name)
+            f16["dram_bytes_per_launch"] = traffic.get(name + "_fp16")
+            if traffic.get(name):
+                # DRAM bytes actually moved (ncu) over the same time: the reversed
+                # second pass finds the first pass's last 52 MiB in L2
+                c64["dram_frac"] = traffic[name] / c64["us_per_iter"] / 1e3 / peaks["hbm_gbs"]
+        out["splits"][name] = c64
+        if s.status() != 0:
+            raise RuntimeError(f"device status after the CRA {name} runs")
+        s.close()
+    tot_us = sum(v["us_per_iter"] for v in out["splits"].values())
+    out["iters_per_s_all_splits"] = len(SPLITS) / tot_us * 1e6
+    out["note"] = ("frac counts algorithmic bytes; where it exceeds the DRAM-based dram_frac the "
+                   "difference is the L2 reuse between the two passes, not a faster memory")
+    return out
+
+
+def small_workload(pkg, stream, dev, barrier, iters: int = 300, reps: int = 5) -> dict:
+    """The 256 x 4096 workload (consensus over 4 row blocks of 64, rho 1, 300
+    iterations): H (8.4 MB) stays in L2, so the iteration is latency bound;
+    iterations per second of one 300-iteration launch (median of `reps`)."""
+    import torch
+    import synth
+    c = synth.CONFIG1
+    p = synth.gaussian_problem(c["m"], c["n"], c["nnz"], seed=c["seed"])
+    with torch.cuda.stream(stream):
+        s = pkg.Solver(torch.from_numpy(p.H_c64()).to(dev), torch.from_numpy(p.g_c64()).to(dev),
+                       c["row_blocks"], 1, p.lam, c["rho"], stream=stream)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps + 1):
+        s.reset()
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s.iterate(iters)
+        b.record(stream)
+        barrier()
+        ts.append(a.elapsed_time(b))
+    if s.status() != 0:
+        raise RuntimeError("device status after the 256x4096 runs")
+    info = s.info()
+    s.close()
+    ms = statistics.median(ts[1:])
+    alg = 2 * info["h_bytes"] + info["factor_bytes"] + state_bytes(c["row_blocks"], c["n"])
+    return {"workload": "Gaussian 256x4096 CN(0,1/256), 16 nonzeros, 30 dB, seed 0, consensus 4x1, rho 1",
+            "iters": iters, "ms": ms, "iters_per_s": iters / ms * 1e3, "us_per_iter": ms / iters * 1e3,
+            "l2_gbs": alg * iters / ms / 1e6, "ctas": info["ctas"],
+            "note": "H is L2-resident: latency bound, HBM fraction not meaningful"}
 
 
 def run_ours(args) -> None:
@@ -687,21 +826,8 @@ def run_ours(args) -> None:
 
     import paper_1811_05571_gb300 as pkg
     pkg.load()
-    p = make_problem(rank)
+    peaks = load_peaks()
     stream = torch.cuda.Stream()
-    H_d = torch.from_numpy(p.H_c64()).to(dev)
-    g_d = torch.from_numpy(p.g_c64()).to(dev)
-    torch.cuda.synchronize()
-    solvers = []
-    with torch.cuda.stream(stream):
-        for M, N in SPLITS:
-            solvers.append(pkg.Solver(H_d, g_d, M, N, p.lam, p.rho, stream=stream))
-    del H_d
-    torch.cuda.synchronize()
-    if args.l2_keep_mb is not None:
-        for s in solvers:
-            s.set_option(pkg.ADMM_OPT_L2_KEEP_BYTES, int(args.l2_keep_mb * (1 << 20)))
-    infos = [s.info() for s in solvers]
 
     def barrier():
         torch.cuda.synchronize()
@@ -709,215 +835,132 @@ def run_ours(args) -> None:
             dist.barrier()
         torch.cuda.synchronize()
 
-    # warm-up
-    for _ in range(max(args.warmup, 0)):
-        for s in solvers:
-            s.iterate(1)
-    barrier()
+    s, g_np, lam, vstar, prep = config3_solver(pkg, stream, dev, rank)
+    info = s.info()
+    if args.l2_keep_mb is not None:
+        s.set_option(pkg.ADMM_OPT_L2_KEEP_BYTES, int(args.l2_keep_mb * (1 << 20)))
+    alg = 2 * info["h_bytes"] + info["factor_bytes"] + state_bytes(C3_BLOCKS, C3_N)
 
+    # warm-up, then K steps as one persistent launch of K iterations
+    for _ in range(max(args.warmup, 0)):
+        s.iterate(1)
+    barrier()
     K = args.steps
-    ev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-           for _ in range(K)] for _ in solvers]
-    t_start, t_end = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(dev)
     clocks.start()
     barrier()
-    # K steps of work, split by split: each handle runs its K iterations as one
-    # persistent launch (admm_iterate(h, K), the way a problem is iterated)
-    t_start.record(stream)
-    for si, s in enumerate(solvers):
-        ev[si][0][0].record(stream)
-        s.iterate(K)
-        ev[si][0][1].record(stream)
-    t_end.record(stream)
+    t0.record(stream)
+    s.iterate(K)
+    t1.record(stream)
     barrier()
     clk = clocks.stop()
-    total_s = t_start.elapsed_time(t_end) / 1e3
-    split_s = [ev[si][0][0].elapsed_time(ev[si][0][1]) / 1e3 for si in range(len(solvers))]
-    # for reference (not in the headline): K single-iteration launches per split
-    barrier()
-    for si, s in enumerate(solvers):
-        for k in range(K):
-            ev[si][k][0].record(stream)
-            s.iterate(1)
-            ev[si][k][1].record(stream)
-    barrier()
-    single_s = [sum(ev[si][k][0].elapsed_time(ev[si][k][1]) for k in range(K)) / 1e3
-                for si in range(len(solvers))]
-    for s in solvers:
-        st = s.status()
-        if st != 0:
-            raise RuntimeError(f"device status {st} after the timed region")
-    total_s = max_over_ranks(total_s, world, dev)
+    if s.status() != 0:
+        raise RuntimeError("device status after the timed region")
+    timed_s = t0.elapsed_time(t1) / 1e3
+    total_s = max_over_ranks(timed_s, world, dev)
 
-    # end to end through the public API with host buffers: per step and split,
-    # set_g from pinned host memory, one iteration, the image back to pinned
-    # memory.  Each split's handle runs on its own stream, so one handle's
-    # copies overlap another handle's iteration (the kernels themselves run
-    # one after the other: each occupies every SM)
-    g_host = torch.from_numpy(p.g_c64()).pin_memory()
-    v_host = [torch.empty(N_COLS, dtype=torch.complex64).pin_memory() for _ in solvers]
-    e2e_streams = [stream] + [torch.cuda.Stream() for _ in solvers[1:]]
+    # for reference: K single-iteration launches
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for st_ in e2e_streams[1:]:
-        st_.wait_event(e0)
-    for s, st_ in zip(solvers, e2e_streams):
-        s.stream = st_
-    for k in range(K):
-        for si, s in enumerate(solvers):
-            s.set_g(g_host)
-            s.iterate(1)
-            s.v(out=v_host[si])
-    for st_ in e2e_streams[1:]:
-        stream.wait_stream(st_)
-    e1.record(stream)
+    for e0, e1 in ev:
+        e0.record(stream)
+        s.iterate(1)
+        e1.record(stream)
     barrier()
-    for s in solvers:
-        s.stream = stream
-    e2e_s = e0.elapsed_time(e1) / 1e3
-    e2e_s = max_over_ranks(e2e_s, world, dev)
+    single_us = sum(e0.elapsed_time(e1) for e0, e1 in ev) / K * 1e3
 
-    # the same three handles streaming the FP16 copy of H (built here, untimed)
-    fp16_split_s = []
-    for s in solvers:
-        s.use_fp16(True)
+    # end to end through the public API with host buffers: per step, the data
+    # vector from pinned host memory, one iteration, the image back to pinned memory
+    g_host = torch.from_numpy(g_np.astype(np.complex64)).pin_memory()
+    v_host = torch.empty(C3_N, dtype=torch.complex64).pin_memory()
+    barrier()
+    t0.record(stream)
+    for _ in range(K):
+        s.set_g(g_host)
+        s.iterate(1)
+        s.v(out=v_host)
+    t1.record(stream)
+    barrier()
+    e2e_s = max_over_ranks(t0.elapsed_time(t1) / 1e3, world, dev)
+
+    # FP16 H: build the copy and its factors (timed), then K iterations in one launch
+    t_f = time.perf_counter()
+    s.use_fp16(True)
     torch.cuda.synchronize()
-    infos16 = [s.info() for s in solvers]
+    setup16_ms = (time.perf_counter() - t_f) * 1e3
+    info16 = s.info()
+    alg16 = 2 * info16["h16_bytes"] + info16["factor_bytes"] + state_bytes(C3_BLOCKS, C3_N)
     for _ in range(max(args.warmup, 0)):
-        for s in solvers:
-            s.iterate(1)
+        s.iterate(1)
     barrier()
-    ev16 = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-             for _ in range(K)] for _ in solvers]
-    for si, s in enumerate(solvers):
-        for k in range(K):
-            ev16[si][k][0].record(stream)
-            s.iterate(1)
-            ev16[si][k][1].record(stream)
+    t0.record(stream)
+    s.iterate(K)
+    t1.record(stream)
     barrier()
-    fp16_split_s = [sum(ev16[si][k][0].elapsed_time(ev16[si][k][1]) for k in range(K)) / 1e3
-                    for si in range(len(solvers))]
-    for s in solvers:
-        if s.status() != 0:
-            raise RuntimeError("device status after the FP16 timed region")
-        s.use_fp16(False)
+    us16 = t0.elapsed_time(t1) / K * 1e3
+    s.use_fp16(False)
+    if s.status() != 0:
+        raise RuntimeError("device status after the FP16 timed region")
 
-    ttt = None
-    if not args.no_time_to_tol:
-        ttt = time_to_tolerance(pkg, stream, dev, barrier)
-    large = None
-    if not args.no_large:
-        large = mixed_precision_large(pkg, stream, dev, barrier, peaks=load_peaks())
-    batched = None
+    us = timed_s / K * 1e6
+    headline = {
+        "complex64": {"us_per_iter": us, "iters_per_s": 1e6 / us, "alg_bytes_per_iter": alg,
+                      "gbs": alg / us / 1e3, "frac": alg / us / 1e3 / peaks["hbm_gbs"],
+                      "us_per_single_iteration_launch": single_us},
+        "fp16_h": {"us_per_iter": us16, "iters_per_s": 1e6 / us16, "alg_bytes_per_iter": alg16,
+                   "gbs": alg16 / us16 / 1e3, "frac": alg16 / us16 / 1e3 / peaks["hbm_gbs"],
+                   "setup_ms": setup16_ms},
+        "ctas": info["ctas"], "rows_per_stage": info["rows_per_stage"], "stages": info["stages"],
+        "inputs_s": prep["inputs_s"], "setup_ms": prep["setup_ms"],
+        "setup_gram_ms": info["setup_gram_ms"], "setup_factor_ms": info["setup_factor_ms"],
+    }
+    if vstar is not None:
+        headline["schedules"] = config3_schedules(s, stream, barrier, vstar)
+        if not args.no_time_to_tol:
+            headline["time_to_tol"] = config3_time_to_tol(s, stream, barrier, vstar, prep["setup_ms"],
+                                                          setup16_ms)
+    s.close()
+    torch.cuda.empty_cache()
+
+    extra = {}
+    if not args.no_cra:
+        extra["cra_three_splits"] = cra_three_splits(pkg, stream, dev, barrier, peaks, K, args.warmup, rank)
+    if not args.no_small:
+        extra["small_256x4096"] = small_workload(pkg, stream, dev, barrier)
     if not args.no_batch:
-        batched = batched_shared_h(pkg, stream, dev, barrier, p, peaks=load_peaks(), batch=args.batch)
-    diff = None
+        extra["batched_shared_h"] = batched_shared_h(pkg, stream, dev, barrier, make_problem(rank),
+                                                     peaks=peaks, batch=args.batch)
     if not args.no_adjoint:
-        diff = differentiable(pkg, stream, dev, barrier)
-    uneven = None
+        extra["differentiable"] = differentiable(pkg, stream, dev, barrier)
     if not args.no_uneven:
-        uneven = uneven_problems(pkg, stream, dev, barrier, peaks=load_peaks())
-    direct = None
+        extra["uneven_problems"] = uneven_problems(pkg, stream, dev, barrier, peaks=peaks)
     if not args.no_direct:
-        direct = direct_form(pkg, stream, dev, barrier, peaks=load_peaks())
+        extra["direct_form"] = direct_form(pkg, stream, dev, barrier, peaks=peaks)
 
-    phases = None
-    if args.trace > 0:
-        import numpy as np
-        import paper_1811_05571_gb300 as pkg2
-        phases = {}
-        names = ["pass_up", "barrier1", "reduce", "barrier2", "factor", "barrier3", "pass_down"]
-        for (M, N), s in zip(SPLITS, solvers):
-            s.set_option(pkg2.ADMM_OPT_TRACE_ITERS, args.trace)
-            s.iterate(args.trace)
-            tr = s.trace(args.trace).astype(np.float64)   # (2, k, 8) ns
-            s.set_option(pkg2.ADMM_OPT_TRACE_ITERS, 0)
-            d = np.diff(tr[0], axis=1)                     # CTA 0
-            it_ns = np.diff(tr[0][:, 0]) if tr.shape[1] > 1 else np.array([tr[0][0, 7] - tr[0][0, 0]])
-            phases[f"{M}x{N}"] = {"us": {n: float(np.median(d[:, q])) / 1e3 for q, n in enumerate(names)},
-                                  "iteration_us": float(np.median(it_ns)) / 1e3}
-        torch.cuda.synchronize()
-
-    peaks = load_peaks()
-    per_split = {}
-    bytes_total, time_total = 0.0, 0.0
-    for (M, N), info, ts in zip(SPLITS, infos, split_s):
-        # algorithmic bytes of one iteration: two passes over H, one read of
-        # every cached factor, and the state vectors read and written once
-        alg = 2 * info["h_bytes"] + info["factor_bytes"] + (2 * M + 2) * N_COLS * 8
-        per_split[f"{M}x{N}"] = {
-            "iters_per_s": K / ts, "us_per_iter": ts / K * 1e6,
-            "us_per_single_iteration_launch": single_s[len(per_split)] / K * 1e6,
-            "alg_bytes_per_iter": alg, "gbs": alg * K / ts / 1e9,
-            "frac": alg * K / ts / 1e9 / peaks["hbm_gbs"],
-            "ctas": info["ctas"], "rows_per_stage": info["rows_per_stage"],
-            "stages": info["stages"],
-            "setup_ms": {"gram": info["setup_gram_ms"], "cholesky_inverse": info["setup_factor_ms"]},
-        }
-        bytes_total += alg * K
-        time_total += ts
-    for (M, N), info, ts in zip(SPLITS, infos16, fp16_split_s):
-        alg = 2 * info["h16_bytes"] + info["factor_bytes"] + (2 * M + 2) * N_COLS * 8
-        per_split[f"{M}x{N}"]["fp16_h"] = {
-            "iters_per_s": K / ts, "us_per_iter": ts / K * 1e6, "alg_bytes_per_iter": alg,
-            "gbs": alg * K / ts / 1e9, "frac": alg * K / ts / 1e9 / peaks["hbm_gbs"]}
-    achieved = bytes_total / time_total / 1e9
     traffic = load_traffic()
-    dram_achieved = None
-    if traffic and all(f"{M}x{N}" in traffic for M, N in SPLITS):
-        # DRAM bytes actually moved (ncu, per iteration) over the same time: the
-        # L2 reuse between the two passes keeps it below the algorithmic bytes
-        dram_achieved = sum(traffic[f"{M}x{N}"] * K for M, N in SPLITS) / time_total / 1e9
-    if traffic is not None:
-        for name in per_split:
-            per_split[name]["dram_bytes_per_launch"] = traffic.get(name)
-            per_split[name]["fp16_h"]["dram_bytes_per_launch"] = traffic.get(name + "_fp16")
-    value = job_value(world, len(SPLITS), K, total_s)
+    tr = traffic.get("c3") if traffic else None
+    value = job_value(world, 1, K, total_s)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": args.warmup, "ms_per_step": total_s / K * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "m": M_ROWS, "n": N_COLS,
-                   "splits": [f"{M}x{N}" for M, N in SPLITS],
-                   "parallelism": "replicas" if world > 1 else "single GPU",
-                   "l2_keep_mb": args.l2_keep_mb,
-                   "lambda": p.lam, "rho": p.rho,
-                   "l2": "inputs larger than L2 (H 377 MB per split vs 129 MB L2), no flush"},
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                     "frac": achieved / peaks["hbm_gbs"],
-                     "traffic": (sum(traffic[f"{M}x{N}"] for M, N in SPLITS) / len(SPLITS))
-                                if traffic and all(f"{M}x{N}" in traffic for M, N in SPLITS) else None,
+        "config": CONFIG,
+        "roofline": {"bound": "hbm", "achieved": alg / us / 1e3, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": alg / us / 1e3 / peaks["hbm_gbs"], "traffic": tr,
                      "peak_source": peaks["source"], "kernel": "admm::iterate_kernel",
                      "per": "iteration (achieved and traffic per iteration; one launch runs K iterations)",
-                     "dram_achieved": dram_achieved,
-                     "dram_frac": dram_achieved / peaks["hbm_gbs"] if dram_achieved else None},
-        "e2e": {"value": job_value(world, len(SPLITS), K, e2e_s), "unit": UNIT,
-                "h2d_bytes_per_step": len(SPLITS) * M_ROWS * 8,
-                "d2h_bytes_per_step": len(SPLITS) * N_COLS * 8},
-        "gpu_launches": len(SPLITS),
+                     "dram_frac": (tr / us / 1e3 / peaks["hbm_gbs"]) if tr else None},
+        "e2e": {"value": job_value(world, 1, K, e2e_s), "unit": UNIT,
+                "h2d_bytes_per_step": C3_M * 8, "d2h_bytes_per_step": C3_N * 8},
+        "gpu_launches": 1,
         "clocks": clk,
-        "splits": per_split,
+        "headline": headline,
+        "parallelism": "replicas" if world > 1 else "single GPU",
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
-    if ttt is not None:
-        line["time_to_tol"] = ttt
-    if large is not None:
-        line["mixed_precision_large"] = large
-    if batched is not None:
-        line["batched_shared_h"] = batched
-    if diff is not None:
-        line["differentiable"] = diff
-    if uneven is not None:
-        line["uneven_problems"] = uneven
-    if direct is not None:
-        line["direct_form"] = direct
-    if phases is not None:
-        line["phases"] = phases
-    for s in solvers:
-        s.close()
+    line.update(extra)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -47,7 +47,7 @@
 extern "C" {
 #endif
 
-#define ADMM_ABI_VERSION 4
+#define ADMM_ABI_VERSION 5
 
 /* status codes */
 #define ADMM_OK            0  /* success */
@@ -148,6 +148,10 @@ typedef struct admm_plan {
     int32_t smem_bytes;       /* dynamic shared memory */
     int32_t max_blocks_per_slab; /* most column blocks one slab intersects */
     int64_t ld;               /* padded row pitch, complex elements */
+    int32_t groups;           /* column groups of consumer warps per CTA: 2 for slabs of more
+                                 than 256 pairs (each group takes half the slab, so a lane
+                                 holds chunks x 32 pairs of a half), else 1 */
+    int32_t reserved;
 } admm_plan_t;
 
 /* ABI version of the loaded library (ADMM_ABI_VERSION at build time). */
@@ -487,6 +491,18 @@ int admm_batch_tune(admm_batch_t* h, void* stream);
  * since the soft-threshold is the iteration's only non-linear step.  0 turns
  * recording off.  Resets the state (admm_batch_reset) and synchronises. */
 int admm_batch_record(admm_batch_t* h, int32_t iters);
+
+/* Replace the per-scene weights lambda[b] >= 0 (`batch` doubles; no
+ * refactorisation: kappa_b = lambda_b / (row_blocks rho)).  The iteration
+ * state is kept; a recording made before is invalidated.  Synchronises the
+ * device. */
+int admm_batch_set_lambda(admm_batch_t* h, const double* lambda);
+
+/* Replace rho > 0: refactors every block rho I + H_b H_b^H of the matrix the
+ * FP16 copy encodes (as admm_set_rho does for a single handle), rescales the
+ * scaled duals by rho_old / rho_new so the unscaled duals are kept, and
+ * invalidates a recording.  Synchronises `stream`. */
+int admm_batch_set_rho(admm_batch_t* h, double rho, void* stream);
 
 /* Reverse sweep over the iterations run since the last reset (all recorded):
  * given dV = dL/dv (batch x n complex64, x_bar = dL/dRe x + i dL/dIm x) of a

@@ -193,7 +193,7 @@ def _sq(x: np.ndarray) -> float:
 # the four iterations
 # ----------------------------------------------------------------------------
 
-def lasso_admm(H, g, lam, rho, iters, eps=None) -> OracleResult:
+def lasso_admm(H, g, lam, rho, iters, eps=None, on_iter=None) -> OracleResult:
     """Unsplit lasso ADMM: Eq. (original) with P = I, Q = -I, c = 0.
 
     u <- (H^*H + rho I)^{-1}(H^* g + rho (v - s));  v <- S_{lam/rho}(u + s);
@@ -215,6 +215,8 @@ def lasso_admm(H, g, lam, rho, iters, eps=None) -> OracleResult:
         s = s + u - v_new
         hist.append((_sq(u - v_new), rho * rho * _sq(v_new - v), _sq(u), _sq(v_new), _sq(s)))
         v = v_new
+        if on_iter is not None:
+            on_iter(k)
         if eps is not None and stop_test(np.array(hist[-1]), n, rho, *eps):
             stopped = k + 1
             break
@@ -223,7 +225,7 @@ def lasso_admm(H, g, lam, rho, iters, eps=None) -> OracleResult:
                         rows=[(0, m)], cols=[(0, n)], iters=len(hist), stopped_at=stopped)
 
 
-def consensus_admm(H, g, M, lam, rho, iters, eps=None) -> OracleResult:
+def consensus_admm(H, g, M, lam, rho, iters, eps=None, on_iter=None) -> OracleResult:
     """Section III-A: H split by rows into M blocks H_i with data g_i.
 
     u^i <- (H_i^*H_i + rho I)^{-1}(H_i^* g_i + rho (v - s^i))      Eq. (x_solution)
@@ -251,6 +253,8 @@ def consensus_admm(H, g, M, lam, rho, iters, eps=None) -> OracleResult:
         hist.append((rp2, rd2, sum(_sq(u[i]) for i in range(M)), M * _sq(v_new),
                      sum(_sq(s[i]) for i in range(M))))
         v = v_new
+        if on_iter is not None:
+            on_iter(k)
         if eps is not None and stop_test(np.array(hist[-1]), M * n, rho, *eps):
             stopped = k + 1
             break
@@ -259,7 +263,7 @@ def consensus_admm(H, g, M, lam, rho, iters, eps=None) -> OracleResult:
                         rows=rows, cols=[(0, n)], iters=len(hist), stopped_at=stopped)
 
 
-def sectioning_admm(H, g, N, lam, rho, iters, eps=None) -> OracleResult:
+def sectioning_admm(H, g, N, lam, rho, iters, eps=None, on_iter=None) -> OracleResult:
     """Section III-B: H split by columns into N blocks H_j, u into segments u_j.
 
     g_j   = g - sum_{q != j} H_q u_q            (previous iterate)   Eq. (g_columns)
@@ -295,6 +299,8 @@ def sectioning_admm(H, g, N, lam, rho, iters, eps=None) -> OracleResult:
         hist.append((rp2, rd2, sum(_sq(x) for x in u_new), sum(_sq(x) for x in v_new),
                      sum(_sq(x) for x in s)))
         u, v = u_new, v_new
+        if on_iter is not None:
+            on_iter(k)
         if eps is not None and stop_test(np.array(hist[-1]), n, rho, *eps):
             stopped = k + 1
             break
@@ -306,7 +312,7 @@ def sectioning_admm(H, g, N, lam, rho, iters, eps=None) -> OracleResult:
                         stopped_at=stopped)
 
 
-def cs_admm(H, g, M, N, lam, rho, iters, eps=None) -> OracleResult:
+def cs_admm(H, g, M, N, lam, rho, iters, eps=None, on_iter=None) -> OracleResult:
     """Section III-C: M x N blocks H_ij; replicas u_j^i of each segment j.
 
     g_ij   = g_i - sum_{q != j} H_iq u_q^i      (previous iterate)   Eq. (g_rows_columns)
@@ -350,6 +356,8 @@ def cs_admm(H, g, M, N, lam, rho, iters, eps=None) -> OracleResult:
                      M * sum(_sq(x) for x in v_new),
                      sum(_sq(s[i][j]) for i in range(M) for j in range(N))))
         u, v = u_new, v_new
+        if on_iter is not None:
+            on_iter(k)
         if eps is not None and stop_test(np.array(hist[-1]), M * n, rho, *eps):
             stopped = k + 1
             break
@@ -365,15 +373,18 @@ def cs_admm(H, g, M, N, lam, rho, iters, eps=None) -> OracleResult:
                         iters=len(hist), stopped_at=stopped)
 
 
-def run_split(H, g, row_blocks, col_blocks, lam, rho, iters, eps=None) -> OracleResult:
-    """Dispatch on (M, N): (1,1) unsplit, (M,1) consensus, (1,N) sectioning, else C&S."""
+def run_split(H, g, row_blocks, col_blocks, lam, rho, iters, eps=None, on_iter=None) -> OracleResult:
+    """Dispatch on (M, N): (1,1) unsplit, (M,1) consensus, (1,N) sectioning, else C&S.
+
+    ``on_iter(k)``, when given, is called after iteration k (0-based) completes;
+    it observes only (the CPU baseline times iterations with it)."""
     if row_blocks == 1 and col_blocks == 1:
-        return lasso_admm(H, g, lam, rho, iters, eps)
+        return lasso_admm(H, g, lam, rho, iters, eps, on_iter)
     if col_blocks == 1:
-        return consensus_admm(H, g, row_blocks, lam, rho, iters, eps)
+        return consensus_admm(H, g, row_blocks, lam, rho, iters, eps, on_iter)
     if row_blocks == 1:
-        return sectioning_admm(H, g, col_blocks, lam, rho, iters, eps)
-    return cs_admm(H, g, row_blocks, col_blocks, lam, rho, iters, eps)
+        return sectioning_admm(H, g, col_blocks, lam, rho, iters, eps, on_iter)
+    return cs_admm(H, g, row_blocks, col_blocks, lam, rho, iters, eps, on_iter)
 
 
 # ----------------------------------------------------------------------------

@@ -22,7 +22,7 @@ ADMM_C64, ADMM_C128 = 0, 1
 ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS = 1, 2, 3, 4
 ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ADMM_OPT_L2_PREFETCH_BYTES, ADMM_OPT_RECORD_ITERS = 5, 6, 7, 8
 ADMM_FORM_LEMMA, ADMM_FORM_DIRECT, ADMM_FORM_AUTO = 0, 1, 2
-ABI_VERSION = 4
+ABI_VERSION = 5
 
 
 class AdmmInfo(ctypes.Structure):
@@ -45,7 +45,7 @@ class AdmmPlan(ctypes.Structure):
     _fields_ = [("ctas", c_int32), ("slab_cols", c_int32), ("chunks", c_int32),
                 ("box_cols", c_int32), ("boxes_per_row", c_int32), ("rows_per_stage", c_int32),
                 ("stages", c_int32), ("smem_bytes", c_int32), ("max_blocks_per_slab", c_int32),
-                ("ld", c_int64)]
+                ("ld", c_int64), ("groups", c_int32), ("reserved", c_int32)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -120,6 +120,8 @@ SIGNATURES = {
     "admm_batch_adjoint": (c_int32, [c_void_p, c_void_p, c_void_p, c_void_p]),
     "admm_batch_status": (c_int32, [c_void_p, c_void_p]),
     "admm_batch_record": (c_int32, [c_void_p, c_int32]),
+    "admm_batch_set_lambda": (c_int32, [c_void_p, ctypes.POINTER(c_double)]),
+    "admm_batch_set_rho": (c_int32, [c_void_p, c_double, c_void_p]),
     "admm_batch_tune": (c_int32, [c_void_p, c_void_p]),
     "admm_batch_backward": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double),
                                       ctypes.POINTER(c_double), c_void_p]),
@@ -408,6 +410,15 @@ def admm_batch_destroy(h: int) -> None:
 
 def admm_batch_record(h: int, iters: int) -> None:
     _bcheck(load().admm_batch_record(h, iters), h)
+
+
+def admm_batch_set_lambda(h: int, lam) -> None:
+    arr = (c_double * len(lam))(*[float(x) for x in lam])
+    _bcheck(load().admm_batch_set_lambda(h, arr), h)
+
+
+def admm_batch_set_rho(h: int, rho: float, stream=None) -> None:
+    _bcheck(load().admm_batch_set_rho(h, float(rho), _stream(stream)), h)
 
 
 def admm_batch_backward(h: int, batch: int, dV, dG, stream=None):

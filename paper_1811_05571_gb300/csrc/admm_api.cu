@@ -178,7 +178,7 @@ void balanced_offsets(int64_t total, int parts, std::vector<int>& off) {
 
 int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_off,
               const std::vector<int>& col_off, int num_sms, int smem_limit, Plan& pl,
-              const char** why, int force_chunks) {
+              const char** why, int force_chunks, int max_groups) {
     *why = "";
     if (num_sms < 1 || smem_limit < 16384) {
         *why = "bad device limits";
@@ -275,6 +275,11 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
         *why = "a CTA column slab would touch more than 4 column blocks (column blocks too narrow)";
         return ADMM_EUNSUPPORTED;
     }
+    // slabs of more than 256 pairs: two column groups of consumer warps, each
+    // with half the slab (8 chunks per lane instead of 16); not in
+    // multi-problem launches, which share one single-group kernel instance
+    pl.npmax = pl.wmax / 2;
+    pl.groups = (max_groups >= 2 && pl.npmax > 256) ? 2 : 1;
     int most = 1;
     for (int j = 0; j < N; ++j) {
         if (pl.j_cta_hi[j] < pl.j_cta_lo[j]) {
@@ -292,11 +297,10 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
         while (need_groups < 32 && static_cast<int64_t>(need_groups) * warps < items) need_groups *= 2;
         const int l_round = 32 / need_groups;
         int l_regs = 1;
-        while (l_regs < 32 && l_regs * 16 < most) l_regs *= 2;
+        while (l_regs < 32 && l_regs * 16 < most * pl.groups) l_regs *= 2;
         pl.red_lanes = std::max(l_regs, l_round);
     }
-    pl.npmax = pl.wmax / 2;
-    const int need = (pl.npmax + 31) / 32;
+    const int need = (((pl.npmax + pl.groups - 1) / pl.groups) + 31) / 32;
     int ch = 1;
     while (ch < need) ch *= 2;
     while (ch < force_chunks) ch *= 2;   // a multi-problem launch shares one kernel instance
@@ -325,9 +329,10 @@ int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_of
     // shared memory: fixed regions, then the deepest ring that fits
     const int ws = pl.njs * pl.ws_rows * 8;
     const int rs = pl.kpmax * 8;   // r_b, and the same again for gt_b
-    pl.red_single = 2 * kConsumerWarps * npitch * 16 > 64 * 1024;
+    const int wg = kConsumerWarps / pl.groups;   // warps summed per pair in the second pass
+    pl.red_single = 2 * wg * npitch * 16 > 64 * 1024;
     pl.sigma_global = static_cast<int64_t>(M) * npitch * 16 > 32 * 1024;
-    const int red = (pl.red_single ? 1 : 2) * kConsumerWarps * npitch * 16;
+    const int red = (pl.red_single ? 1 : 2) * wg * npitch * 16;
     const int sigma = pl.sigma_global ? 0 : M * npitch * 16;
     const int misc = 1024;
     const int fixed = round_up(ws, 128) + 2 * round_up(rs, 128) + round_up(red, 128) +
@@ -908,6 +913,7 @@ void fill_args(admm_t* h, const Plan& pl, const PlanBuffers& b, int iters, int c
     a.ws_rows = pl.ws_rows;
     a.sigma_global = pl.sigma_global ? 1 : 0;
     a.red_single = pl.red_single ? 1 : 0;
+    a.pgroups = pl.groups;
     a.rho = static_cast<float>(h->rho);
     a.rho_d = h->rho;
     a.kappa = static_cast<float>(h->lambda / (h->M * h->rho));
@@ -1140,6 +1146,8 @@ int admm_plan(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks, int3
     out->smem_bytes = pl.smem;
     out->max_blocks_per_slab = pl.njs;
     out->ld = pl.ld;
+    out->groups = pl.groups;
+    out->reserved = 0;
     if (cta_cols) {
         for (int c = 0; c < pl.P; ++c) {
             cta_cols[4 * c] = pl.cta_beg[c];
@@ -1261,7 +1269,7 @@ int admm_setup_form(admm_t** out, const void* H, const void* g, int64_t m, int64
               dalloc(&h->v, ld) == cudaSuccess && dalloc(&h->s, ld * row_blocks) == cudaSuccess &&
               dalloc(&h->u, ld * row_blocks) == cudaSuccess && dalloc(&h->ghat, 2 * Nm) == cudaSuccess &&
               dalloc(&h->gt, scratch) == cudaSuccess && dalloc(&h->r, scratch) == cudaSuccess &&
-              dalloc(&h->w, scratch) == cudaSuccess && dalloc(&h->part, scratch * pl.P) == cudaSuccess &&
+              dalloc(&h->w, scratch) == cudaSuccess && dalloc(&h->part, scratch * pl.P * pl.groups) == cudaSuccess &&
               dalloc(&h->kinv, kel) == cudaSuccess &&
               dalloc(&h->kinv_off_d, h->kinv_off.size()) == cudaSuccess &&
               dalloc(&h->res_part, static_cast<size_t>(pl.P) * 8) == cudaSuccess &&
@@ -1338,9 +1346,9 @@ int admm_setup_form(admm_t** out, const void* H, const void* g, int64_t m, int64
         code = encode_tensor_map(h);
         if (code) return bail(code);
         // opt into the device maximum: several handles share one kernel instance
-        SETUP_CK(admm::prepare_iterate(pl.chunks, h->smem_optin));
+        SETUP_CK(admm::prepare_iterate(pl.chunks, h->smem_optin, pl.groups));
         int per_sm = 0;
-        admm::max_coresident_iterate(pl.chunks, pl.smem, &per_sm);
+        admm::max_coresident_iterate(pl.chunks, pl.smem, &per_sm, pl.groups);
         if (per_sm * h->num_sms < pl.P)
             return bail(fail(h, ADMM_EUNSUPPORTED, "iteration kernel cannot keep %d CTAs resident", pl.P));
     } else {
@@ -1904,7 +1912,7 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
         for (int P = std::min(pmax[q], std::max(1, (ld + 511) / 512)); P <= pmax[q]; ++P) {
             Plan pl;
             const char* why = "";
-            if (admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P, limit, pl, &why) == ADMM_OK &&
+            if (admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P, limit, pl, &why, 0, 1) == ADMM_OK &&
                 pl.P == P) {
                 pmin[q] = P;
                 break;
@@ -1969,11 +1977,11 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
             admm_t* h = handles[w.probs[t]];
             Plan pl;
             const char* why = "";
-            int code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pl, &why);
+            int code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pl, &why, 0, 1);
             // the planner may settle on fewer CTAs than offered; try fewer offers until one fits
             while (code != ADMM_OK && P[t] > pmin[w.probs[t]]) {
                 --P[t];
-                code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pl, &why);
+                code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pl, &why, 0, 1);
             }
             if (code) return bail(gfail(g, code, "problem %d: %s", w.probs[t], why));
             ch = std::max(ch, pl.chunks);
@@ -1989,7 +1997,7 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
             admm_group_t::Prob& pr = g->probs[q];
             pr.h = h;
             const char* why = "";
-            int code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pr.pl, &why, ch);
+            int code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pr.pl, &why, ch, 1);
             if (code) return bail(gfail(g, code, "problem %d with %d chunks: %s", q, ch, why));
             w.smem = std::max(w.smem, pr.pl.smem);
             for (int c = 0; c < pr.pl.P; ++c) {

@@ -605,6 +605,49 @@ int admm_batch_tune(admm_batch_t* h, void* stream) {
     return check_status(h, s);
 }
 
+int admm_batch_set_lambda(admm_batch_t* h, const double* lambda) {
+    if (!h || !lambda) return h ? bfail(h, ADMM_EINVAL, "lambda is NULL") : ADMM_EINVAL;
+    for (int b = 0; b < h->B; ++b)
+        if (!(lambda[b] >= 0.0) || !std::isfinite(lambda[b]))
+            return bfail(h, ADMM_EINVAL, "lambda[%d] must be finite and >= 0", b);
+    std::vector<float> kap(h->B);
+    for (int b = 0; b < h->B; ++b) kap[b] = static_cast<float>(lambda[b] / (h->M * h->rho));
+    BCK(h, cudaDeviceSynchronize());
+    BCK(h, cudaMemcpy(h->kappa, kap.data(), h->B * sizeof(float), cudaMemcpyHostToDevice));
+    h->lam.assign(lambda, lambda + h->B);
+    h->rec_valid = false;
+    return ADMM_OK;
+}
+
+int admm_batch_set_rho(admm_batch_t* h, double rho, void* stream) {
+    if (!h) return ADMM_EINVAL;
+    if (!(rho > 0.0) || !std::isfinite(rho)) return bfail(h, ADMM_EINVAL, "rho must be finite and > 0");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    BCK(h, cudaDeviceSynchronize());
+    int code = admm_set_rho(h->inner, rho, stream);
+    if (code) return bfail(h, code, "refactorisation failed: %s", admm_last_error(h->inner));
+    if (admm::view_handle(h->inner, &h->hv) != ADMM_OK) return bfail(h, ADMM_EINVAL, "inner handle view failed");
+    const int P = h->M * h->N;
+    BCK(h, launch_pack_kinv(h->hv.kinv16, h->hv.kinv_off, h->hv.kinv_pitch, h->hv.row_off, P, h->N, h->mimax,
+                            h->kr, h->Kpack, h->kscale, st));
+    const double old = h->rho;
+    h->rho = rho;
+    h->st.rho = static_cast<float>(rho);
+    std::vector<float> kap(h->B);
+    for (int b = 0; b < h->B; ++b) kap[b] = static_cast<float>(h->lam[b] / (h->M * rho));
+    BCK(h, cudaMemcpyAsync(h->kappa, kap.data(), h->B * sizeof(float), cudaMemcpyHostToDevice, st));
+    // the unscaled duals rho s are kept: s <- s rho_old / rho_new
+    BCK(h, admm::launch_scale(h->S, static_cast<int64_t>(h->M) * h->B * h->n, static_cast<float>(old / rho), st));
+    BCK(h, cudaStreamSynchronize(st));
+    h->rec_valid = false;
+    // the captured iteration carries rho as a kernel argument: capture it again
+    if (h->exec) cudaGraphExecDestroy(h->exec);
+    if (h->graph) cudaGraphDestroy(h->graph);
+    h->exec = nullptr;
+    h->graph = nullptr;
+    return check_status(h, st);
+}
+
 int admm_batch_record(admm_batch_t* h, int32_t iters) {
     if (!h || iters < 0 || iters > (1 << 20)) return h ? bfail(h, ADMM_EINVAL, "bad record length") : ADMM_EINVAL;
     BCK(h, cudaDeviceSynchronize());

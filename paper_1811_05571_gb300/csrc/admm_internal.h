@@ -25,6 +25,7 @@ struct Plan {
     int wmax = 0;         // widest slab (columns, even)
     int npmax = 0;        // widest slab in column pairs
     int chunks = 0;       // per-lane 32-pair chunks (template width)
+    int groups = 1;       // column groups of consumer warps per CTA (2: each takes half the slab)
     int nsub = 0;         // TMA boxes per slab row
     int wbox = 0;         // TMA box width (columns, even, <= 256)
     int R = 0;            // rows per stage (fixed by the chunk count)
@@ -62,10 +63,11 @@ struct Plan {
     std::vector<int> solve_lo;  // P+1 split of the N*m factor-apply rows
 };
 
-// Returns ADMM_OK, ADMM_EINVAL or ADMM_EUNSUPPORTED; fills `plan`.
+// Returns ADMM_OK, ADMM_EINVAL or ADMM_EUNSUPPORTED; fills `plan`.  Multi-problem
+// launches pass force_chunks (their shared instance) and max_groups = 1.
 int make_plan(int64_t m, int64_t n, int M, int N, const std::vector<int>& row_off,
               const std::vector<int>& col_off, int num_sms, int smem_limit, Plan& plan,
-              const char** why, int force_chunks = 0);
+              const char** why, int force_chunks = 0, int max_groups = 2);
 
 void balanced_offsets(int64_t total, int parts, std::vector<int>& off);
 
@@ -119,6 +121,7 @@ struct IterArgs {
     int mimax, kpmax;
     int off_ring, off_full, off_empty, off_ws, off_rs, off_gs, off_red, off_sigma, off_misc;
     int red_lanes, ws_all, ws_rows, sigma_global, red_single;
+    int pgroups;          // column groups per CTA (1 or 2): partial products per row = P * pgroups
     float rho, kappa, inv_M;
     double rho_d;
     const int* row_off;
@@ -201,8 +204,8 @@ int rows_per_stage(int chunks, bool f16 = false);
 cudaError_t launch_iterate(const CUtensorMap& tmap, const IterArgs& a, int chunks, int smem,
                            cudaStream_t stream, bool f16 = false);
 // Opt the kernel instances into `smem` bytes of dynamic shared memory.
-cudaError_t prepare_iterate(int chunks, int smem);
-int max_coresident_iterate(int chunks, int smem, int* per_sm);
+cudaError_t prepare_iterate(int chunks, int smem, int groups = 1);
+int max_coresident_iterate(int chunks, int smem, int* per_sm, int groups = 1);
 
 // ---- setup kernels (admm_factor.cu) ------------------------------------------
 

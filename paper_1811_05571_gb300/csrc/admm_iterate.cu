@@ -282,12 +282,20 @@ struct RowsOf {
     static constexpr int value = F16 ? (2 * base < 64 ? 2 * base : 64) : base;
 };
 
-template <int CH, bool F16>
+// G column groups: the consumer warps split into G groups of kConsumerWarps/G
+// warps; group q covers the q-th of G contiguous shares of the slab's pairs
+// (so a lane holds CH chunks of a share instead of the whole slab), and the
+// warps of a group take the rows of every stage in turn.  Each group's row
+// sums of the first pass are separate partial products (P * G per row).
+template <int CH, bool F16, int G>
 struct Consumer {
+    static constexpr int kWG = kConsumerWarps / G;    // warps per column group
     static constexpr int kR = RowsOf<CH, F16>::value;  // rows per stage
-    static constexpr int kRPW = kR / kConsumerWarps;  // rows per warp per stage
+    static constexpr int kRPW = kR / kWG;             // rows per warp per stage
     static constexpr int kWin = 8 / kRPW;             // stages per 8-row reduction window
     static constexpr bool kPrefetch = CH <= 4;        // keep v and the next s_i in registers
+    static_assert(kConsumerWarps % G == 0 && kR % kWG == 0 && kRPW <= 8 && 8 % kRPW == 0,
+                  "rows per stage must split evenly over the warps of a group");
 
     const IterArgs& a;
     unsigned char* smem;
@@ -296,6 +304,7 @@ struct Consumer {
     uint64_t* empty;
     const unsigned char* ring;
     int tid, warp, lane, cta;
+    int grp, wg, pg0;     // column group, warp within it, first pair of its share
     int c_beg, npairs, jlo, nj, own0, own1, npmax;
     uint32_t valid;       // bit k: pair lane + 32k lies in this slab
     uint32_t owned;       // bit 2k+h: column h of pair lane + 32k is owned by this CTA
@@ -312,8 +321,13 @@ struct Consumer {
         warp = tid >> 5;
         lane = tid & 31;
         cta = cta_index;
+        grp = warp / kWG;
+        wg = warp - grp * kWG;
         c_beg = a.cta_col[cta];
         npairs = (a.cta_end[cta] - c_beg) >> 1;
+        const int share = (npairs + G - 1) / G;
+        pg0 = min(npairs, grp * share);
+        const int pg1 = min(npairs, pg0 + share);
         jlo = a.cta_jlo[cta];
         nj = a.cta_nj[cta];
         own0 = a.cta_own0[cta];
@@ -328,11 +342,11 @@ struct Consumer {
         const int shift = F16 ? (c_beg & 3) : 0;
 #pragma unroll
         for (int k = 0; k < CH; ++k) {
-            const int p = lane + 32 * k;
-            const int rel = p < npairs ? 2 * p + shift : shift;
+            const int p = pg0 + lane + 32 * k;
+            const int rel = p < pg1 ? 2 * p + shift : shift;
             const int sb = rel / a.wbox;
             soff[k] = sb * a.sub_bytes + (rel - sb * a.wbox) * (F16 ? 4 : 8);
-            if (p < npairs) {
+            if (p < pg1) {
                 valid |= 1u << k;
                 const int c0 = c_beg + 2 * p;
                 uint64_t bits = 0;
@@ -354,7 +368,10 @@ struct Consumer {
     __device__ __forceinline__ int jl_of(int k, int h) const {
         return static_cast<int>((jl >> (4 * k + 2 * h)) & 3u);
     }
-    __device__ __forceinline__ int col_of(int k) const { return c_beg + 2 * (lane + 32 * k); }
+    __device__ __forceinline__ int col_of(int k) const { return c_beg + 2 * (pg0 + lane + 32 * k); }
+    // partial-product slot of this CTA's column group, and their count per row
+    __device__ __forceinline__ int part_slot() const { return cta * G + grp; }
+    __device__ __forceinline__ size_t part_pitch() const { return static_cast<size_t>(a.P) * G; }
 
     // one 16-byte complex pair of H (FP16 storage: 8 bytes, converted to FP32)
     __device__ __forceinline__ float4 load_pair(const unsigned char* rowp, int k) const {
@@ -455,7 +472,7 @@ struct Consumer {
 #pragma unroll
                         for (int q = 0; q < kRPW; ++q) {
                             const int v = wi * kRPW + q;
-                            const unsigned char* rowp = buf + (warp + kConsumerWarps * q) * rowpitch;
+                            const unsigned char* rowp = buf + (wg + kWG * q) * rowpitch;
 #pragma unroll
                             for (int k = 0; k < CH; ++k) {
                                 // pairs outside the slab have z = 0
@@ -477,13 +494,13 @@ struct Consumer {
                 float2 sum = butterfly8(val, lane);
                 const int v = lane >> 2;
                 const int wi = v / kRPW, q = v - wi * kRPW;
-                const int row = r0 + (b0 + wi) * kR + warp + kConsumerWarps * q;
+                const int row = r0 + (b0 + wi) * kR + wg + kWG * q;
                 if (F16) {
                     const float sc = row_scale(min(row, a.m - 1));
                     sum = make_float2(sum.x * sc, sum.y * sc);
                 }
                 if ((lane & 3) == 0 && b0 + wi < nb && row < r1)
-                    stcg2(a.part + (static_cast<size_t>(jlo) * a.m + row) * a.P + cta, sum);
+                    stcg2(a.part + (static_cast<size_t>(jlo) * a.m + row) * part_pitch() + part_slot(), sum);
             }
         }
     }
@@ -509,8 +526,8 @@ struct Consumer {
                 const unsigned char* buf = acquire_stage();
 #pragma unroll
                 for (int q = 0; q < kRPW; ++q) {
-                    const int row = y + warp + kConsumerWarps * q;
-                    const unsigned char* rowp = buf + (warp + kConsumerWarps * q) * rowpitch;
+                    const int row = y + wg + kWG * q;
+                    const unsigned char* rowp = buf + (wg + kWG * q) * rowpitch;
                     for (int jj = 0; jj < nj; ++jj) {
                         float2 acc = make_float2(0.f, 0.f);
 #pragma unroll
@@ -528,7 +545,8 @@ struct Consumer {
                             acc = make_float2(acc.x * sc, acc.y * sc);
                         }
                         if (lane == 0 && row < r1)
-                            stcg2(a.part + (static_cast<size_t>(jlo + jj) * a.m + row) * a.P + cta, acc);
+                            stcg2(a.part + (static_cast<size_t>(jlo + jj) * a.m + row) * part_pitch() + part_slot(),
+                                  acc);
                     }
                 }
                 release_stage();
@@ -558,8 +576,9 @@ struct Consumer {
             if (idx < total) {
                 j = idx / a.m;
                 row = idx - j * a.m;
-                const int lo = a.j_cta_lo[j], hi = a.j_cta_hi[j];
-                const float2* pp = a.part + static_cast<size_t>(idx) * a.P;
+                // every column group of the CTAs meeting block j left one partial
+                const int lo = a.j_cta_lo[j] * G, hi = a.j_cta_hi[j] * G + G - 1;
+                const float2* pp = a.part + static_cast<size_t>(idx) * part_pitch();
                 // up to 16 loads per lane issued before any is summed
                 for (int c0 = lo + gl; c0 <= hi; c0 += 16 * L) {
                     float2 x[16];
@@ -711,7 +730,7 @@ struct Consumer {
                 const unsigned char* buf = acquire_stage();
 #pragma unroll
                 for (int q = 0; q < kRPW; ++q) {
-                    const int rl = warp + kConsumerWarps * q;
+                    const int rl = wg + kWG * q;
                     const bool ok = y + rl < r1;
                     const unsigned char* rowp = buf + rl * rowpitch;
                     if (!MULTI) {
@@ -746,19 +765,20 @@ struct Consumer {
                 release_stage();
             }
             // conj(h) w = (h.re w.re + h.im w.im, h.re w.im - h.im w.re); sum over warps
-            float4* rb = red + static_cast<size_t>(a.red_single ? 0 : (bi & 1)) * kConsumerWarps * npmax;
+            // a group's warps sum through kWG rows of npmax pairs (the groups' pairs are disjoint)
+            float4* rb = red + static_cast<size_t>(a.red_single ? 0 : (bi & 1)) * kWG * npmax;
             if (a.red_single) csync();   // the previous replica's sums have been read
 #pragma unroll
             for (int k = 0; k < CH; ++k)
                 if (is_valid(k))
-                    rb[warp * npmax + lane + 32 * k] =
+                    rb[wg * npmax + pg0 + lane + 32 * k] =
                         make_float4(aA0[k].x + aB0[k].y, aB0[k].x - aA0[k].y,
                                     aA1[k].x + aB1[k].y, aB1[k].x - aA1[k].y);
             csync();
             for (int p = tid; p < npairs; p += kConsumerThreads) {
                 float4 s = rb[p];
 #pragma unroll
-                for (int wq = 1; wq < kConsumerWarps; ++wq) s = s + rb[wq * npmax + p];
+                for (int wq = 1; wq < kWG; ++wq) s = s + rb[wq * npmax + p];
                 if (a.sigma_global) {
                     // an edge pair's other column belongs to the neighbouring CTA
                     const int c = c_beg + 2 * p;
@@ -910,7 +930,7 @@ struct Consumer {
 };
 
 // One CTA of a problem's persistent iteration: local CTA index `cta` of a.P.
-template <int CH, bool F16>
+template <int CH, bool F16, int G>
 __device__ __forceinline__ void iterate_body(const CUtensorMap* tmap, const IterArgs& a, int cta,
                                              unsigned char* smem) {
     uint64_t* full = reinterpret_cast<uint64_t*>(smem + a.off_full);
@@ -936,15 +956,15 @@ __device__ __forceinline__ void iterate_body(const CUtensorMap* tmap, const Iter
             producer(tmap, a, full, empty, misc, ring, a.cta_col[cta]);
         return;
     }
-    Consumer<CH, F16> c(a, smem, misc, full, empty, ring, cta);
+    Consumer<CH, F16, G> c(a, smem, misc, full, empty, ring, cta);
     c.run();
 }
 
-template <int CH, bool F16>
+template <int CH, bool F16, int G>
 __global__ void __launch_bounds__(kIterThreads, 1)
     iterate_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ IterArgs a) {
     extern __shared__ __align__(1024) unsigned char smem[];
-    iterate_body<CH, F16>(&tmap, a, blockIdx.x, smem);
+    iterate_body<CH, F16, G>(&tmap, a, blockIdx.x, smem);
 }
 
 // Several problems in one cooperative launch: CTA b runs local CTA cta_local[b]
@@ -957,31 +977,37 @@ __global__ void __launch_bounds__(kIterThreads, 1)
                          const int* __restrict__ cta_local) {
     extern __shared__ __align__(1024) unsigned char smem[];
     const int p = cta_prob[blockIdx.x];
-    iterate_body<CH, F16>(&gp.tmap[p], gp.a[p], cta_local[blockIdx.x], smem);
+    iterate_body<CH, F16, 1>(&gp.tmap[p], gp.a[p], cta_local[blockIdx.x], smem);
 }
 
 __global__ void __launch_bounds__(32) finalize_kernel(const __grid_constant__ IterArgs a, long long kabs) {
     finalize_record(a, kabs, threadIdx.x & 31, false);
 }
 
-template <int CH, bool F16>
+template <int CH, bool F16, int G>
 void* kernel_fn() {
-    return reinterpret_cast<void*>(&iterate_kernel<CH, F16>);
+    return reinterpret_cast<void*>(&iterate_kernel<CH, F16, G>);
 }
 
+// kernel instances: one column group with 1-16 chunks per lane, or two column
+// groups of 8 chunks (slabs of more than 256 pairs)
 template <bool F16>
-void* pick_t(int chunks) {
+void* pick_t(int chunks, int groups) {
+    if (groups == 2) return chunks == 8 ? kernel_fn<8, F16, 2>() : nullptr;
+    if (groups != 1) return nullptr;
     switch (chunks) {
-        case 1: return kernel_fn<1, F16>();
-        case 2: return kernel_fn<2, F16>();
-        case 4: return kernel_fn<4, F16>();
-        case 8: return kernel_fn<8, F16>();
-        case 16: return kernel_fn<16, F16>();
+        case 1: return kernel_fn<1, F16, 1>();
+        case 2: return kernel_fn<2, F16, 1>();
+        case 4: return kernel_fn<4, F16, 1>();
+        case 8: return kernel_fn<8, F16, 1>();
+        case 16: return kernel_fn<16, F16, 1>();
         default: return nullptr;
     }
 }
 
-void* pick(int chunks, bool f16 = false) { return f16 ? pick_t<true>(chunks) : pick_t<false>(chunks); }
+void* pick(int chunks, bool f16 = false, int groups = 1) {
+    return f16 ? pick_t<true>(chunks, groups) : pick_t<false>(chunks, groups);
+}
 
 template <int CH, bool F16>
 void* group_fn() {
@@ -1015,9 +1041,9 @@ int rows_per_stage(int chunks, bool f16) {
     }
 }
 
-cudaError_t prepare_iterate(int chunks, int smem) {
+cudaError_t prepare_iterate(int chunks, int smem, int groups) {
     for (int f = 0; f < 2; ++f) {
-        void* fn = pick(chunks, f == 1);
+        void* fn = pick(chunks, f == 1, groups);
         if (!fn) return cudaErrorInvalidValue;
         const cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
         if (e != cudaSuccess) return e;
@@ -1025,8 +1051,8 @@ cudaError_t prepare_iterate(int chunks, int smem) {
     return cudaSuccess;
 }
 
-int max_coresident_iterate(int chunks, int smem, int* per_sm) {
-    void* fn = pick(chunks);
+int max_coresident_iterate(int chunks, int smem, int* per_sm, int groups) {
+    void* fn = pick(chunks, false, groups);
     if (!fn) return 0;
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fn, kIterThreads, smem) != cudaSuccess)
@@ -1045,7 +1071,7 @@ cudaError_t launch_finalize(const IterArgs& a, long long kabs, cudaStream_t stre
 // exit, so the launch is refused instead.
 bool stage_geometry_ok(const IterArgs& a, int chunks, bool f16) {
     const int eb = f16 ? 4 : 8;
-    return a.elem_bytes == eb && a.R == rows_per_stage(chunks, f16) && a.wbox >= 2 && a.wbox <= 256 &&
+    return (a.pgroups == 1 || (a.pgroups == 2 && chunks == 8)) && a.elem_bytes == eb && a.R == rows_per_stage(chunks, f16) && a.wbox >= 2 && a.wbox <= 256 &&
            (a.wbox * eb) % 16 == 0 && a.nsub >= 1 && a.sub_bytes == a.R * a.wbox * eb &&
            a.stage_bytes == a.sub_bytes * a.nsub && a.stage_bytes <= a.stage_stride &&
            a.nstages >= 2 && a.nstages <= 8 && (!f16 || a.scales != nullptr);
@@ -1054,7 +1080,7 @@ bool stage_geometry_ok(const IterArgs& a, int chunks, bool f16) {
 cudaError_t launch_iterate(const CUtensorMap& tmap, const IterArgs& a, int chunks, int smem,
                            cudaStream_t stream, bool f16) {
     if (!stage_geometry_ok(a, chunks, f16)) return cudaErrorInvalidValue;
-    void* fn = pick(chunks, f16);
+    void* fn = pick(chunks, f16, a.pgroups);
     if (!fn) return cudaErrorInvalidValue;
     void* args[] = {const_cast<CUtensorMap*>(&tmap), const_cast<IterArgs*>(&a)};
     return cudaLaunchCooperativeKernel(fn, dim3(a.P), dim3(kIterThreads), args,
@@ -1071,7 +1097,9 @@ cudaError_t launch_group(const GroupParams& gp, const int* cta_prob, const int* 
     return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kIterThreads), args, static_cast<size_t>(smem), stream);
 }
 
-bool group_stage_geometry_ok(const IterArgs& a, int chunks, bool f16) { return stage_geometry_ok(a, chunks, f16); }
+bool group_stage_geometry_ok(const IterArgs& a, int chunks, bool f16) {
+    return a.pgroups == 1 && stage_geometry_ok(a, chunks, f16);
+}
 
 }  // namespace admm
 

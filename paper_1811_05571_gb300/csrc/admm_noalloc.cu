@@ -164,7 +164,7 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
     const size_t x_gt = cv.take(Nm * sizeof(float2));
     const size_t x_r = cv.take(Nm * sizeof(float2));
     const size_t x_w = cv.take(Nm * sizeof(float2));
-    const size_t x_part = cv.take(Nm * pl.P * sizeof(float2));
+    const size_t x_part = cv.take(Nm * pl.P * pl.groups * sizeof(float2));
     const size_t x_res = cv.take(static_cast<size_t>(pl.P) * 8 * sizeof(double));
     const size_t x_hist = cv.take(5 * sizeof(double));
     const size_t x_kdone = cv.take(sizeof(long long));
@@ -242,7 +242,7 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
         return noalloc_fail(ADMM_ECUDA, "cuTensorMapEncodeTiled failed");
 
     if (iters > 0) {
-        NA_CK(admm::prepare_iterate(pl.chunks, smem_optin));
+        NA_CK(admm::prepare_iterate(pl.chunks, smem_optin, pl.groups));
         admm::IterArgs a;
         std::memset(&a, 0, sizeof a);
         a.m = static_cast<int>(m);
@@ -276,6 +276,7 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
         a.ws_rows = pl.ws_rows;
         a.sigma_global = pl.sigma_global ? 1 : 0;
         a.red_single = pl.red_single ? 1 : 0;
+        a.pgroups = pl.groups;
         a.rho = static_cast<float>(rho);
         a.rho_d = rho;
         a.kappa = static_cast<float>(lambda / (M * rho));

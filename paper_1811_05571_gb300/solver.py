@@ -182,6 +182,21 @@ class BatchSolver:
         self.stream = stream
         self.h = B.admm_batch_setup(H, self.m, self.n, self.M, self.N, self.batch, lam, float(rho),
                                     _dtype_code(H), stream)
+        self.lam = list(lam)
+        self.rho = float(rho)
+
+    def set_lambda(self, lam) -> None:
+        """New per-scene weights (no refactorisation)."""
+        lam = [float(x) for x in lam]
+        if len(lam) != self.batch:
+            raise ValueError("one lambda per scene")
+        B.admm_batch_set_lambda(self.h, lam)
+        self.lam = lam
+
+    def set_rho(self, rho: float) -> None:
+        """New augmented parameter (refactors every block)."""
+        B.admm_batch_set_rho(self.h, float(rho), self.stream)
+        self.rho = float(rho)
 
     def set_g(self, G) -> None:
         G = _contig(G)
@@ -253,43 +268,103 @@ class BatchSolver:
             pass
 
 
+def _push_params(solver, lam_v, rho_v) -> None:
+    """Bring a solver's lambda (list, one per scene) and rho to the given values."""
+    if isinstance(solver, BatchSolver):
+        if lam_v != solver.lam:
+            solver.set_lambda(lam_v)
+        if rho_v != solver.rho:
+            solver.set_rho(rho_v)
+        return
+    info = solver.info()
+    if lam_v[0] != info["lambda"]:
+        solver.set_lambda(lam_v[0])
+    if rho_v != info["rho"]:
+        solver.set_rho(rho_v)
+
+
 def _unrolled_function():
     import torch
 
     class _Unrolled(torch.autograd.Function):
-        """v = ADMM_K(G) for every scene of a BatchSolver; backward runs the
-        library's reverse sweep and leaves dL/dlambda and dL/drho per scene in
-        ``solver.last_param_grads``."""
+        """V = ADMM_K(G; lambda, rho) per scene from the zero state.  The forward
+        runs K recorded iterations, the backward the library's reverse sweep
+        (admm_batch_backward on a BatchSolver, admm_backward on each Solver of
+        a list, one per scene)."""
 
         @staticmethod
-        def forward(ctx, G, solver, iters):
-            solver.record(int(iters))
-            solver.set_g(G.detach().to(torch.complex64).contiguous())
-            solver.iterate(int(iters))
+        def forward(ctx, G, lam, rho, solver, iters):
+            B = G.shape[0]
+            lam_v = [float(x) for x in lam.detach().reshape(-1).cpu().tolist()]
+            if len(lam_v) == 1:
+                lam_v = lam_v * B
+            if len(lam_v) != B:
+                raise ValueError("lam must hold one value per scene or one shared value")
+            rho_v = float(rho.detach().reshape(-1)[0].cpu())
+            Gd = G.detach().to(torch.complex64).contiguous()
+            if isinstance(solver, BatchSolver):
+                _push_params(solver, lam_v, rho_v)
+                solver.record(int(iters))
+                solver.set_g(Gd)
+                solver.iterate(int(iters))
+                V = solver.v()
+            else:
+                if len(solver) != B:
+                    raise ValueError("one Solver per scene")
+                V = torch.empty((B, solver[0].n), dtype=torch.complex64, device=G.device)
+                for b, sv in enumerate(solver):
+                    _push_params(sv, [lam_v[b]], rho_v)
+                    sv.set_g(Gd[b])
+                    sv.record(int(iters))
+                    sv.iterate(int(iters))
+                    sv.v(out=V[b])
             ctx.solver = solver
-            return solver.v()
+            ctx.lam_shape, ctx.lam_dtype, ctx.lam_device = lam.shape, lam.dtype, lam.device
+            ctx.rho_shape, ctx.rho_dtype, ctx.rho_device = rho.shape, rho.dtype, rho.device
+            return V
 
         @staticmethod
         def backward(ctx, dV):
-            dG, dl, dr = ctx.solver.backward(dV.to(torch.complex64).contiguous())
-            ctx.solver.last_param_grads = (dl, dr)
-            return dG, None, None
+            dVc = dV.to(torch.complex64).contiguous()
+            if isinstance(ctx.solver, BatchSolver):
+                dG, dl, dr = ctx.solver.backward(dVc)
+                dl, dr = [float(x) for x in dl], [float(x) for x in dr]
+            else:
+                dG = torch.empty((len(ctx.solver), ctx.solver[0].m), dtype=torch.complex64, device=dV.device)
+                dl, dr = [], []
+                for b, sv in enumerate(ctx.solver):
+                    gg, gl, gr = sv.backward(dVc[b])
+                    dG[b].copy_(gg)
+                    dl.append(float(gl))
+                    dr.append(float(gr))
+            dl_t = torch.tensor(dl, dtype=ctx.lam_dtype)
+            if dl_t.numel() != torch.Size(ctx.lam_shape).numel():
+                dl_t = dl_t.sum()            # one lambda shared by every scene
+            dr_t = torch.tensor(sum(dr), dtype=ctx.rho_dtype)   # rho is shared
+            return (dG, dl_t.reshape(ctx.lam_shape).to(ctx.lam_device),
+                    dr_t.reshape(ctx.rho_shape).to(ctx.rho_device), None, None)
 
     return _Unrolled
 
 
 class UnrolledADMM:
-    """``UnrolledADMM.apply(G, solver, iters)``: the images after `iters`
-    iterations from the zero state as a differentiable function of the
-    measurements G (batch x m); see BatchSolver.record / backward."""
+    """``UnrolledADMM.apply(G, lam, rho, solver, iters)``: the images after
+    `iters` iterations from the zero state (batch x n complex64) as a
+    differentiable function of the measurements G (batch x m complex), the
+    regularisation weights `lam` (real tensor, one per scene or one shared)
+    and the augmented parameter `rho` (real scalar tensor), so that
+    loss.backward() fills G.grad, lam.grad and rho.grad.  `solver` is a
+    BatchSolver (all scenes together on the FP16-encoded H) or a list of
+    Solver handles, one per scene (complex64 or FP16 H).  New lam or rho values
+    are pushed to the solver(s) first (rho refactors)."""
 
     _fn = None
 
     @classmethod
-    def apply(cls, G, solver, iters):
+    def apply(cls, G, lam, rho, solver, iters):
         if cls._fn is None:
             cls._fn = _unrolled_function()
-        return cls._fn.apply(G, solver, iters)
+        return cls._fn.apply(G, lam, rho, solver, iters)
 
 
 class Group:

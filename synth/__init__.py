@@ -9,6 +9,9 @@ parameter); it performs none of the ADMM method's arithmetic.
 from .workloads import (  # noqa: F401
     Problem,
     gaussian_problem,
+    chunked_gaussian_rows,
+    chunked_gaussian_problem,
+    ROWS_PER_DRAW,
     cra_matrix,
     plate_scene,
     noisy_measurements,

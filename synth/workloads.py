@@ -159,6 +159,76 @@ def gaussian_problem(m: int, n: int, nnz: int, seed: int, snr_db: float = 30.0,
 
 
 # ----------------------------------------------------------------------------
+# Gaussian family drawn in independently seeded row chunks (large sizes)
+# ----------------------------------------------------------------------------
+
+ROWS_PER_DRAW = 64
+
+
+def chunked_gaussian_rows(m: int, n: int, seed: int, chunk: int) -> np.ndarray:
+    """Rows [64 c, min(64 c + 64, m)) of H ~ CN(0, 1/m), c = ``chunk``, drawn from
+    default_rng([seed, c]) and rounded to complex64 (returned as complex64)."""
+    rng = np.random.default_rng([seed, chunk])
+    r0 = chunk * ROWS_PER_DRAW
+    r1 = min(m, r0 + ROWS_PER_DRAW)
+    return _complex_normal(rng, (r1 - r0, n), 1.0 / m).astype(np.complex64)
+
+
+def chunked_gaussian_problem(m: int, n: int, nnz: int, seed: int, snr_db: float = 30.0,
+                             lam_frac: float = 0.05, sink=None, threads: int | None = None,
+                             lam: float | None = None):
+    """The Gaussian recipe of ``gaussian_problem`` for matrices too large to draw
+    from one generator in reasonable time: H ~ CN(0, 1/m) i.i.d. in row chunks of
+    64, chunk c from default_rng([seed, c]) (so chunks can be drawn in parallel);
+    the scene from default_rng([seed, 2**30]) in the order support, phases, w;
+    g = Hu + w at exactly ``snr_db`` (FP64 from the complex64 H), rounded to
+    complex64; lam = lam_frac * max|H^H g| in FP64 unless ``lam`` is given.
+
+    ``sink(r0, rows)`` (optional) receives every chunk as it is drawn (from
+    worker threads); otherwise H is kept and returned as one complex64 array.
+    lam needs H, so it is computed only when H is kept.  Returns
+    (H or None, g as complex128, u_true, lam or None)."""
+    from concurrent.futures import ThreadPoolExecutor
+    import os
+    scene = np.random.default_rng([seed, 1 << 30])
+    support = scene.choice(n, size=nnz, replace=False)
+    phases = scene.uniform(0.0, 2.0 * np.pi, size=nnz)
+    u = np.zeros(n, dtype=np.complex128)
+    u[support] = np.exp(1j * phases)
+    chunks = (m + ROWS_PER_DRAW - 1) // ROWS_PER_DRAW
+    cols = np.empty((m, nnz), dtype=np.complex64)
+    H = None if sink is not None else np.empty((m, n), dtype=np.complex64)
+
+    def draw(c):
+        rows = chunked_gaussian_rows(m, n, seed, c)
+        r0 = c * ROWS_PER_DRAW
+        cols[r0:r0 + rows.shape[0]] = rows[:, support]
+        if sink is not None:
+            sink(r0, rows)
+        else:
+            H[r0:r0 + rows.shape[0]] = rows
+
+    workers = threads or min(16, os.cpu_count() or 1)
+    with ThreadPoolExecutor(workers) as ex:
+        list(ex.map(draw, range(chunks)))
+    clean = cols.astype(np.complex128) @ u[support]
+    w = _complex_normal(scene, (m,), 1.0)
+    w *= (np.linalg.norm(clean) / (10.0 ** (snr_db / 20.0))) / np.linalg.norm(w)
+    g = round_to_c64(clean + w)
+    if lam is None and H is not None:
+        def part(c):
+            r0, r1 = c * ROWS_PER_DRAW, min(m, (c + 1) * ROWS_PER_DRAW)
+            blk = H[r0:r1].astype(np.complex128)
+            return np.conj(blk.T @ np.conj(g[r0:r1]))
+        acc = np.zeros(n, dtype=np.complex128)
+        with ThreadPoolExecutor(workers) as ex:
+            for x in ex.map(part, range(chunks)):     # summed in chunk order
+                acc += x
+        lam = float(lam_frac * np.max(np.abs(acc)))
+    return H, g, u, lam
+
+
+# ----------------------------------------------------------------------------
 # CRA-shaped family
 # ----------------------------------------------------------------------------
 
@@ -261,7 +331,7 @@ CONFIG1 = dict(kind="gaussian", m=256, n=4096, nnz=16, seed=0, row_blocks=4, col
                lam_frac=0.05, rho=1.0, iters=300)
 CONFIG2 = dict(kind="cra", m=1440, n=32768, splits=((8, 1), (1, 8), (4, 4)),
                matrix_seed=1, scene_seed=2, lam_frac=0.05, rho_col_blocks=8, iters=300)
-CONFIG3 = dict(kind="gaussian_device", m=8192, n=131072, nnz=400, seed=3, row_blocks=16,
+CONFIG3 = dict(kind="gaussian_chunked", m=8192, n=131072, nnz=400, seed=3, row_blocks=16,
                col_blocks=1, lam_frac=0.05, rho=1.0, fp16_iters=280, polish_iters=20)
 
 # an overdetermined Gaussian problem whose blocks all have m_b >= n_b in the

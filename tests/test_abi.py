@@ -33,7 +33,7 @@ def test_library_loads_and_exports_every_declared_symbol(cuda_lib):
 
 def test_abi_version_and_strerror(cuda_lib):
     import paper_1811_05571_gb300 as P
-    assert P.admm_abi_version() == P.ABI_VERSION == 4
+    assert P.admm_abi_version() == P.ABI_VERSION == 5
     for code in range(0, 9):
         assert P.admm_strerror(code)
     assert P.admm_strerror(99) == "unknown status"
@@ -94,7 +94,9 @@ def test_plan_slabs_cover_columns_and_fit_limits(cuda_lib, m, n, M, N):
             assert w and max(w) - min(w) <= 2
     assert plan["box_cols"] % 2 == 0 and plan["box_cols"] <= 256
     assert plan["box_cols"] * plan["boxes_per_row"] >= plan["slab_cols"]
-    assert plan["slab_cols"] // 2 <= 32 * plan["chunks"]
+    assert plan["groups"] in (1, 2)
+    assert plan["slab_cols"] // 2 <= 32 * plan["chunks"] * plan["groups"]
+    assert (plan["groups"] == 2) == (plan["slab_cols"] // 2 > 256)
     assert plan["rows_per_stage"] % 8 == 0 and 8 <= plan["rows_per_stage"] <= 64
     assert 2 <= plan["stages"] <= 8
     assert plan["smem_bytes"] <= 232448

@@ -97,14 +97,19 @@ def test_differentiable_workload_full_size():
     _check(p.H, G, U, lam, 8, 1, 1.0, 100, range(16), 1, stop_after=1)
 
 
-def test_autograd_function_returns_the_library_gradient():
+def test_autograd_fills_g_lambda_and_rho_gradients():
+    """loss.backward() through UnrolledADMM fills G.grad, lam.grad (one per
+    scene) and rho.grad (summed over the scenes, rho being shared) with the
+    library's reverse-sweep gradient."""
     import paper_1811_05571_gb300 as P
     p = synth.gaussian_problem(256, 4096, 16, seed=3)
     G, U, lam = synth.shared_h_scenes(p.H, 3, seed0=70, nnz=16)
     bs = P.BatchSolver(torch.from_numpy(p.H_c64()).cuda(), 4, 1, lam, 1.0)
     Gt = torch.from_numpy(G.astype(np.complex64)).cuda().requires_grad_(True)
+    lam_t = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+    rho_t = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
     Ut = torch.from_numpy(U.astype(np.complex64)).cuda()
-    V = P.UnrolledADMM.apply(Gt, bs, 20)
+    V = P.UnrolledADMM.apply(Gt, lam_t, rho_t, bs, 20)
     loss = ((V - Ut).abs() ** 2).sum()
     loss.backward()
     dV = (2.0 * (V.detach() - Ut)).contiguous()
@@ -113,7 +118,149 @@ def test_autograd_function_returns_the_library_gradient():
     bs.iterate(20)
     dG, dl, dr = bs.backward(dV)
     assert torch.allclose(Gt.grad, dG, rtol=1e-5, atol=1e-6 * dG.abs().max().item())
+    assert np.allclose(lam_t.grad.numpy(), dl, rtol=1e-12, atol=0)
+    assert abs(rho_t.grad.item() - float(np.sum(dr))) <= 1e-12 * abs(float(np.sum(dr)))
     bs.close()
+
+
+def test_autograd_with_new_lambda_and_rho_matches_the_oracle():
+    """Values of lam and rho other than the solver's are pushed to it
+    (admm_batch_set_lambda, admm_batch_set_rho: refactorisation); the images
+    and the gradients then match the FP64 oracle run with the new values on
+    the matrix the FP16 storage encodes."""
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(256, 4096, 16, seed=3)
+    M, N, K = 2, 2, 20
+    G, U, lam = synth.shared_h_scenes(p.H, 4, seed0=90, nnz=16)
+    rho0 = _rho(p.H, N)
+    bs = P.BatchSolver(torch.from_numpy(p.H_c64()).cuda(), M, N, lam, rho0)
+    lam1 = [1.3 * x for x in lam]
+    rho1 = 1.5 * rho0
+    Gt = torch.from_numpy(G.astype(np.complex64)).cuda().requires_grad_(True)
+    lam_t = torch.tensor(lam1, dtype=torch.float64, requires_grad=True)
+    rho_t = torch.tensor(rho1, dtype=torch.float64, requires_grad=True)
+    V = P.UnrolledADMM.apply(Gt, lam_t, rho_t, bs, K)
+    Vn = V.detach().cpu().numpy()
+    Ut = torch.from_numpy(U.astype(np.complex64)).cuda()
+    ((V - Ut).abs() ** 2).sum().backward()
+    Hq = Q.dequantized(p.H)
+    rho_ref, checked = 0.0, 0
+    for b in range(4):
+        v, rec_a, _, _ = AD.unrolled_forward(Hq, G[b], M, N, lam1[b], rho1, K)
+        assert np.linalg.norm(Vn[b] - v) <= 1e-5 * np.linalg.norm(v)
+        vb = 2.0 * (v - U[b])
+        g_ref, l_ref, r_ref = AD.unrolled_grad(Hq, G[b], M, N, lam1[b], rho1, K, vb)
+        rho_ref += r_ref
+        kappa = lam1[b] / (M * rho1)
+        if min(float(np.min(np.abs(np.abs(a) - kappa))) for a in rec_a) / kappa < KINK:
+            continue
+        eg = np.linalg.norm(Gt.grad[b].cpu().numpy() - g_ref) / np.linalg.norm(g_ref)
+        assert eg <= TOL_GRAD, (b, eg)
+        assert abs(lam_t.grad[b].item() - l_ref) <= TOL_GRAD * abs(l_ref), (b, lam_t.grad[b].item(), l_ref)
+        checked += 1
+    assert checked >= 2
+    assert abs(rho_t.grad.item() - rho_ref) <= TOL_GRAD * abs(rho_ref), (rho_t.grad.item(), rho_ref)
+    bs.close()
+
+
+# ---------------------------------------------------------------------------
+# the differentiable workload with complex64 H: one Solver per scene
+# ---------------------------------------------------------------------------
+
+C5 = dict(m=2048, n=16384, nnz=64, seed=5, scenes=16, seed0=500, M=8, K=100)
+
+
+def _c5_oracle_grad(b: int):
+    """Oracle forward margin and FP64 gradient of scene b of the differentiable
+    workload on the complex64 H (run in a spawned worker)."""
+    p = synth.gaussian_problem(C5["m"], C5["n"], C5["nnz"], seed=C5["seed"])
+    G, U, lam = synth.shared_h_scenes(p.H, C5["scenes"], seed0=C5["seed0"], nnz=C5["nnz"])
+    v, rec_a, _, _ = AD.unrolled_forward(p.H, G[b], C5["M"], 1, lam[b], 1.0, C5["K"])
+    kappa = lam[b] / C5["M"]
+    margin = min(float(np.min(np.abs(np.abs(a) - kappa))) for a in rec_a) / kappa
+    g_ref, l_ref, r_ref = AD.unrolled_grad(p.H, G[b], C5["M"], 1, lam[b], 1.0, C5["K"], 2.0 * (v - U[b]))
+    return b, margin, g_ref, l_ref, r_ref
+
+
+@pytest.fixture(scope="module")
+def c5_gpu():
+    """The differentiable workload through UnrolledADMM over 16 complex64
+    single-scene handles: images and the gradients in G, lam and rho."""
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(C5["m"], C5["n"], C5["nnz"], seed=C5["seed"])
+    G, U, lam = synth.shared_h_scenes(p.H, C5["scenes"], seed0=C5["seed0"], nnz=C5["nnz"])
+    Hd = torch.from_numpy(p.H_c64()).cuda()
+    Gd = torch.from_numpy(G.astype(np.complex64)).cuda()
+    solvers = [P.Solver(Hd, Gd[b], C5["M"], 1, lam[b], 1.0) for b in range(C5["scenes"])]
+    Gt = Gd.clone().requires_grad_(True)
+    lam_t = torch.tensor(lam, dtype=torch.float64, requires_grad=True)
+    rho_t = torch.tensor(1.0, dtype=torch.float64, requires_grad=True)
+    Ut = torch.from_numpy(U.astype(np.complex64)).cuda()
+    V = P.UnrolledADMM.apply(Gt, lam_t, rho_t, solvers, C5["K"])
+    ((V - Ut).abs() ** 2).sum().backward()
+    # per-scene rho gradients (the autograd output is their sum)
+    dV = (2.0 * (V.detach() - Ut)).contiguous()
+    per_rho = [sv.backward(dV[b])[2] for b, sv in enumerate(solvers)]
+    out = dict(p=p, G=G, U=U, lam=lam, V=V.detach().cpu().numpy(), g_bar=Gt.grad.cpu().numpy(),
+               lam_bar=lam_t.grad.numpy().copy(), rho_bar=rho_t.grad.item(), per_rho=per_rho)
+    for sv in solvers:
+        assert sv.status() == 0
+        sv.close()
+    return out
+
+
+def test_differentiable_workload_complex64_every_scene(c5_gpu):
+    """All 16 scenes of the differentiable workload (H 2048 x 16384 complex64,
+    consensus 8 x 1, K = 100) against the FP64 oracle gradient on the same H:
+    every scene clear of the kink is compared, in G, lambda and rho."""
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    with ProcessPoolExecutor(4, mp_context=mp.get_context("spawn")) as ex:
+        refs = list(ex.map(_c5_oracle_grad, range(C5["scenes"])))
+    assert abs(c5_gpu["rho_bar"] - sum(c5_gpu["per_rho"])) <= 1e-9 * abs(sum(c5_gpu["per_rho"]))
+    checked = 0
+    for b, margin, g_ref, l_ref, r_ref in refs:
+        if margin < KINK:
+            continue
+        eg = np.linalg.norm(c5_gpu["g_bar"][b] - g_ref) / np.linalg.norm(g_ref)
+        assert eg <= TOL_GRAD, f"scene {b}: g gradient relative error {eg:.3e}"
+        assert abs(c5_gpu["lam_bar"][b] - l_ref) <= TOL_GRAD * abs(l_ref), (b, c5_gpu["lam_bar"][b], l_ref)
+        assert abs(c5_gpu["per_rho"][b] - r_ref) <= TOL_GRAD * abs(r_ref), (b, c5_gpu["per_rho"][b], r_ref)
+        checked += 1
+    assert checked >= 8, checked
+
+
+def test_differentiable_workload_gradient_matches_central_differences(c5_gpu):
+    """The GPU gradient of scene 0 against central differences (h = 1e-6) of the
+    FP64 oracle's loss ||v_K - u||^2, along three random unit directions in g
+    and in lambda and rho, at the full workload size."""
+    p, G, U, lam = c5_gpu["p"], c5_gpu["G"], c5_gpu["U"], c5_gpu["lam"]
+    M, K = C5["M"], C5["K"]
+    b = 0
+    for b in range(C5["scenes"]):
+        _, rec_a, _, _ = AD.unrolled_forward(p.H, G[b], M, 1, lam[b], 1.0, K)
+        if min(float(np.min(np.abs(np.abs(a) - lam[b] / M))) for a in rec_a) / (lam[b] / M) >= 1e-4:
+            break
+
+    def loss(g, lm, rh):
+        v = A.run_split(p.H, g, M, 1, lm, rh, K).v
+        return float(np.sum(np.abs(v - U[b]) ** 2))
+
+    h = 1e-6
+    rng = np.random.default_rng(11)
+    gb = c5_gpu["g_bar"][b].astype(np.complex128)
+    for _ in range(3):
+        d = rng.standard_normal(p.m) + 1j * rng.standard_normal(p.m)
+        d /= np.linalg.norm(d)
+        fd = (loss(G[b] + h * d, lam[b], 1.0) - loss(G[b] - h * d, lam[b], 1.0)) / (2 * h)
+        an = float(np.real(np.vdot(gb, d)))
+        assert abs(fd - an) <= TOL_GRAD * max(abs(fd), np.linalg.norm(gb)), (fd, an)
+    hl = 1e-6 * lam[b]
+    fd_l = (loss(G[b], lam[b] + hl, 1.0) - loss(G[b], lam[b] - hl, 1.0)) / (2 * hl)
+    assert abs(fd_l - c5_gpu["lam_bar"][b]) <= TOL_GRAD * abs(fd_l), (fd_l, c5_gpu["lam_bar"][b])
+    hr = 1e-6
+    fd_r = (loss(G[b], lam[b], 1.0 + hr) - loss(G[b], lam[b], 1.0 - hr)) / (2 * hr)
+    assert abs(fd_r - c5_gpu["per_rho"][b]) <= TOL_GRAD * abs(fd_r), (fd_r, c5_gpu["per_rho"][b])
 
 
 @pytest.mark.parametrize("M,N,K,fp16", [(4, 1, 30, False), (1, 4, 25, False), (2, 2, 25, False), (4, 1, 30, True)])

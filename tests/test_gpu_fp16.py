@@ -15,7 +15,7 @@ import torch
 import oracle
 import synth
 from oracle import quantize as Q
-from test_gpu_parity import TOL, _rho_cols, compare_all
+from test_gpu_parity import TOL, WIDE_CASES, _rho_cols, compare_all
 
 pytestmark = pytest.mark.gpu
 
@@ -82,6 +82,17 @@ def test_fp16_gaussian_256x4096_consensus4_300_iterations():
     (96, 2048, 2, 16, 80),      # slabs spanning several column blocks
 ])
 def test_fp16_mid_size_parity(m, n, M, N, iters):
+    _fp16_case(m, n, M, N, iters)
+
+
+@pytest.mark.parametrize("m,n,M,N,iters", WIDE_CASES)
+def test_fp16_wide_slabs_two_column_groups(m, n, M, N, iters):
+    """The two-column-group kernel instance in the FP16 mode (slabs of more
+    than 256 pairs; odd slab starts give boxes starting 2 columns early)."""
+    _fp16_case(m, n, M, N, iters)
+
+
+def _fp16_case(m, n, M, N, iters):
     p = synth.gaussian_problem(m, n, max(2, m // 16), seed=m + n + M + N)
     rho = _rho_cols(p, N)
     s = solver(p, M, N, rho=rho)

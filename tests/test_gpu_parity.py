@@ -112,9 +112,35 @@ def cra():
 
 
 @pytest.mark.parametrize("M,N", [(8, 1), (1, 8), (4, 4)])
-def test_cra_1440x32768_all_splits_50_iterations(cra, M, N):
-    ref = oracle_run(cra, M, N, 50)
-    s = gpu_run(cra, M, N, 50)
+def test_cra_1440x32768_all_splits_300_iterations(cra, M, N):
+    """300 iterations: the column splits' Jacobi exchange of estimated data is
+    where FP32 drift would accumulate."""
+    ref = oracle_run(cra, M, N, 300)
+    s = gpu_run(cra, M, N, 300)
+    compare_all(s, ref, M, N)
+
+
+WIDE_CASES = [(96, 90000, 3, 1, 30), (96, 90000, 1, 3, 30), (96, 90000, 2, 2, 30),
+              (64, 90001, 1, 160, 20)]
+
+
+def _sms() -> int:
+    return torch.cuda.get_device_properties(0).multi_processor_count
+
+
+@pytest.mark.parametrize("m,n,M,N,iters", WIDE_CASES)
+def test_wide_slabs_run_two_column_groups(m, n, M, N, iters):
+    """n = 90000: slabs of more than 256 column pairs, so every CTA runs two
+    column groups of consumer warps (half the slab each, two partial products
+    per row); ragged n (padding to 90016), and with 160 column blocks slabs
+    that meet two blocks."""
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(m, n, max(2, m // 16), seed=m + n + M + N)
+    plan, _ = P.admm_plan(m, n, M, N, num_sms=_sms(), smem_limit=232448)
+    assert plan["groups"] == 2, plan
+    rho = _rho_cols(p, N)
+    ref = oracle_run(p, M, N, iters, rho=rho)
+    s = gpu_run(p, M, N, iters, rho=rho)
     compare_all(s, ref, M, N)
 
 

@@ -575,3 +575,54 @@ def test_stored_solution_satisfies_the_lasso_optimality_conditions():
     assert np.max(np.abs(c[~sup])) <= p.lam * (1 + 1e-9)
     # the planted scene is recovered on its support
     assert set(np.flatnonzero(p.u_true)) <= set(np.flatnonzero(v))
+
+
+def test_stored_mixed_precision_solution_satisfies_the_lasso_optimality_conditions():
+    """v* of the 8192 x 131072 workload (tests/golden/make_vstar_config3.py):
+    with c = H^H (g - H v*), c_k = lambda v_k / |v_k| on the support and
+    |c_k| <= lambda elsewhere; the stored lambda is 0.05 max|H^H g| of the
+    recipe.  H is drawn again chunk by chunk (64 rows at a time), never held."""
+    from concurrent.futures import ThreadPoolExecutor
+    path = os.path.join(GOLDEN, "vstar_gaussian_8192x131072_c16.txt")
+    head, rows = {}, []
+    for line in open(path):
+        if line.startswith("#"):
+            parts = line[1:].split()
+            if parts and parts[0] in ("lambda", "rho", "nonzeros"):
+                head[parts[0]] = float(parts[1])
+            continue
+        k, re, im = line.split()
+        rows.append((int(k), float(re) + 1j * float(im)))
+    c3 = synth.CONFIG3
+    m, n = c3["m"], c3["n"]
+    idx = np.array([k for k, _ in rows])
+    vals = np.array([x for _, x in rows])
+    # pass 1: g (its noise scale needs every row of H u)
+    _, g, u, _ = synth.chunked_gaussian_problem(m, n, c3["nnz"], c3["seed"], sink=lambda r0, blk: None,
+                                                lam=-1.0)
+    # pass 2: H^H g and H^H (g - H v*), summed in chunk order
+    chunks = (m + synth.ROWS_PER_DRAW - 1) // synth.ROWS_PER_DRAW
+
+    def part(c):
+        blk = synth.chunked_gaussian_rows(m, n, c3["seed"], c).astype(np.complex128)
+        r0 = c * synth.ROWS_PER_DRAW
+        gc = g[r0:r0 + blk.shape[0]]
+        res = gc - blk[:, idx] @ vals
+        return np.conj(blk.T @ np.conj(gc)), np.conj(blk.T @ np.conj(res))
+
+    hg = np.zeros(n, dtype=np.complex128)
+    cvec = np.zeros(n, dtype=np.complex128)
+    with ThreadPoolExecutor(min(16, os.cpu_count() or 1)) as ex:
+        for a, b in ex.map(part, range(chunks)):
+            hg += a
+            cvec += b
+    lam = head["lambda"]
+    assert abs(lam - c3["lam_frac"] * np.max(np.abs(hg))) <= 1e-12 * lam
+    assert head["rho"] == c3["rho"] and len(rows) == head["nonzeros"]
+    v = np.zeros(n, dtype=np.complex128)
+    v[idx] = vals
+    sup = v != 0
+    assert np.max(np.abs(cvec[sup] - lam * v[sup] / np.abs(v[sup]))) <= 1e-8 * lam
+    assert np.max(np.abs(cvec[~sup])) <= lam * (1 + 1e-8)
+    # the planted scene's support is recovered
+    assert set(np.flatnonzero(u)) <= set(idx.tolist())
