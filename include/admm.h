@@ -356,6 +356,55 @@ int admm_status(admm_t* h, void* stream);
 /* Free everything the handle owns.  NULL is accepted. */
 void admm_destroy(admm_t* h);
 
+/* ---------------------------------------------------------------------------
+ * Sharded iteration (Section IV, Table I): the blocks of one split spread
+ * over several ranks, each rank holding a handle of its own blocks -- the
+ * rows of its row blocks and the columns of its column blocks of H, set up
+ * with those blocks' counts (admm_setup on the sub-matrix, lambda and rho of
+ * the whole problem).  Per iteration the caller moves two sums between ranks
+ * (with any collective library):
+ *   1. column splits: t_local = admm_shard_ghat_sum (the handle's estimated
+ *      data summed over its column blocks, per row); T = the sum of t_local
+ *      over the ranks holding the same rows; admm_shard_set_exchange(T), so
+ *      the handle's blocks fit g_i - sum_{q != j} ghat_iq over every column
+ *      block q of the problem (Eq. g_columns, g_rows_columns);
+ *   2. admm_shard_ustep: the u-step of every local block (the handle's one
+ *      pass pair over its H), writing per column the sum over the local
+ *      replicas of u^i + s^i; S = the sum over the ranks holding the same
+ *      columns;
+ *   3. admm_shard_vstep(S): v = S_kappa(S / row_blocks_total), kappa =
+ *      lambda / (row_blocks_total rho) (Eq. v_variable, v_variable_rows_
+ *      columns), and s^i += u^i - v for the local replicas; rec receives the
+ *      local residual partials sum ||u^i - v||^2, ||v - v_old||^2,
+ *      sum ||u^i||^2, ||v||^2, sum ||s^i||^2 (FP64).
+ * Consensus exchanges only step 2's sums (n per rank), sectioning only step
+ * 1's (m per rank), consensus and sectioning both over sub-groups.  The paper
+ * has no code for this; it describes the node-to-node exchanges.
+ * ------------------------------------------------------------------------- */
+
+/* Put a lemma-form handle into sharded mode: row_blocks_total is the number
+ * of row blocks (replicas) of the whole split.  Keeps the handle's g as the
+ * data vector (admm_set_g and admm_reset keep using it).  Synchronises. */
+int admm_shard_enable(admm_t* h, int32_t row_blocks_total, void* stream);
+
+/* t_local (m complex64, host or device): per row, the sum of the handle's
+ * current estimated data over its column blocks. */
+int admm_shard_ghat_sum(admm_t* h, void* t_local, void* stream);
+
+/* t_global (m complex64): the sum of t_local over the ranks sharing these
+ * rows; the blocks then fit g - t_global + t_local - sum of the other local
+ * blocks' estimated data. */
+int admm_shard_set_exchange(admm_t* h, const void* t_global, void* stream);
+
+/* One u-step of every local block (one launch of the persistent kernel);
+ * sum_out (n complex64) receives sum over local replicas of u^i + s^i. */
+int admm_shard_ustep(admm_t* h, void* sum_out, void* stream);
+
+/* v and s update from sum_global (n complex64, the sum over all replicas);
+ * rec: 5 doubles, the local residual partials.  Synchronises `stream`;
+ * returns a device status (ADMM_ETIMEOUT, ADMM_EDIVERGED) raised meanwhile. */
+int admm_shard_vstep(admm_t* h, const void* sum_global, double* rec, void* stream);
+
 /* Allocation-free solve of a small problem.  The paper has no counterpart:
  * this entry point exists for callers that cannot allocate device memory --
  * a framework whose own pool allocator owns all of the GPU's memory, or a

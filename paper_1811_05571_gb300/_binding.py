@@ -107,6 +107,11 @@ SIGNATURES = {
     "admm_backward": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                                 c_void_p]),
     "admm_destroy": (None, [c_void_p]),
+    "admm_shard_enable": (c_int32, [c_void_p, c_int32, c_void_p]),
+    "admm_shard_ghat_sum": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "admm_shard_set_exchange": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "admm_shard_ustep": (c_int32, [c_void_p, c_void_p, c_void_p]),
+    "admm_shard_vstep": (c_int32, [c_void_p, c_void_p, ctypes.POINTER(c_double), c_void_p]),
     "admm_solve_small_noalloc": (c_int32, [c_void_p, c_void_p, c_int64, c_int64, c_int32, c_int32,
                                            c_double, c_double, c_int32, c_void_p, c_void_p]),
     "admm_batch_setup": (c_int32, [ctypes.POINTER(c_void_p), c_void_p, c_int64, c_int64, c_int32, c_int32,
@@ -326,6 +331,29 @@ def admm_status(h: int, stream=None) -> int:
 def admm_destroy(h: int) -> None:
     if h:
         load().admm_destroy(h)
+
+
+def admm_shard_enable(h: int, row_blocks_total: int, stream=None) -> None:
+    _check(load().admm_shard_enable(h, row_blocks_total, _stream(stream)), h)
+
+
+def admm_shard_ghat_sum(h: int, t_local, stream=None) -> None:
+    _check(load().admm_shard_ghat_sum(h, _ptr(t_local), _stream(stream)), h)
+
+
+def admm_shard_set_exchange(h: int, t_global, stream=None) -> None:
+    _check(load().admm_shard_set_exchange(h, _ptr(t_global), _stream(stream)), h)
+
+
+def admm_shard_ustep(h: int, sum_out, stream=None) -> None:
+    _check(load().admm_shard_ustep(h, _ptr(sum_out), _stream(stream)), h)
+
+
+def admm_shard_vstep(h: int, sum_global, stream=None):
+    import numpy as np
+    rec = (c_double * 5)()
+    _check(load().admm_shard_vstep(h, _ptr(sum_global), rec, _stream(stream)), h)
+    return np.array(rec[:], dtype=np.float64)
 
 
 def admm_solve_small_noalloc(H, g, m: int, n: int, row_blocks: int, col_blocks: int, lam: float,

@@ -104,6 +104,11 @@ struct admm_problem {
     DirectState dir;
     int broken = 0;      // sticky error that blocks further iterations
     double gram_ms = 0.0, factor_ms = 0.0;
+    // sharded iteration (admm_shard_*): replicas of all ranks, the data vector
+    // as given, the exchanged sums and the residual partials
+    int sh_Mtot = 0;     // 0: not sharded
+    float2 *sh_g0 = nullptr, *sh_tloc = nullptr, *sh_tglob = nullptr, *sh_sum = nullptr;
+    double* sh_rec = nullptr;
     std::string err;
 };
 
@@ -143,7 +148,7 @@ void free_all(admm_t* h) {
                     h->kinv_off_d, h->ints_d, h->res_part, h->hist, h->k_done, h->bar, h->status,
                     h->stop_flag, h->trace, h->H16, h->scales, h->gmax, h->kinv16, h->rec_a, h->rec_w,
                     h->bVb, h->bSb, h->bGhb, h->bGt, h->bdG, h->bSig, h->bP, h->bR, h->bW, h->bkbar,
-                    h->brbar, h->bkappa, h->bupd};
+                    h->brbar, h->bkappa, h->bupd, h->sh_g0, h->sh_tloc, h->sh_tglob, h->sh_sum, h->sh_rec};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DirectState& d = h->dir;
@@ -632,6 +637,7 @@ int zero_state(admm_t* h, cudaStream_t st) {
     CK(h, cudaMemsetAsync(h->k_done, 0, sizeof(long long), st));
     CK(h, cudaMemsetAsync(h->hist, 0, static_cast<size_t>(h->hist_cap) * 5 * sizeof(double), st));
     h->dir.q_valid = false;
+    if (h->sh_g0) CK(h, cudaMemcpyAsync(h->g, h->sh_g0, h->m * sizeof(float2), cudaMemcpyDeviceToDevice, st));
     if (h->form == ADMM_FORM_DIRECT) {
         CK(h, cudaMemsetAsync(h->dir.cnt, 0, static_cast<size_t>(h->dir.ncnt) * sizeof(unsigned), st));
         CK(h, cudaMemsetAsync(h->dir.stop_pending, 0, sizeof(int), st));
@@ -1449,7 +1455,10 @@ int admm_set_g(admm_t* h, const void* g, int32_t h_dtype, void* stream) {
     if (h->k > 0) h->rec_valid = false;
     h->dir.c_valid = false;
     h->dir.q_valid = false;
-    return copy_vector_in(h, h->g, g, h->m, h_dtype, as_stream(stream));
+    const int code = copy_vector_in(h, h->g, g, h->m, h_dtype, as_stream(stream));
+    if (code == ADMM_OK && h->sh_g0)
+        CK(h, cudaMemcpyAsync(h->sh_g0, h->g, h->m * sizeof(float2), cudaMemcpyDeviceToDevice, as_stream(stream)));
+    return code;
 }
 
 int admm_set_lambda(admm_t* h, double lambda) {
@@ -1792,6 +1801,101 @@ int admm_backward(admm_t* h, const void* grad_v, void* grad_g, double* grad_lamb
 int admm_status(admm_t* h, void* stream) {
     if (!h) return ADMM_EINVAL;
     return device_status(h, as_stream(stream));
+}
+
+// ---------------------------------------------------------------------------
+// sharded iteration: this handle holds some of the blocks of a larger split
+// (Section IV); the caller exchanges the sums between ranks
+// ---------------------------------------------------------------------------
+
+int admm_shard_enable(admm_t* h, int32_t row_blocks_total, void* stream) {
+    if (!h) return ADMM_EINVAL;
+    if (h->form == ADMM_FORM_DIRECT)
+        return fail(h, ADMM_EUNSUPPORTED, "the sharded iteration runs the lemma form only");
+    if (row_blocks_total < h->M) return fail(h, ADMM_EINVAL, "row_blocks_total must be >= the handle's row blocks");
+    cudaStream_t st = as_stream(stream);
+    if (!h->sh_g0) {
+        const size_t ld = h->plan.ld;
+        if (dalloc(&h->sh_g0, h->m) != cudaSuccess || dalloc(&h->sh_tloc, h->m) != cudaSuccess ||
+            dalloc(&h->sh_tglob, h->m) != cudaSuccess || dalloc(&h->sh_sum, ld) != cudaSuccess ||
+            dalloc(&h->sh_rec, 5) != cudaSuccess)
+            return fail(h, ADMM_ENOMEM, "no room for the sharded-iteration buffers");
+        CK(h, cudaMemcpyAsync(h->sh_g0, h->g, h->m * sizeof(float2), cudaMemcpyDeviceToDevice, st));
+        CK(h, cudaMemsetAsync(h->sh_sum, 0, ld * sizeof(float2), st));
+        CK(h, cudaMemsetAsync(h->sh_tloc, 0, h->m * sizeof(float2), st));
+    }
+    h->sh_Mtot = row_blocks_total;
+    CK(h, cudaStreamSynchronize(st));
+    return ADMM_OK;
+}
+
+int admm_shard_ghat_sum(admm_t* h, void* t_local, void* stream) {
+    if (!h || !t_local) return h ? fail(h, ADMM_EINVAL, "t_local is NULL") : ADMM_EINVAL;
+    if (!h->sh_Mtot) return fail(h, ADMM_EINVAL, "admm_shard_enable first");
+    cudaStream_t st = as_stream(stream);
+    const float2* cur = h->ghat + static_cast<size_t>(h->k & 1) * h->N * h->m;
+    CK(h, admm::launch_shard_ghat_sum(cur, h->N, h->m, h->sh_tloc, st));
+    CK(h, cudaMemcpyAsync(t_local, h->sh_tloc, h->m * sizeof(float2), cudaMemcpyDefault, st));
+    return ADMM_OK;
+}
+
+int admm_shard_set_exchange(admm_t* h, const void* t_global, void* stream) {
+    if (!h || !t_global) return h ? fail(h, ADMM_EINVAL, "t_global is NULL") : ADMM_EINVAL;
+    if (!h->sh_Mtot) return fail(h, ADMM_EINVAL, "admm_shard_enable first");
+    cudaStream_t st = as_stream(stream);
+    CK(h, cudaMemcpyAsync(h->sh_tglob, t_global, h->m * sizeof(float2), cudaMemcpyDefault, st));
+    CK(h, admm::launch_shard_geff(h->sh_g0, h->sh_tglob, h->sh_tloc, h->m, h->g, st));
+    return ADMM_OK;
+}
+
+int admm_shard_ustep(admm_t* h, void* sum_out, void* stream) {
+    if (!h || !sum_out) return h ? fail(h, ADMM_EINVAL, "sum_out is NULL") : ADMM_EINVAL;
+    if (!h->sh_Mtot) return fail(h, ADMM_EINVAL, "admm_shard_enable first");
+    if (h->broken) return fail(h, ADMM_ECUDA, "handle is in an error state; call admm_reset");
+    cudaStream_t st = as_stream(stream);
+    if (h->pending) {
+        const int code = device_status(h, st);
+        if (code) return code;
+    }
+    const Plan& pl = h->plan;
+    admm::IterArgs a;
+    fill_args(h, pl, handle_buffers(h), 1, 0, 0.0, 0.0, a);
+    a.shard_sum = h->sh_sum;
+    a.pending_prev = 0;
+    a.rec_a = nullptr;
+    a.rec_w = nullptr;
+    a.rec_cap = 0;
+    a.trace = nullptr;
+    const bool f16 = h->use_f16 != 0;
+    cudaError_t e = admm::launch_iterate(f16 ? h->tmap16 : h->tmap, a, pl.chunks, pl.smem, st, f16);
+    if (e != cudaSuccess) return cuda_fail(h, e, "cooperative launch of the sharded u-step");
+    h->k += 1;
+    h->pending = 0;
+    h->rec_valid = false;
+    CK(h, cudaMemcpyAsync(sum_out, h->sh_sum, h->n * sizeof(float2), cudaMemcpyDefault, st));
+    return ADMM_OK;
+}
+
+int admm_shard_vstep(admm_t* h, const void* sum_global, double* rec, void* stream) {
+    if (!h || !sum_global || !rec) return h ? fail(h, ADMM_EINVAL, "NULL argument") : ADMM_EINVAL;
+    if (!h->sh_Mtot) return fail(h, ADMM_EINVAL, "admm_shard_enable first");
+    cudaStream_t st = as_stream(stream);
+    CK(h, cudaMemcpyAsync(h->sh_sum, sum_global, h->n * sizeof(float2), cudaMemcpyDefault, st));
+    const double Mt = h->sh_Mtot;
+    CK(h, admm::launch_shard_vstep(h->v, h->s, h->u, h->sh_sum, h->n, h->plan.ld, h->M,
+                                   static_cast<float>(1.0 / Mt), static_cast<float>(h->lambda / (Mt * h->rho)),
+                                   h->sh_rec, st));
+    CK(h, cudaMemcpyAsync(rec, h->sh_rec, 5 * sizeof(double), cudaMemcpyDefault, st));
+    CK(h, cudaStreamSynchronize(st));
+    int code = 0;
+    CK(h, cudaMemcpy(&code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (code) {
+        if (code == ADMM_ETIMEOUT) h->broken = 1;
+        return fail(h, code, "device status raised during the sharded iteration");
+    }
+    if (!std::isfinite(rec[0] + rec[1] + rec[2] + rec[3] + rec[4]))
+        return fail(h, ADMM_EDIVERGED, "the iterates became NaN or Inf");
+    return ADMM_OK;
 }
 
 void admm_destroy(admm_t* h) {

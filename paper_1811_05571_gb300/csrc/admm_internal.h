@@ -173,6 +173,9 @@ struct IterArgs {
     int rec_cap;
     int rec_pitch;
     int pending_prev;     // the previous launch's last residual record is still to be summed
+    // sharded iteration (null otherwise): the epilogue writes u and, per column,
+    // the sum over this handle's replicas of u_i + s_i here, and leaves v and s
+    float2* shard_sum;
 };
 
 // The problems of a multi-problem launch, passed as kernel parameters (so the
@@ -324,6 +327,15 @@ cudaError_t launch_conj_transpose(const float2* H, int64_t m, int64_t n, int64_t
 cudaError_t launch_pack_c128(const double2* src, int64_t m, int64_t n, float2* dst, int64_t ld,
                              cudaStream_t s);
 cudaError_t launch_finite_check(const float2* x, int64_t count, int* flag, cudaStream_t s);
+// sharded iteration: out[r] = sum_q ghat[q * m + r] over the N column blocks;
+// g[r] = g0[r] - t_glob[r] + t_loc[r];  v = S_kappa(sum / M_total), s_i += u_i - v
+// for the M local replicas, with the FP64 residual partials (sum ||u_i - v||^2,
+// ||v - v_old||^2, sum ||u_i||^2, ||v||^2, sum ||s_i||^2) added into rec[5]
+cudaError_t launch_shard_ghat_sum(const float2* ghat, int N, int64_t m, float2* out, cudaStream_t s);
+cudaError_t launch_shard_geff(const float2* g0, const float2* t_glob, const float2* t_loc, int64_t m, float2* g,
+                              cudaStream_t s);
+cudaError_t launch_shard_vstep(float2* v, float2* s, const float2* u, const float2* sum, int64_t n, int64_t ld, int M,
+                               float inv_Mtot, float kappa, double* rec, cudaStream_t st);
 cudaError_t launch_scale(float2* x, int64_t count, float alpha, cudaStream_t s);
 // FP16 copy of H with one power-of-two scale per 64-row group (and, when Hdeq
 // is not null, the dequantised matrix in FP32); gmax_bits holds ceil(m/64) words.

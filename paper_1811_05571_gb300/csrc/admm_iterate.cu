@@ -805,7 +805,33 @@ struct Consumer {
     }
 
     // ---- epilogue: u_i = z_i + sigma_i, v = S(mean u + mean s), s += u - v ----
+    // ---- sharded epilogue: u_i = z_i + sigma_i and the sum over this handle's
+    // replicas of u_i + s_i (the v and s update waits for the other ranks' sums)
+    __device__ void shard_sums() {
+        for (int p = tid; p < npairs; p += kConsumerThreads) {
+            const int c = c_beg + 2 * p;
+            const bool o0 = c >= own0 && c < own1, o1 = c + 1 >= own0 && c + 1 < own1;
+            const float4 vv = *reinterpret_cast<const float4*>(a.v + c);
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int i = 0; i < a.M; ++i) {
+                const float4 ss = *reinterpret_cast<const float4*>(a.s + static_cast<size_t>(i) * a.ld + c);
+                const float4 uu = (vv - ss) + sigma_of(i, p);
+                acc = acc + (uu + ss);
+                float2* up = reinterpret_cast<float2*>(a.u + static_cast<size_t>(i) * a.ld + c);
+                if (o0) up[0] = lo2(uu);
+                if (o1) up[1] = hi2(uu);
+            }
+            float2* sp = reinterpret_cast<float2*>(a.shard_sum + c);
+            if (o0) sp[0] = lo2(acc);
+            if (o1) sp[1] = hi2(acc);
+        }
+    }
+
     __device__ void update_state(long long rec_slot) {
+        if (a.shard_sum) {
+            shard_sums();
+            return;
+        }
         float rp = 0.f, rdv = 0.f, u2 = 0.f, v2 = 0.f, s2 = 0.f;
         for (int p = tid; p < npairs; p += kConsumerThreads) {
             const int c = c_beg + 2 * p;

@@ -92,6 +92,65 @@ __global__ void dequantize_kernel(const __half2* __restrict__ H16, int64_t m, in
     }
 }
 
+// ---- sharded iteration (Section IV: the blocks of one problem on several ranks)
+
+__global__ void shard_ghat_sum_kernel(const float2* __restrict__ ghat, int N, int64_t m, float2* __restrict__ out) {
+    for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < m;
+         r += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        float2 t = make_float2(0.f, 0.f);
+        for (int q = 0; q < N; ++q) {
+            const float2 x = ghat[q * m + r];
+            t.x += x.x;
+            t.y += x.y;
+        }
+        out[r] = t;
+    }
+}
+
+__global__ void shard_geff_kernel(const float2* __restrict__ g0, const float2* __restrict__ tg,
+                                  const float2* __restrict__ tl, int64_t m, float2* __restrict__ g) {
+    for (int64_t r = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; r < m;
+         r += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        g[r] = make_float2(g0[r].x - tg[r].x + tl[r].x, g0[r].y - tg[r].y + tl[r].y);
+}
+
+// v = S_kappa(sum / M_total) (Eq. softhresholding, the complex sign a/|a|),
+// s_i += u_i - v for the local replicas, and the residual partials in FP64
+__global__ void shard_vstep_kernel(float2* __restrict__ v, float2* __restrict__ s, const float2* __restrict__ u,
+                                   const float2* __restrict__ sum, int64_t n, int64_t ld, int M, float inv_Mtot,
+                                   float kappa, double* __restrict__ rec) {
+    double acc[5] = {0, 0, 0, 0, 0};
+    for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < n;
+         c += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const float2 a = make_float2(sum[c].x * inv_Mtot, sum[c].y * inv_Mtot);
+        const float mag = hypotf(a.x, a.y);
+        float2 vn = make_float2(0.f, 0.f);
+        if (mag > kappa) {
+            const float sc = 1.0f - kappa / mag;
+            vn = make_float2(a.x * sc, a.y * sc);
+        }
+        const float2 vo = v[c];
+        v[c] = vn;
+        acc[1] += static_cast<double>((vn.x - vo.x) * (vn.x - vo.x) + (vn.y - vo.y) * (vn.y - vo.y));
+        acc[3] += static_cast<double>(vn.x * vn.x + vn.y * vn.y);
+        for (int i = 0; i < M; ++i) {
+            const float2 uu = u[i * ld + c];
+            float2 ss = s[i * ld + c];
+            ss = make_float2((ss.x + uu.x) - vn.x, (ss.y + uu.y) - vn.y);
+            s[i * ld + c] = ss;
+            acc[0] += static_cast<double>((uu.x - vn.x) * (uu.x - vn.x) + (uu.y - vn.y) * (uu.y - vn.y));
+            acc[2] += static_cast<double>(uu.x * uu.x + uu.y * uu.y);
+            acc[4] += static_cast<double>(ss.x * ss.x + ss.y * ss.y);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        double x = acc[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if ((threadIdx.x & 31) == 0) atomicAdd(rec + q, x);
+    }
+}
+
 int grid_for(int64_t count) {
     int64_t blocks = (count + 255) / 256;
     if (blocks > 4096) blocks = 4096;
@@ -128,6 +187,25 @@ cudaError_t launch_quantize_f16(const float2* H, int64_t m, int64_t ld, unsigned
 cudaError_t launch_dequantize_f16(const void* H16, int64_t m, int64_t ld, const float* scales,
                                   float2* Hdeq, cudaStream_t s) {
     dequantize_kernel<<<grid_for(m * ld), 256, 0, s>>>(static_cast<const __half2*>(H16), m, ld, scales, Hdeq);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_ghat_sum(const float2* ghat, int N, int64_t m, float2* out, cudaStream_t s) {
+    shard_ghat_sum_kernel<<<grid_for(m), 256, 0, s>>>(ghat, N, m, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_geff(const float2* g0, const float2* t_glob, const float2* t_loc, int64_t m, float2* g,
+                              cudaStream_t s) {
+    shard_geff_kernel<<<grid_for(m), 256, 0, s>>>(g0, t_glob, t_loc, m, g);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shard_vstep(float2* v, float2* s, const float2* u, const float2* sum, int64_t n, int64_t ld, int M,
+                               float inv_Mtot, float kappa, double* rec, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(rec, 0, 5 * sizeof(double), st);
+    if (e != cudaSuccess) return e;
+    shard_vstep_kernel<<<std::min(grid_for(n), 1024), 256, 0, st>>>(v, s, u, sum, n, ld, M, inv_Mtot, kappa, rec);
     return cudaGetLastError();
 }
 
