@@ -447,7 +447,8 @@ int admm_solve_small_noalloc(const void* H, const void* g, int64_t m, int64_t n,
  * each on its own CTAs with its own grid barriers.  Problems that do not fit
  * the SMs together go to further waves (launched one after another).  The
  * paper solves one problem at a time; this is the library's scheduler for
- * many uneven ones.
+ * many uneven ones.  Up to 48 problems, all waves run in ONE cooperative
+ * launch of the kernel instance every problem's plan shares.
  * ------------------------------------------------------------------------- */
 typedef struct admm_group admm_group_t;
 
@@ -463,6 +464,12 @@ int admm_group_iterate(admm_group_t* g, int32_t iters, void* stream);
 
 /* Number of waves, and the CTAs each problem was given (cap entries). */
 int admm_group_info(const admm_group_t* g, int32_t* waves, int32_t* ctas, int32_t cap);
+
+/* Cooperative launches per admm_group_iterate: 1 when every wave runs in one
+ * launch (groups of up to 48 problems: a CTA moves on to its next wave's
+ * problem as soon as its current one is done), else the number of waves.
+ * -1 for NULL. */
+int admm_group_launches(const admm_group_t* g);
 
 const char* admm_group_last_error(const admm_group_t* g);
 void admm_group_destroy(admm_group_t* g);

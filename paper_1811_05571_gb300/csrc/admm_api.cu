@@ -1929,6 +1929,11 @@ struct admm_group {
     };
     std::vector<Prob> probs;
     std::vector<Wave> waves;
+    // all waves in one cooperative launch (up to kMaxGroupWave problems): per
+    // wave and CTA the problem (-1 idle), then per wave and CTA the local CTA
+    int* all_map = nullptr;
+    int all_ctas = 0, all_chunks = 1, all_smem = 0;
+    bool one_launch = false;
     std::string err;
 };
 
@@ -1955,6 +1960,7 @@ void free_group(admm_group_t* g) {
     }
     for (auto& w : g->waves)
         if (w.cta_map) cudaFree(w.cta_map);
+    if (g->all_map) cudaFree(g->all_map);
 }
 
 // tensor map of h's H (f16: its FP16 copy) with the box of plan pl
@@ -2055,7 +2061,13 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
         g->waves[w].probs.push_back(q);
         used[w] += pmin[q];
     }
-    for (auto& w : g->waves) {
+    // with every problem in one launch, all share one kernel instance: the
+    // largest chunk count any problem's plan needs
+    const bool one_launch = count <= admm::kMaxGroupWave;
+    std::vector<std::vector<int>> wave_P(g->waves.size());
+    int ch_all = 1;
+    for (size_t wi = 0; wi < g->waves.size(); ++wi) {
+        auto& w = g->waves[wi];
         // CTAs in proportion to the work, within [pmin, pmax], at most one per SM in total
         double tot = 0.0;
         for (int q : w.probs) tot += work[q];
@@ -2091,6 +2103,14 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
             ch = std::max(ch, pl.chunks);
         }
         w.chunks = ch;
+        ch_all = std::max(ch_all, ch);
+        wave_P[wi] = P;
+    }
+    for (size_t wi = 0; wi < g->waves.size(); ++wi) {
+        auto& w = g->waves[wi];
+        std::vector<int>& P = wave_P[wi];
+        if (one_launch) w.chunks = ch_all;
+        const int ch = w.chunks;
         w.ctas = 0;
         w.smem = 0;
         std::vector<int> cta_map;
@@ -2144,14 +2164,108 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
             cudaMemcpy(w.cta_map, cta_map.data(), cta_map.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(gfail(g, ADMM_ENOMEM, "device allocation failed for a wave"));
     }
+    if (one_launch) {
+        const int W = static_cast<int>(g->waves.size());
+        int C = 0, smem = 0;
+        for (const auto& w : g->waves) {
+            C = std::max(C, w.ctas);
+            smem = std::max(smem, w.smem);
+        }
+        std::vector<int> map(2 * static_cast<size_t>(W) * C, -1);
+        for (int wi = 0; wi < W; ++wi) {
+            int b = 0;
+            for (int q : g->waves[wi].probs)
+                for (int c = 0; c < g->probs[q].pl.P; ++c, ++b) {
+                    map[static_cast<size_t>(wi) * C + b] = q;
+                    map[static_cast<size_t>(W + wi) * C + b] = c;
+                }
+        }
+        if (dalloc(&g->all_map, map.size()) != cudaSuccess ||
+            cudaMemcpy(g->all_map, map.data(), map.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(gfail(g, ADMM_ENOMEM, "device allocation failed for the launch map"));
+        g->all_ctas = C;
+        g->all_chunks = ch_all;
+        g->all_smem = smem;
+        g->one_launch = true;
+    }
     *out = g;
     return ADMM_OK;
 }
+
+namespace {
+
+// the last residual record of each problem's launch, from its group plan's partials
+int finalize_group_records(admm_group_t* g, const std::vector<int>& probs, int iters, cudaStream_t st) {
+    for (int q : probs) {
+        admm_group_t::Prob& pr = g->probs[q];
+        admm_t* h = pr.h;
+        h->k += iters;
+        admm::IterArgs a;
+        std::memset(&a, 0, sizeof a);
+        a.M = h->M;
+        a.n = static_cast<int>(h->n);
+        a.P = pr.pl.P;
+        a.rho_d = h->rho;
+        a.res_part = pr.res_part;
+        a.hist = h->hist;
+        a.hist_cap = h->hist_cap;
+        a.status = h->status;
+        const cudaError_t e = admm::launch_finalize(a, h->k - 1, st);
+        if (e != cudaSuccess) return gfail(g, ADMM_ECUDA, "finalize failed: %s", cudaGetErrorString(e));
+        h->pending = 0;
+    }
+    return ADMM_OK;
+}
+
+// arguments of problem q of the group for a launch of `iters` iterations
+int group_args(admm_group_t* g, int q, int iters, bool f16, int chunks, cudaStream_t st, admm::IterArgs& a,
+               CUtensorMap& map) {
+    admm_group_t::Prob& pr = g->probs[q];
+    admm_t* h = pr.h;
+    if (h->broken) return gfail(g, ADMM_ECUDA, "problem %d is in an error state", q);
+    if ((h->use_f16 != 0) != f16) return gfail(g, ADMM_EINVAL, "the problems of a group launch must share the H mode");
+    if (h->pending) {
+        const int code = device_status(h, st);
+        if (code) return gfail(g, code, "problem %d: %s", q, h->err.c_str());
+    }
+    const int* T = pr.tabs;
+    PlanBuffers b{T + pr.o_beg, T + pr.o_end, T + pr.o_own0, T + pr.o_own1, T + pr.o_jlo, T + pr.o_nj,
+                  T + pr.o_jl, T + pr.o_jh, T + pr.o_sl, pr.part, pr.res_part, pr.bar};
+    fill_args(h, pr.pl, b, iters, 0, 0.0, 0.0, a);
+    a.trace = nullptr;
+    map = f16 ? pr.tmap16 : pr.tmap;
+    if (!admm::group_stage_geometry_ok(a, chunks, f16))
+        return gfail(g, ADMM_EUNSUPPORTED, "inconsistent stage geometry for problem %d", q);
+    return ADMM_OK;
+}
+
+}  // namespace
 
 int admm_group_iterate(admm_group_t* g, int32_t iters, void* stream) {
     if (!g || iters < 0) return g ? gfail(g, ADMM_EINVAL, "iters must be >= 0") : ADMM_EINVAL;
     if (iters == 0) return ADMM_OK;
     cudaStream_t st = as_stream(stream);
+    if (g->one_launch) {
+        const bool f16 = g->probs[0].h->use_f16 != 0;
+        std::vector<admm::GroupParams> gpv(1);   // ~30 KB: on the heap
+        admm::GroupParams& gp = gpv[0];
+        std::memset(&gp, 0, sizeof gp);
+        const int count = static_cast<int>(g->probs.size());
+        gp.count = count;
+        std::vector<int> all(count);
+        for (int q = 0; q < count; ++q) {
+            all[q] = q;
+            const int code = group_args(g, q, iters, f16, g->all_chunks, st, gp.a[q], gp.tmap[q]);
+            if (code) return code;
+            // a CTA that reaches a later wave's problem early waits at its first
+            // grid barrier while the earlier waves finish
+            gp.a[q].timeout_ns += 10000000000LL;
+        }
+        cudaError_t e = admm::launch_waves(gp, g->all_map, static_cast<int>(g->waves.size()), g->all_ctas,
+                                           g->all_chunks, f16, g->all_smem, st);
+        if (e != cudaSuccess) return gfail(g, ADMM_ECUDA, "group launch failed: %s", cudaGetErrorString(e));
+        return finalize_group_records(g, all, iters, st);
+    }
     for (auto& w : g->waves) {
         const bool f16 = g->probs[w.probs[0]].h->use_f16 != 0;
         std::vector<admm::GroupParams> gpv(1);   // ~30 KB: on the heap
@@ -2207,6 +2321,11 @@ int admm_group_info(const admm_group_t* g, int32_t* waves, int32_t* ctas, int32_
     if (ctas)
         for (int q = 0; q < cap && q < static_cast<int>(g->probs.size()); ++q) ctas[q] = g->probs[q].pl.P;
     return ADMM_OK;
+}
+
+int admm_group_launches(const admm_group_t* g) {
+    if (!g) return -1;
+    return g->one_launch ? 1 : static_cast<int>(g->waves.size());
 }
 
 void admm_group_destroy(admm_group_t* g) {

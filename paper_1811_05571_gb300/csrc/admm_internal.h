@@ -180,7 +180,7 @@ struct IterArgs {
 
 // The problems of a multi-problem launch, passed as kernel parameters (so the
 // tensor maps and arguments sit in the parameter space, as for one problem).
-constexpr int kMaxGroupWave = 24;
+constexpr int kMaxGroupWave = 48;
 struct GroupParams {
     CUtensorMap tmap[kMaxGroupWave];
     IterArgs a[kMaxGroupWave];
@@ -193,6 +193,11 @@ struct GroupParams {
 // cta_local[b] of problem cta_prob[b].
 cudaError_t launch_group(const GroupParams& gp, const int* cta_prob, const int* cta_local, int ctas, int chunks,
                          bool f16, int smem, cudaStream_t stream);
+// Every wave of a group in one cooperative launch of `ctas` CTAs: cta_map holds
+// waves x ctas problem indices into gp (-1 idle) and then waves x ctas local
+// CTA indices.
+cudaError_t launch_waves(const GroupParams& gp, const int* cta_map, int waves, int ctas, int chunks, bool f16,
+                         int smem, cudaStream_t stream);
 bool group_stage_geometry_ok(const IterArgs& a, int chunks, bool f16);
 
 // Sum the per-CTA residual partials of iteration kabs into the history ring.

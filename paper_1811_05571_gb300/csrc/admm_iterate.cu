@@ -980,10 +980,20 @@ __device__ __forceinline__ void iterate_body(const CUtensorMap* tmap, const Iter
     if (warp == kConsumerWarps) {
         if ((threadIdx.x & 31) == 0)
             producer(tmap, a, full, empty, misc, ring, a.cta_col[cta]);
-        return;
+    } else {
+        Consumer<CH, F16, G> c(a, smem, misc, full, empty, ring, cta);
+        c.run();
     }
-    Consumer<CH, F16, G> c(a, smem, misc, full, empty, ring, cta);
-    c.run();
+    // every copy has landed (the consumers drained the ring): the barriers can
+    // be set up again for the CTA's next problem
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < a.nstages; ++s) {
+            mbar_inval(&full[s]);
+            mbar_inval(&empty[s]);
+        }
+    }
+    __syncthreads();
 }
 
 template <int CH, bool F16, int G>
@@ -1004,6 +1014,22 @@ __global__ void __launch_bounds__(kIterThreads, 1)
     extern __shared__ __align__(1024) unsigned char smem[];
     const int p = cta_prob[blockIdx.x];
     iterate_body<CH, F16, 1>(&gp.tmap[p], gp.a[p], cta_local[blockIdx.x], smem);
+}
+
+// All waves of a group in one cooperative launch: in wave w, CTA b runs local
+// CTA cta_map[W C + w C + b] of problem cta_map[w C + b] (-1: idle in that wave).
+// A CTA that finishes its wave-w problem early goes on to its wave-(w+1)
+// problem, whose grid barriers wait for that problem's other CTAs.
+template <int CH, bool F16>
+__global__ void __launch_bounds__(kIterThreads, 1)
+    iterate_waves_kernel(const __grid_constant__ GroupParams gp, const int* __restrict__ cta_map, int waves) {
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int C = gridDim.x;
+    for (int w = 0; w < waves; ++w) {
+        const int p = cta_map[w * C + blockIdx.x];
+        if (p < 0) continue;
+        iterate_body<CH, F16, 1>(&gp.tmap[p], gp.a[p], cta_map[(waves + w) * C + blockIdx.x], smem);
+    }
 }
 
 __global__ void __launch_bounds__(32) finalize_kernel(const __grid_constant__ IterArgs a, long long kabs) {
@@ -1053,6 +1079,23 @@ void* pick_group_t(int chunks) {
 }
 
 void* pick_group(int chunks, bool f16) { return f16 ? pick_group_t<true>(chunks) : pick_group_t<false>(chunks); }
+
+template <int CH, bool F16>
+void* waves_fn() {
+    return reinterpret_cast<void*>(&iterate_waves_kernel<CH, F16>);
+}
+
+template <bool F16>
+void* pick_waves_t(int chunks) {
+    switch (chunks) {
+        case 1: return waves_fn<1, F16>();
+        case 2: return waves_fn<2, F16>();
+        case 4: return waves_fn<4, F16>();
+        case 8: return waves_fn<8, F16>();
+        case 16: return waves_fn<16, F16>();
+        default: return nullptr;
+    }
+}
 
 }  // namespace
 
@@ -1120,6 +1163,16 @@ cudaError_t launch_group(const GroupParams& gp, const int* cta_prob, const int* 
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     void* args[] = {const_cast<GroupParams*>(&gp), const_cast<int**>(&cta_prob), const_cast<int**>(&cta_local)};
+    return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kIterThreads), args, static_cast<size_t>(smem), stream);
+}
+
+cudaError_t launch_waves(const GroupParams& gp, const int* cta_map, int waves, int ctas, int chunks, bool f16,
+                         int smem, cudaStream_t stream) {
+    void* fn = f16 ? pick_waves_t<true>(chunks) : pick_waves_t<false>(chunks);
+    if (!fn) return cudaErrorInvalidValue;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {const_cast<GroupParams*>(&gp), const_cast<int**>(&cta_map), &waves};
     return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kIterThreads), args, static_cast<size_t>(smem), stream);
 }
 

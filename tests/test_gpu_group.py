@@ -74,3 +74,26 @@ def test_group_result_matches_the_problem_run_alone():
         v, va = s.v().cpu().numpy(), a.v().cpu().numpy()
         assert np.linalg.norm(v - va) <= 1e-5 * max(np.linalg.norm(va), 1e-30)
     g.close()
+
+
+def test_group_of_several_waves_runs_in_one_launch():
+    """A problem large enough to take a wave of its own (2048 x 16384) beside the
+    six shared-wave shapes: at least two waves, all in one cooperative launch,
+    every problem still the oracle's at the 1e-5 bar."""
+    import paper_1811_05571_gb300 as P
+    probs, solvers = _solvers(40)
+    big = synth.gaussian_problem(2048, 16384, 64, seed=399)
+    s_big = P.Solver(torch.from_numpy(big.H_c64()).cuda(), torch.from_numpy(big.g_c64()).cuda(), 8, 1,
+                     big.lam, 1.0)
+    probs.append((big, 8, 1, 1.0))
+    solvers.append(s_big)
+    g = P.Group(solvers)
+    info = g.info()
+    assert info["waves"] >= 2 and info["launches"] == 1, info
+    g.iterate(25)
+    g.iterate(15)
+    for (p, M, N, rho), s in zip(probs, solvers):
+        assert s.status() == 0
+        assert s.info()["iterations"] == 40
+        compare_all(s, oracle.run_split(p.H, p.g, M, N, p.lam, rho, 40), M, N)
+    g.close()
