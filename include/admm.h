@@ -471,6 +471,12 @@ int admm_group_info(const admm_group_t* g, int32_t* waves, int32_t* ctas, int32_
  * -1 for NULL. */
 int admm_group_launches(const admm_group_t* g);
 
+/* 1 when that one launch is replayed from a CUDA graph captured on the first
+ * admm_group_iterate (per H mode; each call updates the graph node's
+ * arguments), 0 when it is launched directly (before the first call, with
+ * more than 48 problems, or where capture failed), -1 for NULL. */
+int admm_group_uses_graph(const admm_group_t* g);
+
 const char* admm_group_last_error(const admm_group_t* g);
 void admm_group_destroy(admm_group_t* g);
 

@@ -103,6 +103,7 @@ SIGNATURES = {
     "admm_group_iterate": (c_int32, [c_void_p, c_int32, c_void_p]),
     "admm_group_info": (c_int32, [c_void_p, ctypes.POINTER(c_int32), ctypes.POINTER(c_int32), c_int32]),
     "admm_group_launches": (c_int32, [c_void_p]),
+    "admm_group_uses_graph": (c_int32, [c_void_p]),
     "admm_group_last_error": (ctypes.c_char_p, [c_void_p]),
     "admm_group_destroy": (None, [c_void_p]),
     "admm_backward": (c_int32, [c_void_p, c_void_p, c_void_p, ctypes.POINTER(c_double), ctypes.POINTER(c_double),
@@ -500,6 +501,10 @@ def admm_group_info(g: int, count: int):
 
 def admm_group_launches(g: int) -> int:
     return int(load().admm_group_launches(g))
+
+
+def admm_group_uses_graph(g: int) -> int:
+    return int(load().admm_group_uses_graph(g))
 
 
 def admm_group_destroy(g: int) -> None:

@@ -1934,6 +1934,13 @@ struct admm_group {
     int* all_map = nullptr;
     int all_ctas = 0, all_chunks = 1, all_smem = 0;
     bool one_launch = false;
+    // that launch captured once into a CUDA graph (one kernel node); each call
+    // updates the node's arguments and replays it
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t node = nullptr;
+    int graph_f16 = -1;    // H mode the graph was captured with (-1: none)
+    bool graph_failed = false;
     std::string err;
 };
 
@@ -1961,6 +1968,8 @@ void free_group(admm_group_t* g) {
     for (auto& w : g->waves)
         if (w.cta_map) cudaFree(w.cta_map);
     if (g->all_map) cudaFree(g->all_map);
+    if (g->exec) cudaGraphExecDestroy(g->exec);
+    if (g->graph) cudaGraphDestroy(g->graph);
 }
 
 // tensor map of h's H (f16: its FP16 copy) with the box of plan pl
@@ -2261,8 +2270,59 @@ int admm_group_iterate(admm_group_t* g, int32_t iters, void* stream) {
             // grid barrier while the earlier waves finish
             gp.a[q].timeout_ns += 10000000000LL;
         }
-        cudaError_t e = admm::launch_waves(gp, g->all_map, static_cast<int>(g->waves.size()), g->all_ctas,
-                                           g->all_chunks, f16, g->all_smem, st);
+        const int W = static_cast<int>(g->waves.size());
+        cudaError_t e = admm::prepare_waves(g->all_chunks, f16, g->all_smem);
+        if (e != cudaSuccess) return gfail(g, ADMM_ECUDA, "group launch setup failed: %s", cudaGetErrorString(e));
+        if (g->graph_f16 != (f16 ? 1 : 0) && !g->graph_failed) {
+            // capture the cooperative launch once (per H mode) into a graph
+            if (g->exec) cudaGraphExecDestroy(g->exec);
+            if (g->graph) cudaGraphDestroy(g->graph);
+            g->exec = nullptr;
+            g->graph = nullptr;
+            g->graph_f16 = -1;
+            cudaStream_t cap = nullptr;
+            cudaError_t c = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
+            if (c == cudaSuccess) c = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+            if (c == cudaSuccess) {
+                const cudaError_t c2 = admm::launch_waves(gp, g->all_map, W, g->all_ctas, g->all_chunks, f16,
+                                                          g->all_smem, cap);
+                c = cudaStreamEndCapture(cap, &g->graph);
+                if (c2 != cudaSuccess) c = c2;
+            }
+            size_t nodes = 1;
+            if (c == cudaSuccess) c = cudaGraphGetNodes(g->graph, &g->node, &nodes);
+            if (c == cudaSuccess && nodes != 1) c = cudaErrorInvalidValue;
+            if (c == cudaSuccess) c = cudaGraphInstantiate(&g->exec, g->graph, 0);
+            if (cap) cudaStreamDestroy(cap);
+            if (c == cudaSuccess) {
+                g->graph_f16 = f16 ? 1 : 0;
+            } else {
+                // no graph: launch directly from now on
+                cudaGetLastError();
+                if (g->exec) cudaGraphExecDestroy(g->exec);
+                if (g->graph) cudaGraphDestroy(g->graph);
+                g->exec = nullptr;
+                g->graph = nullptr;
+                g->graph_failed = true;
+            }
+        }
+        if (g->exec) {
+            // this call's arguments (iteration counts, history slots) into the captured node
+            cudaKernelNodeParams kp;
+            std::memset(&kp, 0, sizeof kp);
+            const int* map = g->all_map;
+            int waves = W;
+            void* args[] = {&gp, const_cast<int**>(&map), &waves};
+            kp.func = admm::waves_kernel(g->all_chunks, f16);
+            kp.gridDim = dim3(g->all_ctas);
+            kp.blockDim = dim3(admm::kIterThreads);
+            kp.sharedMemBytes = static_cast<unsigned>(g->all_smem);
+            kp.kernelParams = args;
+            e = cudaGraphExecKernelNodeSetParams(g->exec, g->node, &kp);
+            if (e == cudaSuccess) e = cudaGraphLaunch(g->exec, st);
+        } else {
+            e = admm::launch_waves(gp, g->all_map, W, g->all_ctas, g->all_chunks, f16, g->all_smem, st);
+        }
         if (e != cudaSuccess) return gfail(g, ADMM_ECUDA, "group launch failed: %s", cudaGetErrorString(e));
         return finalize_group_records(g, all, iters, st);
     }
@@ -2326,6 +2386,11 @@ int admm_group_info(const admm_group_t* g, int32_t* waves, int32_t* ctas, int32_
 int admm_group_launches(const admm_group_t* g) {
     if (!g) return -1;
     return g->one_launch ? 1 : static_cast<int>(g->waves.size());
+}
+
+int admm_group_uses_graph(const admm_group_t* g) {
+    if (!g) return -1;
+    return g->exec ? 1 : 0;
 }
 
 void admm_group_destroy(admm_group_t* g) {

@@ -198,6 +198,9 @@ cudaError_t launch_group(const GroupParams& gp, const int* cta_prob, const int* 
 // CTA indices.
 cudaError_t launch_waves(const GroupParams& gp, const int* cta_map, int waves, int ctas, int chunks, bool f16,
                          int smem, cudaStream_t stream);
+// the kernel of launch_waves, and its shared-memory opt-in (outside any capture)
+void* waves_kernel(int chunks, bool f16);
+cudaError_t prepare_waves(int chunks, bool f16, int smem);
 bool group_stage_geometry_ok(const IterArgs& a, int chunks, bool f16);
 
 // Sum the per-CTA residual partials of iteration kabs into the history ring.

@@ -1166,12 +1166,18 @@ cudaError_t launch_group(const GroupParams& gp, const int* cta_prob, const int* 
     return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kIterThreads), args, static_cast<size_t>(smem), stream);
 }
 
+void* waves_kernel(int chunks, bool f16) { return f16 ? pick_waves_t<true>(chunks) : pick_waves_t<false>(chunks); }
+
+cudaError_t prepare_waves(int chunks, bool f16, int smem) {
+    void* fn = waves_kernel(chunks, f16);
+    if (!fn) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t launch_waves(const GroupParams& gp, const int* cta_map, int waves, int ctas, int chunks, bool f16,
                          int smem, cudaStream_t stream) {
-    void* fn = f16 ? pick_waves_t<true>(chunks) : pick_waves_t<false>(chunks);
+    void* fn = waves_kernel(chunks, f16);
     if (!fn) return cudaErrorInvalidValue;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e != cudaSuccess) return e;
     void* args[] = {const_cast<GroupParams*>(&gp), const_cast<int**>(&cta_map), &waves};
     return cudaLaunchCooperativeKernel(fn, dim3(ctas), dim3(kIterThreads), args, static_cast<size_t>(smem), stream);
 }

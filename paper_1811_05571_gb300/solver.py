@@ -382,7 +382,8 @@ class Group:
 
     def info(self):
         waves, ctas = B.admm_group_info(self.g, len(self.solvers))
-        return {"waves": waves, "ctas": ctas, "launches": B.admm_group_launches(self.g)}
+        return {"waves": waves, "ctas": ctas, "launches": B.admm_group_launches(self.g),
+                "graph": B.admm_group_uses_graph(self.g)}
 
     def close(self) -> None:
         if getattr(self, "g", None):

@@ -92,6 +92,7 @@ def test_group_of_several_waves_runs_in_one_launch():
     assert info["waves"] >= 2 and info["launches"] == 1, info
     g.iterate(25)
     g.iterate(15)
+    assert g.info()["graph"] == 1, "the one launch is replayed from a captured CUDA graph"
     for (p, M, N, rho), s in zip(probs, solvers):
         assert s.status() == 0
         assert s.info()["iterations"] == 40
