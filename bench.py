@@ -74,6 +74,8 @@ def parse_args(argv=None):
     ap.add_argument("--no-cra", action="store_true",
                     help="skip the CRA-shaped 1440x32768 workload in the three splits")
     ap.add_argument("--no-small", action="store_true", help="skip the 256x4096 workload")
+    ap.add_argument("--no-sharded", action="store_true",
+                    help="skip the sharded iteration of the headline problem on one GPU")
     ap.add_argument("--no-time-to-tol", action="store_true",
                     help="skip the time-to-1e-4 comparison of FP16+polish against plain complex64")
     ap.add_argument("--l2-keep-mb", type=float, default=None,
@@ -806,6 +808,40 @@ def small_workload(pkg, stream, dev, barrier, iters: int = 300, reps: int = 5) -
             "note": "H is L2-resident: latency bound, HBM fraction not meaningful"}
 
 
+def sharded_one_gpu(pkg, stream, dev, barrier, peaks, ranks: int = 2, iters: int = 10) -> dict:
+    """The sharded iteration (Section IV) of the headline workload's consensus
+    split with its 16 row blocks on `ranks` ranks, every rank a handle of its
+    8192/ranks rows on this one GPU and the consensus sums exchanged in this
+    process (sharded.LocalComm).  Per iteration: each rank's u-step launch over
+    its rows, the n-value sums, each rank's v/s update; CUDA events on the
+    stream.  The exchange a multi-GPU run would do over NCCL is a host-side
+    sum here, so the time is the ranks' kernels one after the other plus the
+    exchange: a check of the sharded path at full size, not a multi-GPU
+    timing."""
+    import torch
+    import synth
+    from paper_1811_05571_gb300 import sharded as SH
+    H, g, _, lam = synth.gaussian_problem_device(C3_M, C3_N, C3_NNZ, C3_SEED, device=dev)
+    lays = [SH.ShardLayout(C3_M, C3_N, C3_BLOCKS, 1, ranks, 1, r) for r in range(ranks)]
+    engines = [SH.CudaShardEngine(H, g, lay, lam, 1.0) for lay in lays]
+    del H, g
+    torch.cuda.synchronize()
+    torch.cuda.empty_cache()
+    sol = SH.ShardedSolver(list(zip(lays, engines)), SH.LocalComm(lays), 1.0)
+    sol.iterate(2)
+    barrier()
+    t0 = time.perf_counter()
+    sol.iterate(iters)
+    barrier()
+    ms = (time.perf_counter() - t0) / iters * 1e3
+    for e in engines:
+        e.close()
+    alg = 2 * C3_M * C3_N * 8 + state_bytes(C3_BLOCKS, C3_N)
+    return {"workload": f"headline problem shape (device generator), consensus 16x1 over {ranks} ranks on one GPU",
+            "ranks": ranks, "ms_per_iter": ms, "alg_gbs": alg / ms / 1e6,
+            "timing": "host clock around synchronised iterations (the exchange runs on the host)"}
+
+
 def run_ours(args) -> None:
     import numpy as np
     import torch
@@ -937,6 +973,8 @@ def run_ours(args) -> None:
         extra["uneven_problems"] = uneven_problems(pkg, stream, dev, barrier, peaks=peaks)
     if not args.no_direct:
         extra["direct_form"] = direct_form(pkg, stream, dev, barrier, peaks=peaks)
+    if not args.no_sharded:
+        extra["sharded_one_gpu"] = sharded_one_gpu(pkg, stream, dev, barrier, peaks)
 
     traffic = load_traffic()
     tr = traffic.get("c3") if traffic else None

@@ -920,6 +920,7 @@ void fill_args(admm_t* h, const Plan& pl, const PlanBuffers& b, int iters, int c
     a.sigma_global = pl.sigma_global ? 1 : 0;
     a.red_single = pl.red_single ? 1 : 0;
     a.pgroups = pl.groups;
+    a.chunks = pl.chunks;
     a.rho = static_cast<float>(h->rho);
     a.rho_d = h->rho;
     a.kappa = static_cast<float>(h->lambda / (h->M * h->rho));
@@ -2115,11 +2116,13 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
         ch_all = std::max(ch_all, ch);
         wave_P[wi] = P;
     }
+    // with one launch every problem keeps its own chunk count (the kernel
+    // switches per problem)
+    const bool own_chunks = one_launch;
     for (size_t wi = 0; wi < g->waves.size(); ++wi) {
         auto& w = g->waves[wi];
         std::vector<int>& P = wave_P[wi];
-        if (one_launch) w.chunks = ch_all;
-        const int ch = w.chunks;
+        const int ch = own_chunks ? 0 : w.chunks;
         w.ctas = 0;
         w.smem = 0;
         std::vector<int> cta_map;
@@ -2132,6 +2135,8 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
             const char* why = "";
             int code = admm::make_plan(h->m, h->n, h->M, h->N, h->row_off, h->col_off, P[t], limit, pr.pl, &why, ch, 1);
             if (code) return bail(gfail(g, code, "problem %d with %d chunks: %s", q, ch, why));
+            if (!own_chunks && pr.pl.chunks != w.chunks)
+                return bail(gfail(g, ADMM_EUNSUPPORTED, "problem %d: %d chunks in a wave of %d", q, pr.pl.chunks, w.chunks));
             w.smem = std::max(w.smem, pr.pl.smem);
             for (int c = 0; c < pr.pl.P; ++c) {
                 cprob.push_back(static_cast<int>(t));
@@ -2173,7 +2178,7 @@ int admm_group_setup(admm_group_t** out, admm_t* const* handles, int32_t count, 
             cudaMemcpy(w.cta_map, cta_map.data(), cta_map.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess)
             return bail(gfail(g, ADMM_ENOMEM, "device allocation failed for a wave"));
     }
-    if (one_launch) {
+    if (own_chunks) {
         const int W = static_cast<int>(g->waves.size());
         int C = 0, smem = 0;
         for (const auto& w : g->waves) {
@@ -2264,7 +2269,7 @@ int admm_group_iterate(admm_group_t* g, int32_t iters, void* stream) {
         std::vector<int> all(count);
         for (int q = 0; q < count; ++q) {
             all[q] = q;
-            const int code = group_args(g, q, iters, f16, g->all_chunks, st, gp.a[q], gp.tmap[q]);
+            const int code = group_args(g, q, iters, f16, g->probs[q].pl.chunks, st, gp.a[q], gp.tmap[q]);
             if (code) return code;
             // a CTA that reaches a later wave's problem early waits at its first
             // grid barrier while the earlier waves finish

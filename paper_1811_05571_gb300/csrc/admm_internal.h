@@ -122,6 +122,7 @@ struct IterArgs {
     int off_ring, off_full, off_empty, off_ws, off_rs, off_gs, off_red, off_sigma, off_misc;
     int red_lanes, ws_all, ws_rows, sigma_global, red_single;
     int pgroups;          // column groups per CTA (1 or 2): partial products per row = P * pgroups
+    int chunks;           // the plan's chunk count (the kernel instance of a one-launch group)
     float rho, kappa, inv_M;
     double rho_d;
     const int* row_off;

@@ -1019,8 +1019,9 @@ __global__ void __launch_bounds__(kIterThreads, 1)
 // All waves of a group in one cooperative launch: in wave w, CTA b runs local
 // CTA cta_map[W C + w C + b] of problem cta_map[w C + b] (-1: idle in that wave).
 // A CTA that finishes its wave-w problem early goes on to its wave-(w+1)
-// problem, whose grid barriers wait for that problem's other CTAs.
-template <int CH, bool F16>
+// problem, whose grid barriers wait for that problem's other CTAs.  Each
+// problem runs the body of its own chunk count (a.chunks).
+template <bool F16>
 __global__ void __launch_bounds__(kIterThreads, 1)
     iterate_waves_kernel(const __grid_constant__ GroupParams gp, const int* __restrict__ cta_map, int waves) {
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -1028,7 +1029,14 @@ __global__ void __launch_bounds__(kIterThreads, 1)
     for (int w = 0; w < waves; ++w) {
         const int p = cta_map[w * C + blockIdx.x];
         if (p < 0) continue;
-        iterate_body<CH, F16, 1>(&gp.tmap[p], gp.a[p], cta_map[(waves + w) * C + blockIdx.x], smem);
+        const int local = cta_map[(waves + w) * C + blockIdx.x];
+        switch (gp.a[p].chunks) {
+            case 1: iterate_body<1, F16, 1>(&gp.tmap[p], gp.a[p], local, smem); break;
+            case 2: iterate_body<2, F16, 1>(&gp.tmap[p], gp.a[p], local, smem); break;
+            case 4: iterate_body<4, F16, 1>(&gp.tmap[p], gp.a[p], local, smem); break;
+            case 8: iterate_body<8, F16, 1>(&gp.tmap[p], gp.a[p], local, smem); break;
+            default: iterate_body<16, F16, 1>(&gp.tmap[p], gp.a[p], local, smem); break;
+        }
     }
 }
 
@@ -1080,21 +1088,11 @@ void* pick_group_t(int chunks) {
 
 void* pick_group(int chunks, bool f16) { return f16 ? pick_group_t<true>(chunks) : pick_group_t<false>(chunks); }
 
-template <int CH, bool F16>
-void* waves_fn() {
-    return reinterpret_cast<void*>(&iterate_waves_kernel<CH, F16>);
-}
-
+// the one-launch kernel runs problems of 1 to 16 chunks
 template <bool F16>
 void* pick_waves_t(int chunks) {
-    switch (chunks) {
-        case 1: return waves_fn<1, F16>();
-        case 2: return waves_fn<2, F16>();
-        case 4: return waves_fn<4, F16>();
-        case 8: return waves_fn<8, F16>();
-        case 16: return waves_fn<16, F16>();
-        default: return nullptr;
-    }
+    if (chunks < 1 || chunks > 16) return nullptr;
+    return reinterpret_cast<void*>(&iterate_waves_kernel<F16>);
 }
 
 }  // namespace
