@@ -667,10 +667,12 @@ def direct_form(pkg, stream, dev, barrier, peaks, iters: int = 64) -> dict:
                        f"seed {c['seed']} (device generator), lambda 0.05 max|H^H g|, rho {c['rho']}",
            "iters_per_call": iters, "splits": {}}
 
-    def measure(M, N, form):
+    def measure(M, N, form, factor_pass=0):
         t0 = time.perf_counter()
         with torch.cuda.stream(stream):
             s = pkg.Solver(H, g, M, N, lam, c["rho"], stream=stream, form=form)
+            if factor_pass:
+                s.set_option(pkg.ADMM_OPT_DIR_FACTOR_PASS, factor_pass)
         torch.cuda.synchronize()
         setup_ms = (time.perf_counter() - t0) * 1e3
         info = s.info()
@@ -691,13 +693,17 @@ def direct_form(pkg, stream, dev, barrier, peaks, iters: int = 64) -> dict:
         else:
             alg = 2 * info["h_bytes"] + info["factor_bytes"] + state
         s.close()
-        return {"factor_form": form, "us_per_iter": us, "iters_per_s": 1e6 / us, "alg_bytes_per_iter": alg,
+        return {"factor_form": form, "factor_pass": ("tiles" if info["rows_per_stage"] == 64 else "rows")
+                if form == "direct" else None,
+                "us_per_iter": us, "iters_per_s": 1e6 / us, "alg_bytes_per_iter": alg,
                 "gbs": alg / us / 1e3, "frac": alg / us / 1e3 / peaks["hbm_gbs"],
                 "factor_bytes": info["factor_bytes"], "setup_ms": setup_ms,
                 "setup_gram_ms": info["setup_gram_ms"], "setup_factor_ms": info["setup_factor_ms"]}
 
     for M, N in c["splits"]:
         out["splits"][f"{M}x{N}"] = measure(M, N, "direct")
+    # the full-factor-row pass beside the lower-triangle tiles
+    out["rows_pass_8x1"] = measure(8, 1, "direct", factor_pass=1)
     lem = measure(8, 1, "lemma")
     out["lemma_8x1"] = lem
     out["speedup_8x1"] = lem["us_per_iter"] / out["splits"]["8x1"]["us_per_iter"]

@@ -85,6 +85,15 @@ extern "C" {
 #define ADMM_OPT_RECORD_ITERS  8  /* record the next `value` iterations for admm_backward
                                      (their shrinkage arguments a and factor solutions w);
                                      0 turns recording off.  Resets the state. */
+#define ADMM_OPT_DIR_FACTOR_PASS 9  /* direct form: how u_b = L_b q_b reads the factors.  2: the
+                                     lower triangle of the Hermitian L_b only, in 64 x 64 tiles
+                                     (about half the bytes; blocks of 256 columns and more, else
+                                     ADMM_EUNSUPPORTED): each tile adds L_IJ q_J to the rows of
+                                     panel I and, below the diagonal, L_IJ^H q_I to those of panel
+                                     J, summed per row in a fixed order; 1: full factor rows (plain
+                                     loads, or bulk copies for blocks of 1024-2048 columns); 0 (the
+                                     default): 2 for blocks of 1024 columns and more, else 1.  The
+                                     lemma form ignores it. */
 #define ADMM_OPT_H_FP16        6  /* 1: stream an FP16 copy of H (half the bytes per pass);
                                      0: stream the complex64 H (the default).  The first 1
                                      builds the copy: every 64-row group g of H gets the scale
@@ -117,14 +126,18 @@ typedef struct admm_info {
     int32_t ctas;             /* CTAs of the persistent iteration kernel (one per SM at most);
                                  direct form: CTAs of the factor pass */
     int32_t rows_per_stage;   /* rows of H per pipeline stage; direct form: factor rows per
-                                 stage of the streamed factor pass (0: plain loads) */
-    int32_t stages;           /* depth of the TMA pipeline (direct form: of the factor ring) */
+                                 stage of the streamed factor pass (0: plain loads; 64: the
+                                 tile pass over the lower triangles) */
+    int32_t stages;           /* depth of the TMA pipeline (direct form: of the factor ring; the
+                                 tile pass: slots of its ring of 16-row tile pieces) */
     int32_t slab_cols;        /* widest column slab owned by one CTA (0 in the direct form) */
     int32_t smem_bytes;       /* dynamic shared memory of the iteration kernel (direct form:
-                                 of the streamed factor pass, 0 with plain loads) */
+                                 of the streamed factor pass or the tile pass, 0 with plain
+                                 loads) */
     int32_t num_sms;
     int64_t h_bytes;          /* bytes of H streamed by one pass (m * n * 8) */
-    int64_t factor_bytes;     /* bytes of all cached factors (complex64) */
+    int64_t factor_bytes;     /* bytes of all cached factors (complex64); with the direct form's
+                                 tile pass, of the lower-triangle tiles an iteration reads */
     int64_t state_bytes;      /* bytes of v, s, u, estimated data and scratch */
     double setup_gram_ms;     /* device time of the Gram products */
     double setup_factor_ms;   /* device time of the FP64 Cholesky and inverse */

@@ -12,7 +12,8 @@ from ._binding import (  # noqa: F401
     ADMM_C64, ADMM_C128, ADMM_OK, ADMM_EINVAL, ADMM_ENOMEM, ADMM_ECUDA, ADMM_ENOTPD,
     ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED,
     ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS,
-    ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ADMM_OPT_L2_PREFETCH_BYTES, ADMM_OPT_RECORD_ITERS, ABI_VERSION,
+    ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ADMM_OPT_L2_PREFETCH_BYTES, ADMM_OPT_RECORD_ITERS,
+    ADMM_OPT_DIR_FACTOR_PASS, ABI_VERSION,
     ADMM_FORM_LEMMA, ADMM_FORM_DIRECT, ADMM_FORM_AUTO,
     AdmmError, load, library_path,
     admm_abi_version, admm_strerror, admm_partition, admm_comm_elements, admm_plan, admm_setup, admm_setup_form, admm_iterate,

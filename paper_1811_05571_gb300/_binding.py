@@ -21,6 +21,7 @@ ADMM_ENONFINITE, ADMM_ETIMEOUT, ADMM_EUNSUPPORTED, ADMM_EDIVERGED = 5, 6, 7, 8
 ADMM_C64, ADMM_C128 = 0, 1
 ADMM_OPT_TIMEOUT_NS, ADMM_OPT_HIST_CAP, ADMM_OPT_BARRIER_EXTRA, ADMM_OPT_TRACE_ITERS = 1, 2, 3, 4
 ADMM_OPT_L2_KEEP_BYTES, ADMM_OPT_H_FP16, ADMM_OPT_L2_PREFETCH_BYTES, ADMM_OPT_RECORD_ITERS = 5, 6, 7, 8
+ADMM_OPT_DIR_FACTOR_PASS = 9
 ADMM_FORM_LEMMA, ADMM_FORM_DIRECT, ADMM_FORM_AUTO = 0, 1, 2
 ABI_VERSION = 5
 

@@ -34,6 +34,14 @@ struct DirectState {
     int* stop_pending = nullptr;
     int npitch = 0, njmax = 0, S = 1, ccn = 1, ctas = 1, frows = 0, hrows = 0, nchunks = 0, ncnt = 0;
     int fac_stream = 0, fac_ctas = 0, fac_ns = 0, fac_stage = 0, fitems = 0;   // streamed factor pass
+    // the tile pass over the lower triangles (blocks of kDirHermMinCols columns and more)
+    int herm = 0;                  // the tiles exist
+    int pass = 0;                  // ADMM_OPT_DIR_FACTOR_PASS: 0 auto, 1 full rows, 2 tiles
+    float2 *Lt = nullptr, *RP = nullptr, *CP = nullptr;
+    long long* T_off = nullptr;    // P + 1
+    int4* T_seq = nullptr;         // ntiles: the pass order, {index, p, I, J}
+    long long ntiles = 0;
+    int herm_ctas = 0;
     int64_t bytes = 0;
     bool c_valid = false;          // C = H_i^H g_i matches g (one column block)
     bool q_valid = false;          // Q of the current iteration matches C, v, s and rho
@@ -152,7 +160,8 @@ void free_all(admm_t* h) {
     for (void* p : ptrs)
         if (p) cudaFree(p);
     DirectState& d = h->dir;
-    void* dptrs[] = {d.C, d.Q, d.part, d.cnt, d.ints, d.L_off, d.res_chunk, d.stop_pending};
+    void* dptrs[] = {d.C, d.Q, d.part, d.cnt, d.ints, d.L_off, d.res_chunk, d.stop_pending,
+                     d.Lt, d.RP, d.CP, d.T_off, d.T_seq};
     for (void* p : dptrs)
         if (p) cudaFree(p);
     if (d.g1) cudaGraphExecDestroy(d.g1);
@@ -656,7 +665,8 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
     const int P = h->M * h->N;
     const int mimax = h->plan.mimax;
     d.njmax = njmax;
-    d.npitch = round_up(njmax, 4);
+    d.herm = njmax >= admm::kDirHermMinCols && h->M <= admm::kDirHermMaxRowBlocks ? 1 : 0;
+    d.npitch = d.herm ? round_up(njmax, admm::kDirTile) : round_up(njmax, 4);   // tiles read whole q panels
     // column tiles: pairs from each block's first column rounded down to even
     int pairs = 1;
     for (int j = 0; j < h->N; ++j) {
@@ -721,11 +731,46 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
     // several column blocks, C = H_i^H g_i once per data vector with one)
     const size_t nc = h->N == 1 ? vec : 1, np = static_cast<size_t>(d.S) * vec;
     const size_t nq = h->N == 1 ? 2 * vec : vec;   // one column block: a slot per iteration parity
-    const bool ok = dalloc(&d.C, nc) == cudaSuccess && dalloc(&d.Q, nq) == cudaSuccess &&
-                    dalloc(&d.part, np) == cudaSuccess && dalloc(&d.cnt, d.ncnt) == cudaSuccess &&
-                    dalloc(&d.ints, ints.size()) == cudaSuccess && dalloc(&d.L_off, off.size()) == cudaSuccess &&
-                    dalloc(&d.res_chunk, static_cast<size_t>(d.nchunks) * 5) == cudaSuccess &&
-                    dalloc(&d.stop_pending, 1) == cudaSuccess;
+    bool ok = dalloc(&d.C, nc) == cudaSuccess && dalloc(&d.Q, nq) == cudaSuccess &&
+              dalloc(&d.part, np) == cudaSuccess && dalloc(&d.cnt, d.ncnt) == cudaSuccess &&
+              dalloc(&d.ints, ints.size()) == cudaSuccess && dalloc(&d.L_off, off.size()) == cudaSuccess &&
+              dalloc(&d.res_chunk, static_cast<size_t>(d.nchunks) * 5) == cudaSuccess &&
+              dalloc(&d.stop_pending, 1) == cudaSuccess;
+    if (ok && d.herm) {
+        // block p's tiles (I, J), J <= I, indexed from T_off[p]
+        std::vector<long long> toff(P + 1, 0);
+        std::vector<int> nt(P, 0);
+        for (int q = 0; q < P; ++q) {
+            const int j = q % h->N;
+            nt[q] = (h->col_off[j + 1] - h->col_off[j] + admm::kDirTile - 1) / admm::kDirTile;
+            toff[q + 1] = toff[q] + static_cast<long long>(nt[q]) * (nt[q] + 1) / 2;
+        }
+        d.ntiles = toff[P];
+        // the pass order: tile column J, then block, then tile row I
+        std::vector<int4> seq;
+        seq.reserve(static_cast<size_t>(d.ntiles));
+        const int ntmax = *std::max_element(nt.begin(), nt.end());
+        for (int J = 0; J < ntmax; ++J)
+            for (int q = 0; q < P; ++q)
+                for (int I = J; I < nt[q]; ++I)
+                    seq.push_back(make_int4(static_cast<int>(toff[q] + static_cast<long long>(I) * (I + 1) / 2 + J),
+                                            q, I, J));
+        const size_t tile = static_cast<size_t>(admm::kDirTile) * admm::kDirTile;
+        ok = dalloc(&d.Lt, static_cast<size_t>(d.ntiles) * tile) == cudaSuccess &&
+             dalloc(&d.RP, static_cast<size_t>(d.ntiles) * admm::kDirTile) == cudaSuccess &&
+             dalloc(&d.CP, static_cast<size_t>(d.ntiles) * admm::kDirTile) == cudaSuccess &&
+             dalloc(&d.T_off, toff.size()) == cudaSuccess && dalloc(&d.T_seq, seq.size()) == cudaSuccess;
+        int per_sm = 0;
+        if (ok && (admm::herm_per_sm(&per_sm) != cudaSuccess || per_sm < 1)) {
+            cudaGetLastError();
+            d.herm = 0;   // no tile pass on this device: the full-row passes remain
+        }
+        d.herm_ctas = h->num_sms * std::max(per_sm, 1);
+        if (ok && d.herm) {
+            CK(h, cudaMemcpy(d.T_off, toff.data(), toff.size() * sizeof(long long), cudaMemcpyHostToDevice));
+            CK(h, cudaMemcpy(d.T_seq, seq.data(), seq.size() * sizeof(int4), cudaMemcpyHostToDevice));
+        }
+    }
     if (!ok) return ADMM_ENOMEM;
     // Q and C padding entries stay zero (the factor pass reads whole pairs)
     CK(h, cudaMemset(d.C, 0, nc * sizeof(float2)));
@@ -735,7 +780,22 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
     CK(h, cudaMemcpy(d.ints, ints.data(), ints.size() * sizeof(int), cudaMemcpyHostToDevice));
     CK(h, cudaMemcpy(d.L_off, off.data(), off.size() * sizeof(long long), cudaMemcpyHostToDevice));
     d.bytes = static_cast<int64_t>((nc + nq + np) * sizeof(float2) + d.nchunks * 5 * sizeof(double));
+    if (d.herm) d.bytes += static_cast<int64_t>(d.ntiles) * (admm::kDirTile * admm::kDirTile + 2 * admm::kDirTile) * 8;
     return ADMM_OK;
+}
+
+// the tile pass reads the factor's lower triangle: (re)pack it after every factorisation
+int pack_direct_tiles(admm_t* h, cudaStream_t st) {
+    const DirectState& d = h->dir;
+    if (h->form != ADMM_FORM_DIRECT || !d.herm) return ADMM_OK;
+    CK(h, admm::launch_pack_herm(h->kinv, d.L_off, d.ints + (h->N + 1), h->col_off_d, h->N, d.T_seq, d.ntiles, d.Lt,
+                                 st));
+    return ADMM_OK;
+}
+
+// the tile pass runs for this handle (forced, or by default on blocks of kDirHermAutoCols columns and more)
+bool uses_tiles(const DirectState& d) {
+    return d.herm && (d.pass == 2 || (d.pass == 0 && d.njmax >= admm::kDirHermAutoCols));
 }
 
 admm::DirectArgs direct_args(admm_t* h, int check_stop, double eps_abs, double eps_rel) {
@@ -772,6 +832,14 @@ admm::DirectArgs direct_args(admm_t* h, int check_stop, double eps_abs, double e
     a.fac_ctas = d.fac_ctas;
     a.fac_ns = d.fac_ns;
     a.fac_stage = d.fac_stage;
+    a.fac_herm = uses_tiles(d) ? 1 : 0;
+    a.Lt = d.Lt;
+    a.T_seq = d.T_seq;
+    a.T_off = d.T_off;
+    a.RP = d.RP;
+    a.CP = d.CP;
+    a.ntiles = static_cast<int>(d.ntiles);
+    a.herm_ctas = d.herm_ctas;
     a.timeout_ns = h->timeout_ns;
     a.frows = d.frows;
     a.hrows = d.hrows;
@@ -1348,6 +1416,7 @@ int admm_setup_form(admm_t** out, const void* H, const void* g, int64_t m, int64
     SETUP_CK(cudaMemcpy(&flag, h->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) return bail(fail(h, ADMM_ENONFINITE, "H or g holds NaN or Inf"));
     code = build_factors(h, st, h->H, h->kinv, true);
+    if (code == ADMM_OK && direct) code = pack_direct_tiles(h, st);
     if (code) return bail(code);
     if (!direct) {
         code = encode_tensor_map(h);
@@ -1478,10 +1547,12 @@ int admm_set_rho(admm_t* h, double rho, void* stream) {
     h->rho = rho;
     int code = build_factors(h, st, h->H, h->kinv, true);
     if (code == ADMM_OK && h->H16) code = build_factors_f16(h, st);
+    if (code == ADMM_OK) code = pack_direct_tiles(h, st);
     if (code) {
         h->rho = old;
         build_factors(h, st, h->H, h->kinv, true);
         if (h->H16) build_factors_f16(h, st);
+        pack_direct_tiles(h, st);
         return code;
     }
     h->rec_valid = false;
@@ -1577,6 +1648,14 @@ int admm_get_info(const admm_t* h, admm_info_t* info) {
         info->stages = d.fac_stream ? d.fac_ns : 0;
         info->slab_cols = 0;
         info->smem_bytes = d.fac_stream ? static_cast<int32_t>(admm::stream_smem(d.fac_ns, d.fac_stage)) : 0;
+        if (uses_tiles(d)) {
+            // the tile pass: the lower-triangle tiles through a ring of 16-row pieces
+            info->ctas = d.herm_ctas;
+            info->rows_per_stage = admm::kDirTile;
+            info->stages = admm::kHermSlots;
+            info->smem_bytes = static_cast<int32_t>(admm::herm_smem_bytes());
+            info->factor_bytes = d.ntiles * admm::kDirTile * admm::kDirTile * static_cast<int64_t>(sizeof(float2));
+        }
     }
     return ADMM_OK;
 }
@@ -1634,6 +1713,18 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
         case ADMM_OPT_L2_PREFETCH_BYTES:
             if (value < 0) return fail(h, ADMM_EINVAL, "L2 prefetch bytes must be >= 0");
             h->l2_prefetch_bytes = value;
+            return ADMM_OK;
+        case ADMM_OPT_DIR_FACTOR_PASS:
+            if (value < 0 || value > 2) return fail(h, ADMM_EINVAL, "ADMM_OPT_DIR_FACTOR_PASS takes 0, 1 or 2");
+            if (h->form != ADMM_FORM_DIRECT) return ADMM_OK;   // the lemma form has no factor pass
+            if (value == 2 && !h->dir.herm)
+                return fail(h, ADMM_EUNSUPPORTED, "the tile pass needs blocks of %d columns or more",
+                            admm::kDirHermMinCols);
+            if (h->dir.pass != static_cast<int>(value)) {
+                CK(h, cudaStreamSynchronize(h->dir.cap));
+                drop_direct_graphs(h->dir);
+                h->dir.pass = static_cast<int>(value);
+            }
             return ADMM_OK;
         case ADMM_OPT_BARRIER_EXTRA:
             if (value < 0 || value > 1024) return fail(h, ADMM_EINVAL, "barrier extra out of range");

@@ -16,7 +16,8 @@
 // done by whichever CTA increments the step's counter last; that CTA also
 // resets the counter.  No CTA waits for another; the only waits are those
 // between the producer lane and the consumer warps of one CTA of the streamed
-// factor pass (mbarriers, each bounded by the handle's timeout).
+// factor pass and of the tile pass (mbarriers, each bounded by the handle's
+// timeout).
 #include "admm_internal.h"
 #include "ptx.cuh"
 
@@ -224,6 +225,8 @@ __global__ void __launch_bounds__(kDirFacThreads) dir_q_kernel(const DirectArgs 
     }
 }
 
+__device__ void finish_record(const DirectArgs& a, long long k, int lane);
+
 // Consensus update of update chunk `chunk` (entries row0 .. row0 + 16 of
 // column block j), run by the warp that completed the chunk: v_j, s_j^i over
 // those columns (with one column block also the next iteration's q_i there),
@@ -297,8 +300,15 @@ __device__ void update_chunk(const DirectArgs& a, int j, int c0, int nj, int row
         fin = atomicAdd(a.cnt_glob, 1u) == static_cast<unsigned>(a.nchunks - 1);
     }
     if (!__shfl_sync(0xffffffffu, fin, 0)) return;
+    finish_record(a, k, lane);
+}
+
+// Residual record of iteration k from the update chunks' partials (the same
+// five norms as the persistent kernel), by the warp that finished the last
+// chunk; with the stopping test, the stop flags; then the device iteration
+// count.
+__device__ void finish_record(const DirectArgs& a, long long k, int lane) {
     __threadfence();
-    // residual record of the iteration (the same five norms as the persistent kernel)
     double acc[5] = {0, 0, 0, 0, 0};
     for (int c = lane; c < a.nchunks; c += 32) {
 #pragma unroll
@@ -416,6 +426,307 @@ __global__ void __launch_bounds__(kDirFacThreads, 2) dir_factor_kernel(const Dir
         }
         if (__shfl_sync(0xffffffffu, last, 0)) update_chunk(a, j, c0, nj, row0, chunk, k, lane);
         r += g;
+    }
+}
+
+// ---- Hermitian factor pass + update -------------------------------------------
+// L_b is Hermitian, so only its lower triangle is kept, in kDirTile x kDirTile
+// tiles (diagonal tiles whole), about half the bytes of the full factor.
+// Tile (I, J) adds L_IJ q_J to the rows of panel I and, below the diagonal,
+// L_IJ^H q_I to the rows of panel J:
+//     u_I = sum_{J <= I} L_IJ q_J + sum_{I' > I} L_I'I^H q_I'.
+// Each tile's two sums are written out and added per row in a fixed order,
+// so the result does not depend on which warp took which tile.
+
+// a slot's piece number, published by the producer before it arms the slot
+__device__ __forceinline__ void st_release_shared(int* p, int v) {
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_acquire_shared(const int* p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];" : "=r"(v) : "r"(smem_u32(p)) : "memory");
+    return v;
+}
+
+// Consumer wait for piece e in `slot`.  Different warps consume a slot's
+// successive uses, so a warp may reach its use while the slot is still two
+// phases behind, where a parity test alone would pass on the older phase:
+// first the producer's piece number for the slot must be e (the slot's phase
+// is then e's, running or complete), then the phase's parity.  Both waits are
+// bounded.
+__device__ __forceinline__ bool herm_wait_piece(const int* meta, uint64_t* full, int slot, long long e,
+                                                const DirectArgs& a) {
+    if (ld_acquire_shared(meta + slot) != static_cast<int>(e)) {
+        const long long t0 = global_timer_ns();
+        while (ld_acquire_shared(meta + slot) != static_cast<int>(e)) {
+            if (global_timer_ns() - t0 > a.timeout_ns) {
+                raise_status(a.status, ADMM_ETIMEOUT);
+                return false;
+            }
+            __nanosleep(64);
+        }
+    }
+    return mbar_wait_bounded(&full[slot], static_cast<uint32_t>((e / kHermSlots) & 1), a.status, a.timeout_ns);
+}
+
+constexpr int kHermPieces = kDirTile / kHermPieceRows;          // pieces per tile
+constexpr int kHermPieceBytes = kHermPieceRows * kDirTile * 8;  // 8 KB
+static_assert(kHermSlots % kHermPieces == 0, "a tile's pieces sit in consecutive slots");
+
+__global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel(const DirectArgs a) {
+    extern __shared__ __align__(128) unsigned char hsm[];
+    uint64_t* full = reinterpret_cast<uint64_t*>(hsm + static_cast<size_t>(kHermSlots) * kHermPieceBytes);
+    uint64_t* empty = full + kHermSlots;
+    int* meta = reinterpret_cast<int*>(empty + kHermSlots);   // piece number of each slot's current use
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int G = gridDim.x, c = blockIdx.x;
+    const int ntile = c < a.ntiles ? (a.ntiles - 1 - c) / G + 1 : 0;   // this CTA's tiles
+    // (a CTA with tiles starts before the iteration's record is written, so
+    // all of its threads read the same stop flag)
+    if (ntile == 0 || stopped(a)) return;
+    if (threadIdx.x == 0) {
+        for (int q = 0; q < kHermSlots; ++q) {
+            mbar_init(&full[q], 1);
+            mbar_init(&empty[q], 1);
+            meta[q] = -1;
+        }
+        fence_mbarrier_init();
+    }
+    __syncthreads();
+    if (warp == kHermWarps) {
+        // producer: piece e = kHermPieces i + h of the CTA's stream into slot e % kHermSlots
+        if (lane != 0) return;
+        const uint64_t pol = policy_evict_first();   // every tile is read once per iteration
+        long long e = 0;
+        bool ok = true;
+        for (int i = 0; i < ntile && ok; ++i) {
+            const unsigned char* src = reinterpret_cast<const unsigned char*>(
+                a.Lt + (static_cast<size_t>(c) + static_cast<size_t>(i) * G) * kDirTile * kDirTile);
+            for (int h = 0; h < kHermPieces; ++h, ++e) {
+                const int slot = static_cast<int>(e % kHermSlots);
+                const uint32_t use = static_cast<uint32_t>(e / kHermSlots);
+                if (use > 0 && !mbar_wait_bounded(&empty[slot], (use - 1) & 1u, a.status, a.timeout_ns)) {
+                    ok = false;
+                    break;
+                }
+                st_release_shared(meta + slot, static_cast<int>(e));
+                mbar_arrive_expect_tx(&full[slot], static_cast<uint32_t>(kHermPieceBytes));
+                unsigned char* dst = hsm + static_cast<size_t>(slot) * kHermPieceBytes;
+                const unsigned char* sp = src + static_cast<size_t>(h) * kHermPieceBytes;
+                bulk_load_hint(dst, sp, kHermPieceBytes / 2, &full[slot], pol);
+                bulk_load_hint(dst + kHermPieceBytes / 2, sp + kHermPieceBytes / 2, kHermPieceBytes / 2, &full[slot],
+                               pol);
+            }
+        }
+        // every copy into this CTA's shared memory lands before the CTA ends
+        // (earlier pieces' slots were consumed and reused)
+        for (long long q = e - 1; q >= 0 && q >= e - kHermSlots; --q)
+            mbar_wait_bounded(&full[q % kHermSlots], static_cast<uint32_t>((q / kHermSlots) & 1), a.status,
+                              a.timeout_ns);
+        return;
+    }
+    const long long k = __ldcg(a.k_done);
+    const size_t qslot = a.N == 1 ? static_cast<size_t>(k & 1) * a.P * a.npitch : 0;
+    // the warp's next tile and its q pairs, fetched one tile ahead
+    int4 tn = make_int4(0, 0, 0, 0);
+    float4 nqJ = make_float4(0.f, 0.f, 0.f, 0.f), nqI = nqJ;
+    auto fetch = [&](int i) {
+        tn = __ldg(a.T_seq + c + static_cast<long long>(i) * G);
+        const float2* qb = a.Q + qslot + static_cast<size_t>(tn.y) * a.npitch;
+        nqJ = __ldg(reinterpret_cast<const float4*>(qb + tn.w * kDirTile) + lane);
+        nqI = __ldg(reinterpret_cast<const float4*>(qb + tn.z * kDirTile) + lane);
+    };
+    if (warp < ntile) fetch(warp);
+    for (int i = warp; i < ntile; i += kHermWarps) {
+        const int t = tn.x, I = tn.z, J = tn.w;
+        const float4 qJ = nqJ, qI = nqI;
+        if (i + kHermWarps < ntile) fetch(i + kHermWarps);
+        const bool diag = I == J;
+        float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
+        bool ok = true;
+        for (int h = 0; h < kHermPieces; ++h) {
+            const long long e = static_cast<long long>(i) * kHermPieces + h;
+            const int slot = static_cast<int>(e % kHermSlots);
+            if (!herm_wait_piece(meta, full, slot, e, a)) {
+                ok = false;
+                break;
+            }
+            const float4* T4 = reinterpret_cast<const float4*>(hsm + static_cast<size_t>(slot) * kHermPieceBytes);
+#pragma unroll
+            for (int gg = 0; gg < kHermPieceRows / 8; ++gg) {
+                float4 l[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) l[q] = T4[(8 * gg + q) * (kDirTile / 2) + lane];
+                float2 racc[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    racc[q] = make_float2(0.f, 0.f);
+                    cfma(racc[q], make_float2(l[q].x, l[q].y), make_float2(qJ.x, qJ.y));
+                    cfma(racc[q], make_float2(l[q].z, l[q].w), make_float2(qJ.z, qJ.w));
+                }
+                const int row0 = h * kHermPieceRows + 8 * gg;   // tile row of l[0]
+                const float2 rs = lanes_sum8(racc, lane);
+                if ((lane & 3) == 0) stcg2(a.RP + static_cast<size_t>(t) * kDirTile + row0 + (lane >> 2), rs);
+                if (!diag) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        // q_I of tile row row0 + q, held by lane (row0 + q) / 2
+                        const int src = (row0 >> 1) + (q >> 1);
+                        const float2 qi = make_float2(__shfl_sync(0xffffffffu, (q & 1) ? qI.z : qI.x, src),
+                                                      __shfl_sync(0xffffffffu, (q & 1) ? qI.w : qI.y, src));
+                        cfma_conj(c0, make_float2(l[q].x, l[q].y), qi);
+                        cfma_conj(c1, make_float2(l[q].z, l[q].w), qi);
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&empty[slot]);
+        }
+        if (!ok) break;
+        if (!diag)   // the tile's column sums
+            __stcg(reinterpret_cast<float4*>(a.CP + static_cast<size_t>(t) * kDirTile) + lane,
+                   make_float4(c0.x, c0.y, c1.x, c1.y));
+    }
+}
+
+// ---- panel sums + update (after the tile pass) ---------------------------------
+// One CTA per update chunk (kDirChunk columns of column block j).  Warp w takes
+// the replicas i = w, w + 8, ...: the chunk's rows of u_b, each the sum of its
+// NT tile sums in tile order (lanes 0-15 the first half of the tiles, 16-31
+// the second, sixteen loads in flight, then the two halves added), kept in
+// shared memory with s_i and, with one column block, H_i^H g_i.  Then v over
+// the chunk (warp 0, replicas in order), the duals and the next q per replica,
+// and the chunk's residual partials (warps in order); the CTA that adds the
+// last chunk writes the iteration's record.  Shared memory: 3 M kDirChunk + kDirChunk
+// complex values.
+__global__ void __launch_bounds__(kDirFacThreads) dir_herm_update_kernel(const DirectArgs a) {
+    extern __shared__ float2 hred[];
+    if (stopped(a)) return;
+    constexpr int kWarps = kDirFacThreads / 32;
+    float2* us = hred;                                  // M x kDirChunk: u
+    float2* ss = us + a.M * kDirChunk;                  // s before the update
+    float2* cs = ss + a.M * kDirChunk;                  // H_i^H g_i (one column block)
+    float2* vs = cs + a.M * kDirChunk;                  // kDirChunk: the new v
+    __shared__ float dred[kWarps][5];
+    __shared__ int last;
+    const int chunk = blockIdx.x;
+    int j = 0;
+    while (a.chunk_off[j + 1] <= chunk) ++j;
+    const int c0 = a.col_off[j], nj = a.col_off[j + 1] - c0;
+    const int row0 = (chunk - a.chunk_off[j]) * kDirChunk;   // the chunk's first column in the block
+    const int X = row0 / kDirTile, rr = row0 - X * kDirTile;
+    const int NT = (nj + kDirTile - 1) / kDirTile;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int r = lane & (kDirChunk - 1), half = lane >> 4;
+    const bool inb = row0 + r < nj;
+    const int col = c0 + row0 + r;
+    const long long k = __ldcg(a.k_done);
+    const int hK = (NT + 1) >> 1;
+    const int kb = half ? hK : 0, ke = half ? NT : hK;
+    for (int i = warp; i < a.M; i += kWarps) {
+        const int p = i * a.N + j;
+        const long long tb = a.T_off[p];
+        float2 sv = make_float2(0.f, 0.f), cv = sv;
+        if (half == 0 && inb) {
+            sv = ldcg2(a.s + static_cast<size_t>(i) * a.ld + col);
+            if (a.N == 1) cv = ldcg2(a.C + static_cast<size_t>(i) * a.npitch + col);
+        }
+        // the contributions to row row0 + r: tiles (X, kk) for kk <= X (row
+        // sums), tiles (kk, X) for kk > X (column sums)
+        float2 acc = make_float2(0.f, 0.f);
+        for (int k0 = kb; k0 < ke; k0 += 16) {
+            float2 x[16];
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                const int kk = k0 + q;
+                const float2* src = kk <= X ? a.RP + (tb + X * (X + 1) / 2 + kk) * kDirTile
+                                            : a.CP + (tb + static_cast<long long>(kk) * (kk + 1) / 2 + X) * kDirTile;
+                x[q] = kk < ke ? ldcg2(src + rr + r) : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int q = 0; q < 16; ++q) {
+                acc.x += x[q].x;
+                acc.y += x[q].y;
+            }
+        }
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 16);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
+        if (half == 0) {
+            us[i * kDirChunk + r] = acc;
+            ss[i * kDirChunk + r] = sv;
+            cs[i * kDirChunk + r] = cv;
+            if (inb) stcg2(a.u + static_cast<size_t>(i) * a.ld + col, acc);
+        }
+    }
+    __syncthreads();
+    float d[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    if (warp == 0 && half == 0 && inb) {
+        float2 sum = make_float2(0.f, 0.f);
+        for (int i = 0; i < a.M; ++i) {
+            sum.x += us[i * kDirChunk + r].x + ss[i * kDirChunk + r].x;
+            sum.y += us[i * kDirChunk + r].y + ss[i * kDirChunk + r].y;
+        }
+        const float2 vv = ldcg2(a.v + col);
+        const float2 vn = shrink(make_float2(sum.x * a.inv_M, sum.y * a.inv_M), a.kappa);
+        d[1] = sq2(make_float2(vn.x - vv.x, vn.y - vv.y));
+        d[3] = sq2(vn);
+        vs[r] = vn;
+        stcg2(a.v + col, vn);
+    }
+    __syncthreads();
+    if (half == 0 && inb) {
+        const float2 vn = vs[r];
+        float2* qn = a.Q + (a.N == 1 ? static_cast<size_t>((k + 1) & 1) * a.P * a.npitch : 0);
+        for (int i = warp; i < a.M; i += kWarps) {
+            const float2 uu = us[i * kDirChunk + r], so = ss[i * kDirChunk + r];
+            const float2 sn = make_float2(so.x + uu.x - vn.x, so.y + uu.y - vn.y);
+            d[0] += sq2(make_float2(uu.x - vn.x, uu.y - vn.y));
+            d[2] += sq2(uu);
+            d[4] += sq2(sn);
+            stcg2(a.s + static_cast<size_t>(i) * a.ld + col, sn);
+            if (a.N == 1) {   // q_i of the next iteration: H_i^H g_i + rho (v - s_i)
+                const float2 cv = cs[i * kDirChunk + r];
+                stcg2(qn + static_cast<size_t>(i) * a.npitch + col,
+                      make_float2(cv.x + a.rho * (vn.x - sn.x), cv.y + a.rho * (vn.y - sn.y)));
+            }
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+        for (int o = 8; o > 0; o >>= 1) d[q] += __shfl_xor_sync(0xffffffffu, d[q], o);
+        if (lane == 0) dred[warp][q] = d[q];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+            double t = 0.0;
+            for (int w = 0; w < kWarps; ++w) t += static_cast<double>(dred[w][q]);
+            __stcg(a.res_chunk + static_cast<size_t>(chunk) * 5 + q, t);
+        }
+        __threadfence();
+        last = atomicAdd(a.cnt_glob, 1u) == static_cast<unsigned>(a.nchunks - 1);
+    }
+    __syncthreads();
+    if (last && warp == 0) finish_record(a, k, lane);
+}
+
+// the tiles of the pass, in its order, from the full factors (setup, after
+// every factorisation); the parts of a tile past n_j are zero
+__global__ void pack_herm_kernel(const float2* __restrict__ L, const long long* __restrict__ L_off,
+                                 const int* __restrict__ L_pitch, const int* __restrict__ col_off, int N,
+                                 const int4* __restrict__ T_seq, long long ntiles, float2* __restrict__ Lt) {
+    const long long total = ntiles * kDirTile * kDirTile;
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+        const long long pos = e / (kDirTile * kDirTile);
+        const int w = static_cast<int>(e - pos * kDirTile * kDirTile);
+        const int4 tq = T_seq[pos];
+        const int p = tq.y, j = p % N;
+        const int nj = col_off[j + 1] - col_off[j];
+        const int r = tq.z * kDirTile + w / kDirTile, cc = tq.w * kDirTile + w % kDirTile;
+        Lt[e] = (r < nj && cc < nj) ? L[L_off[p] + static_cast<long long>(r) * L_pitch[p] + cc]
+                                    : make_float2(0.f, 0.f);
     }
 }
 
@@ -813,8 +1124,37 @@ cudaError_t launch_dir_q(const DirectArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+size_t herm_smem_bytes() {
+    return static_cast<size_t>(kHermSlots) * kHermPieceBytes + kHermSlots * (2 * sizeof(uint64_t) + sizeof(int));
+}
+
+size_t herm_update_smem(int M) { return (static_cast<size_t>(3) * M * kDirChunk + kDirChunk) * sizeof(float2); }
+
+cudaError_t herm_per_sm(int* per_sm) {
+    const int smem = static_cast<int>(herm_smem_bytes());
+    cudaError_t e = cudaFuncSetAttribute(dir_herm_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(dir_herm_update_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(herm_update_smem(kDirHermMaxRowBlocks)));
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, dir_herm_tile_kernel, (kHermWarps + 1) * 32, smem);
+}
+
+cudaError_t launch_pack_herm(const float2* L, const long long* L_off, const int* L_pitch, const int* col_off,
+                             int N, const int4* T_seq, long long ntiles, float2* Lt, cudaStream_t s) {
+    const long long total = ntiles * kDirTile * kDirTile;
+    const int blocks = static_cast<int>(std::min<long long>((total + 255) / 256, 8192));
+    pack_herm_kernel<<<blocks, 256, 0, s>>>(L, L_off, L_pitch, col_off, N, T_seq, ntiles, Lt);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dir_factor(const DirectArgs& a, cudaStream_t s) {
-    if (a.fac_stream) {
+    if (a.fac_herm) {
+        dir_herm_tile_kernel<<<a.herm_ctas, (kHermWarps + 1) * 32, herm_smem_bytes(), s>>>(a);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        dir_herm_update_kernel<<<a.nchunks, kDirFacThreads, herm_update_smem(a.M), s>>>(a);
+    } else if (a.fac_stream) {
         const size_t smem = stream_smem(a.fac_ns, a.fac_stage);
         dir_factor_stream_kernel<<<a.fac_ctas, (kDirBulkWarps + 1) * 32, smem, s>>>(a);
     } else {

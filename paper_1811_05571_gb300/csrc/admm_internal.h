@@ -263,6 +263,14 @@ constexpr int kDirBulkMinCols = 1024;  // blocks the streamed factor pass takes:
 constexpr int kDirBulkMaxCols = 2048;  // (8 to 16 KB rows; narrower factors are latency-bound and
                                        // measured faster with the plain-load pass)
 constexpr int kDirMaxCols = 12288;   // widest block of the direct branch (u_b staged in shared memory)
+constexpr int kDirTile = 64;         // Hermitian factor pass: 64 x 64 tiles of each factor's lower triangle
+constexpr int kDirHermMinCols = 256; // blocks this wide and wider keep their factors as such tiles
+constexpr int kDirHermAutoCols = 1024;  // ... and use them by default from this width on (narrower
+                                        // blocks have too few tiles to fill the GPU)
+constexpr int kHermWarps = 8;        // tile pass: consumer warps per CTA (and a producer), one CTA per SM
+constexpr int kHermSlots = 24;       // slots of the CTA's ring of tile pieces
+constexpr int kHermPieceRows = 16;   // tile rows per piece (8 KB)
+constexpr int kDirHermMaxRowBlocks = 512;   // the tile pass's update keeps 3 M x 16 values in shared memory
 
 struct DirectArgs {
     int m, n, ld, M, N, P;
@@ -310,6 +318,18 @@ struct DirectArgs {
     int* status;
     int* stop_flag;           // set once the stopping test passed (with check_stop)
     int* stop_pending;        // set by the update, turned into stop_flag after the row pass
+    // Hermitian factor pass: the lower triangle of every L_b in kDirTile x kDirTile
+    // tiles (diagonal tiles whole).  Block p's tile (I, J), J <= I, has the
+    // index T_off[p] + I (I + 1) / 2 + J; Lt holds the tiles in the order of the
+    // pass, T_seq[s] = {index, p, I, J} of the tile at position s.
+    int fac_herm;
+    const float2* Lt;         // ntiles x kDirTile x kDirTile, row-major tiles
+    const int4* T_seq;        // ntiles
+    const long long* T_off;   // P + 1
+    float2* RP;               // ntiles x kDirTile, by index: row sums L_IJ q_J
+    float2* CP;               // ntiles x kDirTile, by index: column sums L_IJ^H q_I (J < I)
+    int ntiles;
+    int herm_ctas;            // CTAs of the tile pass (one per SM)
     int check_stop;
     double eps_abs, eps_rel;
     float rho, kappa, inv_M;
@@ -322,6 +342,13 @@ cudaError_t launch_dir_cols(const DirectArgs& a, int mode, cudaStream_t s);
 cudaError_t launch_dir_q(const DirectArgs& a, cudaStream_t s);
 cudaError_t launch_dir_factor(const DirectArgs& a, cudaStream_t s);
 cudaError_t launch_dir_rows(const DirectArgs& a, cudaStream_t s);
+// the tiles of the tile pass from the full factors (the parts of a tile past n_j zero)
+cudaError_t launch_pack_herm(const float2* L, const long long* L_off, const int* L_pitch, const int* col_off,
+                             int N, const int4* T_seq, long long ntiles, float2* Lt, cudaStream_t s);
+// the tile pass: its shared memory, and its resident CTAs per SM (after opting
+// in to that shared memory)
+size_t herm_smem_bytes();
+cudaError_t herm_per_sm(int* per_sm);
 cudaError_t prepare_direct(int smem_optin);
 // shared memory of the streamed factor pass with `ns` stages of `stage` bytes,
 // and its resident CTAs per SM with `smem` bytes

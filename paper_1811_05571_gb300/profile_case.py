@@ -4,6 +4,12 @@ or FP16 H; `warmup` single-iteration launches, then one launch of `iters`
 iterations timed with CUDA events.
 
     python -m paper_1811_05571_gb300.profile_case --m 1024 --n 131072 --M 16 --iters 2 [--fp16]
+    python -m paper_1811_05571_gb300.profile_case --m 32768 --n 2048 --M 8 --form direct [--factor-pass 1|2]
+
+With the direct factor form (blocks with at least as many rows as columns)
+an iteration is the factor pass (and, with several column blocks, the column
+and row passes); `--factor-pass` picks the full factor rows (1) or the
+lower-triangle tiles (2).
 
 The launches of the iteration kernel are, in order: the warm-up launches, then
 the timed one (so ``ncu -k regex:iterate_kernel -s <warmup> -c 1`` captures the
@@ -25,12 +31,14 @@ def main(argv=None) -> int:
     ap.add_argument("--iters", type=int, default=2)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--fp16", action="store_true")
+    ap.add_argument("--form", choices=("lemma", "direct"), default="lemma")
+    ap.add_argument("--factor-pass", type=int, default=0)
     args = ap.parse_args(argv)
 
     import torch
 
     import synth
-    from . import Solver, load
+    from . import ADMM_OPT_DIR_FACTOR_PASS, Solver, load
 
     load()
     dev = torch.device("cuda:0")
@@ -41,7 +49,9 @@ def main(argv=None) -> int:
         rho *= (1.0 + (args.n / args.N / args.m) ** 0.5) ** 2
     st = torch.cuda.Stream()
     with torch.cuda.stream(st):
-        s = Solver(H, g, args.M, args.N, lam, rho, stream=st)
+        s = Solver(H, g, args.M, args.N, lam, rho, stream=st, form=args.form)
+        if args.factor_pass:
+            s.set_option(ADMM_OPT_DIR_FACTOR_PASS, args.factor_pass)
     torch.cuda.synchronize()
     del H, g
     if args.fp16:
@@ -58,9 +68,13 @@ def main(argv=None) -> int:
         raise RuntimeError("device status after the profiled launch")
     info = s.info()
     hb = info["h16_bytes"] if args.fp16 else info["h_bytes"]
-    alg = 2 * hb + info["factor_bytes"] + (3 * args.M + 3) * args.n * 8
+    state = (3 * args.M + 3) * args.n * 8
+    if args.form == "direct":   # no pass over H with one column block (H_i^H g_i cached and read)
+        alg = (0 if args.N == 1 else 2 * hb) + info["factor_bytes"] + state + (args.M * args.n * 8 if args.N == 1 else 0)
+    else:
+        alg = 2 * hb + info["factor_bytes"] + state
     us = a.elapsed_time(b) / args.iters * 1e3
-    print(json.dumps({"m": args.m, "n": args.n, "M": args.M, "N": args.N, "fp16": args.fp16, "us_per_iter": us,
+    print(json.dumps({"m": args.m, "n": args.n, "M": args.M, "N": args.N, "fp16": args.fp16, "form": args.form, "us_per_iter": us,
                       "alg_bytes_per_iter": alg, "gbs": alg / us / 1e3, "ctas": info["ctas"],
                       "stages": info["stages"], "rows_per_stage": info["rows_per_stage"]}))
     s.close()

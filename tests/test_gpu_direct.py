@@ -24,11 +24,13 @@ def _need_gpu():
     P.load()
 
 
-def direct_run(p, M, N, iters, rho=None, form="direct", lam=None):
+def direct_run(p, M, N, iters, rho=None, form="direct", lam=None, factor_pass=0):
     import paper_1811_05571_gb300 as P
     H = torch.from_numpy(p.H_c64()).cuda()
     g = torch.from_numpy(p.g_c64()).cuda()
     s = P.Solver(H, g, M, N, p.lam if lam is None else lam, p.rho if rho is None else rho, form=form)
+    if factor_pass:
+        s.set_option(P.ADMM_OPT_DIR_FACTOR_PASS, factor_pass)
     s.iterate(iters)
     assert s.status() == 0
     return s
@@ -46,15 +48,102 @@ def direct_run(p, M, N, iters, rho=None, form="direct", lam=None):
     (4000, 2400, 2, 2, 30),     # the streamed factor pass with two column blocks (q from the column pass)
 ])
 def test_direct_form_matches_the_oracle(m, n, M, N, iters):
+    """The full-factor-row passes (ADMM_OPT_DIR_FACTOR_PASS 1)."""
     rows = A.balanced_blocks(m, M)
     cols = A.balanced_blocks(n, N)
     assert all(not A.lemma_applies(r1 - r0, c1 - c0) for r0, r1 in rows for c0, c1 in cols)
     p = synth.gaussian_problem(m, n, max(2, n // 32), seed=m + n + M + N + 1)
     rho = _rho_cols(p, N)
     ref = oracle_run(p, M, N, iters, rho=rho)
-    s = direct_run(p, M, N, iters, rho=rho)
-    assert s.info()["factor_form"] == 1
+    s = direct_run(p, M, N, iters, rho=rho, factor_pass=1)
+    info = s.info()
+    assert info["factor_form"] == 1 and info["rows_per_stage"] != 64
     compare_all(s, ref, M, N)
+
+
+def _tile_bytes(n, N):
+    """Bytes of the lower-triangle 64 x 64 tiles of one replica's factors."""
+    total = 0
+    for c0, c1 in A.balanced_blocks(n, N):
+        nt = -(-(c1 - c0) // 64)
+        total += nt * (nt + 1) // 2 * 64 * 64 * 8
+    return total
+
+
+@pytest.mark.parametrize("m,n,M,N,iters,fp", [
+    (1200, 512, 2, 1, 120, 2),   # 512 columns (8 tile panels), forced below the default width
+    (3000, 1500, 2, 1, 40, 0),   # 1500 columns: the default from 1024 on; a ragged last panel of 28
+    (5000, 2100, 2, 1, 40, 0),   # 2100 columns, 33 panels (several rounds of the panel sums)
+    (4000, 2400, 2, 2, 30, 0),   # two column blocks: q from the column pass, the row pass after
+    (3600, 300, 9, 1, 60, 2),    # nine replicas: the update's general path (more than eight)
+    (700, 300, 1, 1, 80, 2),     # the lasso (one block): a panel's update right after its sums
+    (2600, 770, 2, 3, 40, 2),    # ragged column blocks of 257 / 257 / 256
+])
+def test_tile_pass_matches_the_oracle(m, n, M, N, iters, fp):
+    """The lower-triangle tile pass (ADMM_OPT_DIR_FACTOR_PASS 2, the default
+    from 1024 columns): the same iterates as the oracle's direct branch, and
+    exactly the tile bytes per iteration."""
+    p = synth.gaussian_problem(m, n, max(2, n // 32), seed=m + n + M + N + 2)
+    rho = _rho_cols(p, N)
+    ref = oracle_run(p, M, N, iters, rho=rho)
+    s = direct_run(p, M, N, iters, rho=rho, factor_pass=fp)
+    info = s.info()
+    assert info["rows_per_stage"] == 64
+    assert info["factor_bytes"] == M * _tile_bytes(n, N)
+    compare_all(s, ref, M, N)
+
+
+def test_tile_and_row_passes_agree():
+    """The two factor passes compute the same u_b = L_b q_b: after 60
+    iterations of 1100 x 1100 blocks their images agree to FP32 rounding."""
+    p = synth.gaussian_problem(3 * 1100, 1100, 30, seed=60)
+    a = direct_run(p, 3, 1, 60, factor_pass=1)
+    b = direct_run(p, 3, 1, 60, factor_pass=2)
+    va, vb = a.v().cpu().numpy(), b.v().cpu().numpy()
+    assert np.linalg.norm(va - vb) <= 1e-5 * np.linalg.norm(va)
+    ra, rb = a.residuals(60), b.residuals(60)
+    for q in range(5):
+        x, y = np.sqrt(ra[:, q]), np.sqrt(rb[:, q])
+        assert np.max(np.abs(x - y)) <= 1e-4 * np.max(x), q
+
+
+def test_tile_pass_set_rho_restart_and_stop():
+    """A new rho repacks the tiles; a restart from a checkpoint is bit exact
+    (fixed summation order); the stopping test ends where the oracle's does."""
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(2048, 1024, 24, seed=61)
+    s = direct_run(p, 2, 1, 10, rho=1.0)
+    assert s.info()["rows_per_stage"] == 64
+    s.set_rho(2.5)
+    s.reset()
+    s.iterate(60)
+    compare_all(s, oracle_run(p, 2, 1, 60, rho=2.5), 2, 1)
+    k, v, sd, gh = s.state()
+    s.iterate(15)
+    v_straight = s.v().cpu()
+    s.set_state(k, v, sd, None)
+    s.iterate(15)
+    assert s.status() == 0 and torch.equal(s.v().cpu(), v_straight)
+    t = P.Solver(torch.from_numpy(p.H_c64()).cuda(), torch.from_numpy(p.g_c64()).cuda(), 2, 1, p.lam, 1.0,
+                 form="direct")
+    done = t.solve(2000, 1e-5, 1e-4)
+    ref = oracle.run_split(p.H, p.g, 2, 1, p.lam, 1.0, 2000, eps=(1e-5, 1e-4))
+    assert ref.stopped_at is not None and abs(done - ref.stopped_at) <= 2, (done, ref.stopped_at)
+
+
+def test_factor_pass_option_is_checked():
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(512, 128, 4, seed=62)
+    s = direct_run(p, 2, 1, 2)          # 128-column blocks: no tiles
+    with pytest.raises(P.AdmmError) as e:
+        s.set_option(P.ADMM_OPT_DIR_FACTOR_PASS, 2)
+    assert e.value.status == P.ADMM_EUNSUPPORTED
+    with pytest.raises(P.AdmmError) as e:
+        s.set_option(P.ADMM_OPT_DIR_FACTOR_PASS, 3)
+    assert e.value.status == P.ADMM_EINVAL
+    s.set_option(P.ADMM_OPT_DIR_FACTOR_PASS, 1)
+    s.iterate(2)
+    assert s.status() == 0 and s.state()[0] == 4
 
 
 def test_streamed_factor_pass_with_more_items_than_its_chunk_table():
@@ -63,7 +152,7 @@ def test_streamed_factor_pass_with_more_items_than_its_chunk_table():
     their rows in the global chunk counters at once."""
     p = synth.gaussian_problem(80 * 1024, 1024, 16, seed=44)
     ref = oracle_run(p, 80, 1, 3)
-    s = direct_run(p, 80, 1, 3)
+    s = direct_run(p, 80, 1, 3, factor_pass=1)
     info = s.info()
     assert info["rows_per_stage"] == 4 and 5120 > 32 * info["ctas"]
     compare_all(s, ref, 80, 1)
