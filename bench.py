@@ -653,11 +653,13 @@ def direct_form(pkg, stream, dev, barrier, peaks, iters: int = 64) -> dict:
     """The direct factor form on an overdetermined 32768 x 2048 Gaussian
     problem in three splits (every block has m_b >= n_b), and the lemma form on
     the consensus split for comparison.  Per split: one call of `iters`
-    iterations timed with CUDA events on the launching stream, after three
-    warm-up iterations.  Algorithmic bytes per iteration: the passes over H
-    (none with one column block: H_i^H g_i is cached, two otherwise), every
-    factor once, the state v, s read and written, and with one column block
-    the cached H_i^H g_i."""
+    iterations timed with CUDA events on the launching stream, after 19
+    warm-up iterations (which capture both iteration graphs).  Algorithmic
+    bytes per iteration: the passes over H (none with one column block:
+    H_i^H g_i is cached, two otherwise), every factor once (the tile pass: its
+    lower-triangle tiles), the state v, s read and written, and with one
+    column block the cached H_i^H g_i.  The consensus split also runs with the
+    full-factor-row pass (`rows_pass_8x1`)."""
     import torch
     import synth
     c = synth.TALL
@@ -676,7 +678,7 @@ def direct_form(pkg, stream, dev, barrier, peaks, iters: int = 64) -> dict:
         torch.cuda.synchronize()
         setup_ms = (time.perf_counter() - t0) * 1e3
         info = s.info()
-        s.iterate(3)
+        s.iterate(19)   # both iteration graphs (16 and 1) captured before the timed call
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)

@@ -341,7 +341,7 @@ __device__ void finish_record(const DirectArgs& a, long long k, int lane) {
                 else *reinterpret_cast<volatile int*>(a.stop_pending) = 1;
             }
         }
-        __threadfence();
+        // (the next kernel reads the count after this one ends)
         *reinterpret_cast<volatile long long*>(a.k_done) = k + 1;
     }
 }
@@ -438,6 +438,14 @@ __global__ void __launch_bounds__(kDirFacThreads, 2) dir_factor_kernel(const Dir
 // Each tile's two sums are written out and added per row in a fixed order,
 // so the result does not depend on which warp took which tile.
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start before its predecessor in the stream completes;
+// pdl_wait blocks until the predecessor has completed and its writes are
+// visible (a no-op without such a predecessor), pdl_trigger lets the
+// successor start once every CTA of this grid has triggered or exited.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // a slot's piece number, published by the producer before it arms the slot
 __device__ __forceinline__ void st_release_shared(int* p, int v) {
     asm volatile("st.release.cta.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(p)), "r"(v) : "memory");
@@ -470,6 +478,7 @@ __device__ __forceinline__ bool herm_wait_piece(const int* meta, uint64_t* full,
 }
 
 constexpr int kHermPieces = kDirTile / kHermPieceRows;          // pieces per tile
+constexpr int kHermUpdThreads = 256;                             // the update kernel's CTA
 constexpr int kHermPieceBytes = kHermPieceRows * kDirTile * 8;  // 8 KB
 static_assert(kHermSlots % kHermPieces == 0, "a tile's pieces sit in consecutive slots");
 
@@ -481,10 +490,12 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int G = gridDim.x, c = blockIdx.x;
     const int ntile = c < a.ntiles ? (a.ntiles - 1 - c) / G + 1 : 0;   // this CTA's tiles
-    // (a CTA with tiles starts before the iteration's record is written, so
-    // all of its threads read the same stop flag)
-    if (ntile == 0 || stopped(a)) return;
+    if (ntile == 0) return;
+    __shared__ int skip;
     if (threadIdx.x == 0) {
+        // the previous update may still run (programmatic launch): the flag
+        // read here can be stale, so the consumers read it again after their wait
+        skip = stopped(a) ? 1 : 0;
         for (int q = 0; q < kHermSlots; ++q) {
             mbar_init(&full[q], 1);
             mbar_init(&empty[q], 1);
@@ -493,15 +504,21 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
         fence_mbarrier_init();
     }
     __syncthreads();
+    if (skip) return;
     if (warp == kHermWarps) {
-        // producer: piece e = kHermPieces i + h of the CTA's stream into slot e % kHermSlots
+        // producer: piece e = kHermPieces i + h of the CTA's stream into slot e % kHermSlots.
+        // The tiles change only at a factorisation, never inside an iteration,
+        // so the producer streams while the previous update still runs.
         if (lane != 0) return;
         const uint64_t pol = policy_evict_first();   // every tile is read once per iteration
         long long e = 0;
         bool ok = true;
-        for (int i = 0; i < ntile && ok; ++i) {
-            const unsigned char* src = reinterpret_cast<const unsigned char*>(
+        auto tile_src = [&](int i) {
+            return reinterpret_cast<const unsigned char*>(
                 a.Lt + (static_cast<size_t>(c) + static_cast<size_t>(i) * G) * kDirTile * kDirTile);
+        };
+        for (int i = 0; i < ntile && ok; ++i) {
+            const unsigned char* src = tile_src(i);
             for (int h = 0; h < kHermPieces; ++h, ++e) {
                 const int slot = static_cast<int>(e % kHermSlots);
                 const uint32_t use = static_cast<uint32_t>(e / kHermSlots);
@@ -525,6 +542,11 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
                               a.timeout_ns);
         return;
     }
+    // consumers: q_b, the iteration count and the tile sums' buffers belong to
+    // the previous kernel until it completes; then the update may launch
+    pdl_wait();
+    pdl_trigger();
+    const bool live = !stopped(a);   // stopped by the previous update: release the pieces unread
     const long long k = __ldcg(a.k_done);
     const size_t qslot = a.N == 1 ? static_cast<size_t>(k & 1) * a.P * a.npitch : 0;
     // the warp's next tile and its q pairs, fetched one tile ahead
@@ -550,6 +572,11 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
             if (!herm_wait_piece(meta, full, slot, e, a)) {
                 ok = false;
                 break;
+            }
+            if (!live) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[slot]);
+                continue;
             }
             const float4* T4 = reinterpret_cast<const float4*>(hsm + static_cast<size_t>(slot) * kHermPieceBytes);
 #pragma unroll
@@ -583,15 +610,15 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
             if (lane == 0) mbar_arrive(&empty[slot]);
         }
         if (!ok) break;
-        if (!diag)   // the tile's column sums
+        if (live && !diag)   // the tile's column sums
             __stcg(reinterpret_cast<float4*>(a.CP + static_cast<size_t>(t) * kDirTile) + lane,
                    make_float4(c0.x, c0.y, c1.x, c1.y));
     }
 }
 
 // ---- panel sums + update (after the tile pass) ---------------------------------
-// One CTA per update chunk (kDirChunk columns of column block j).  Warp w takes
-// the replicas i = w, w + 8, ...: the chunk's rows of u_b, each the sum of its
+// One CTA per update chunk (kDirChunk columns of column block j), eight
+// warps.  Warp w takes the replicas i = w, w + 8, ...: the chunk's rows of u_b, each the sum of its
 // NT tile sums in tile order (lanes 0-15 the first half of the tiles, 16-31
 // the second, sixteen loads in flight, then the two halves added), kept in
 // shared memory with s_i and, with one column block, H_i^H g_i.  Then v over
@@ -599,10 +626,14 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
 // and the chunk's residual partials (warps in order); the CTA that adds the
 // last chunk writes the iteration's record.  Shared memory: 3 M kDirChunk + kDirChunk
 // complex values.
-__global__ void __launch_bounds__(kDirFacThreads) dir_herm_update_kernel(const DirectArgs a) {
+__global__ void __launch_bounds__(kHermUpdThreads) dir_herm_update_kernel(const DirectArgs a) {
     extern __shared__ float2 hred[];
+    // launched once every tile CTA has seen the previous update complete, so
+    // the stop flag, v, s, H_i^H g_i and the iteration count are current here;
+    // the next tile pass may start streaming right away
     if (stopped(a)) return;
-    constexpr int kWarps = kDirFacThreads / 32;
+    pdl_trigger();
+    constexpr int kWarps = kHermUpdThreads / 32;
     float2* us = hred;                                  // M x kDirChunk: u
     float2* ss = us + a.M * kDirChunk;                  // s before the update
     float2* cs = ss + a.M * kDirChunk;                  // H_i^H g_i (one column block)
@@ -623,14 +654,22 @@ __global__ void __launch_bounds__(kDirFacThreads) dir_herm_update_kernel(const D
     const long long k = __ldcg(a.k_done);
     const int hK = (NT + 1) >> 1;
     const int kb = half ? hK : 0, ke = half ? NT : hK;
+    // v, s_i and H_i^H g_i of the chunk before the tile pass ends
+    const float2 vv = (warp == 0 && half == 0 && inb) ? ldcg2(a.v + col) : make_float2(0.f, 0.f);
+    for (int i = warp; i < a.M; i += kWarps)
+        if (half == 0) {
+            float2 sv = make_float2(0.f, 0.f), cv = sv;
+            if (inb) {
+                sv = ldcg2(a.s + static_cast<size_t>(i) * a.ld + col);
+                if (a.N == 1) cv = ldcg2(a.C + static_cast<size_t>(i) * a.npitch + col);
+            }
+            ss[i * kDirChunk + r] = sv;
+            cs[i * kDirChunk + r] = cv;
+        }
+    pdl_wait();   // the tile sums
     for (int i = warp; i < a.M; i += kWarps) {
         const int p = i * a.N + j;
         const long long tb = a.T_off[p];
-        float2 sv = make_float2(0.f, 0.f), cv = sv;
-        if (half == 0 && inb) {
-            sv = ldcg2(a.s + static_cast<size_t>(i) * a.ld + col);
-            if (a.N == 1) cv = ldcg2(a.C + static_cast<size_t>(i) * a.npitch + col);
-        }
         // the contributions to row row0 + r: tiles (X, kk) for kk <= X (row
         // sums), tiles (kk, X) for kk > X (column sums)
         float2 acc = make_float2(0.f, 0.f);
@@ -653,8 +692,6 @@ __global__ void __launch_bounds__(kDirFacThreads) dir_herm_update_kernel(const D
         acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 16);
         if (half == 0) {
             us[i * kDirChunk + r] = acc;
-            ss[i * kDirChunk + r] = sv;
-            cs[i * kDirChunk + r] = cv;
             if (inb) stcg2(a.u + static_cast<size_t>(i) * a.ld + col, acc);
         }
     }
@@ -666,7 +703,6 @@ __global__ void __launch_bounds__(kDirFacThreads) dir_herm_update_kernel(const D
             sum.x += us[i * kDirChunk + r].x + ss[i * kDirChunk + r].x;
             sum.y += us[i * kDirChunk + r].y + ss[i * kDirChunk + r].y;
         }
-        const float2 vv = ldcg2(a.v + col);
         const float2 vn = shrink(make_float2(sum.x * a.inv_M, sum.y * a.inv_M), a.kappa);
         d[1] = sq2(make_float2(vn.x - vv.x, vn.y - vv.y));
         d[3] = sq2(vn);
@@ -1150,10 +1186,25 @@ cudaError_t launch_pack_herm(const float2* L, const long long* L_off, const int*
 
 cudaError_t launch_dir_factor(const DirectArgs& a, cudaStream_t s) {
     if (a.fac_herm) {
-        dir_herm_tile_kernel<<<a.herm_ctas, (kHermWarps + 1) * 32, herm_smem_bytes(), s>>>(a);
-        const cudaError_t e = cudaGetLastError();
+        // both with programmatic stream serialization: each may start while
+        // its predecessor finishes (the kernels wait where they need to)
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(a.herm_ctas);
+        cfg.blockDim = dim3((kHermWarps + 1) * 32);
+        cfg.dynamicSmemBytes = herm_smem_bytes();
+        cfg.stream = s;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        cudaError_t e = cudaLaunchKernelEx(&cfg, dir_herm_tile_kernel, a);
         if (e != cudaSuccess) return e;
-        dir_herm_update_kernel<<<a.nchunks, kDirFacThreads, herm_update_smem(a.M), s>>>(a);
+        cfg.gridDim = dim3(a.nchunks);
+        cfg.blockDim = dim3(kHermUpdThreads);
+        cfg.dynamicSmemBytes = herm_update_smem(a.M);
+        e = cudaLaunchKernelEx(&cfg, dir_herm_update_kernel, a);
+        if (e != cudaSuccess) return e;
     } else if (a.fac_stream) {
         const size_t smem = stream_smem(a.fac_ns, a.fac_stage);
         dir_factor_stream_kernel<<<a.fac_ctas, (kDirBulkWarps + 1) * 32, smem, s>>>(a);
