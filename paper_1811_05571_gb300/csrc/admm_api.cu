@@ -40,6 +40,7 @@ struct DirectState {
     float2 *Lt = nullptr, *RP = nullptr, *CP = nullptr;
     long long* T_off = nullptr;    // P + 1
     int4* T_seq = nullptr;         // ntiles: the pass order, {index, p, I, J}
+    long long* dctl = nullptr;     // 4: the deferred record's counters (one column block)
     long long ntiles = 0;
     int herm_ctas = 0;
     int64_t bytes = 0;
@@ -161,7 +162,7 @@ void free_all(admm_t* h) {
         if (p) cudaFree(p);
     DirectState& d = h->dir;
     void* dptrs[] = {d.C, d.Q, d.part, d.cnt, d.ints, d.L_off, d.res_chunk, d.stop_pending,
-                     d.Lt, d.RP, d.CP, d.T_off, d.T_seq};
+                     d.Lt, d.RP, d.CP, d.T_off, d.T_seq, d.dctl};
     for (void* p : dptrs)
         if (p) cudaFree(p);
     if (d.g1) cudaGraphExecDestroy(d.g1);
@@ -759,7 +760,8 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
         ok = dalloc(&d.Lt, static_cast<size_t>(d.ntiles) * tile) == cudaSuccess &&
              dalloc(&d.RP, static_cast<size_t>(d.ntiles) * admm::kDirTile) == cudaSuccess &&
              dalloc(&d.CP, static_cast<size_t>(d.ntiles) * admm::kDirTile) == cudaSuccess &&
-             dalloc(&d.T_off, toff.size()) == cudaSuccess && dalloc(&d.T_seq, seq.size()) == cudaSuccess;
+             dalloc(&d.T_off, toff.size()) == cudaSuccess && dalloc(&d.T_seq, seq.size()) == cudaSuccess &&
+             dalloc(&d.dctl, 4) == cudaSuccess;
         int per_sm = 0;
         if (ok && (admm::herm_per_sm(&per_sm) != cudaSuccess || per_sm < 1)) {
             cudaGetLastError();
@@ -769,6 +771,7 @@ int alloc_direct(admm_t* h, const std::vector<long long>& off, const std::vector
         if (ok && d.herm) {
             CK(h, cudaMemcpy(d.T_off, toff.data(), toff.size() * sizeof(long long), cudaMemcpyHostToDevice));
             CK(h, cudaMemcpy(d.T_seq, seq.data(), seq.size() * sizeof(int4), cudaMemcpyHostToDevice));
+            CK(h, cudaMemset(d.dctl, 0, 4 * sizeof(long long)));
         }
     }
     if (!ok) return ADMM_ENOMEM;
@@ -840,6 +843,8 @@ admm::DirectArgs direct_args(admm_t* h, int check_stop, double eps_abs, double e
     a.CP = d.CP;
     a.ntiles = static_cast<int>(d.ntiles);
     a.herm_ctas = d.herm_ctas;
+    a.defer_record = a.fac_herm && h->N == 1 ? 1 : 0;
+    a.dctl = d.dctl;
     a.timeout_ns = h->timeout_ns;
     a.frows = d.frows;
     a.hrows = d.hrows;
@@ -895,6 +900,11 @@ int run_direct(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
             d.q_valid = true;
         }
     }
+    if (a.defer_record) {
+        // the tile pass counts from the recorded iterations, nothing pending
+        CK(h, cudaMemcpyAsync(d.dctl, h->k_done, sizeof(long long), cudaMemcpyDeviceToDevice, st));
+        CK(h, cudaMemsetAsync(d.dctl + 2, 0, sizeof(long long), st));
+    }
     const double key[7] = {h->rho, h->lambda, static_cast<double>(check_stop), eps_abs, eps_rel,
                            static_cast<double>(h->hist_cap), static_cast<double>(h->timeout_ns)};
     if (!d.key_set || std::memcmp(key, d.key, sizeof key) != 0 || d.key_hist != h->hist) {
@@ -915,6 +925,7 @@ int run_direct(admm_t* h, int iters, int check_stop, double eps_abs, double eps_
                 if (e == cudaSuccess) e = admm::launch_dir_rows(a, d.cap);
             }
         }
+        if (e == cudaSuccess && a.defer_record) e = admm::launch_dir_record(a, d.cap);
         cudaGraph_t graph = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(d.cap, &graph);
         if (e == cudaSuccess) e = e2;

@@ -546,8 +546,22 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
     // the previous kernel until it completes; then the update may launch
     pdl_wait();
     pdl_trigger();
+    long long k;
+    if (a.defer_record) {
+        k = __ldcg(a.dctl);
+        if (c == 0 && warp == 0) {
+            // the record of the previous iteration (its partials are in), and
+            // the iteration number for the update
+            if (lane == 0) a.dctl[1] = k;
+            if (__ldcg(a.dctl + 2) != 0) {
+                finish_record(a, k - 1, lane);
+                if (lane == 0) a.dctl[2] = 0;
+            }
+        }
+    } else {
+        k = __ldcg(a.k_done);
+    }
     const bool live = !stopped(a);   // stopped by the previous update: release the pieces unread
-    const long long k = __ldcg(a.k_done);
     const size_t qslot = a.N == 1 ? static_cast<size_t>(k & 1) * a.P * a.npitch : 0;
     // the warp's next tile and its q pairs, fetched one tile ahead
     int4 tn = make_int4(0, 0, 0, 0);
@@ -629,9 +643,10 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
 __global__ void __launch_bounds__(kHermUpdThreads) dir_herm_update_kernel(const DirectArgs a) {
     extern __shared__ float2 hred[];
     // launched once every tile CTA has seen the previous update complete, so
-    // the stop flag, v, s, H_i^H g_i and the iteration count are current here;
-    // the next tile pass may start streaming right away
-    if (stopped(a)) return;
+    // v, s and H_i^H g_i are current here (and, unless the record is deferred
+    // to the tile pass, the stop flag); the next tile pass may start
+    // streaming right away
+    if (!a.defer_record && stopped(a)) return;
     pdl_trigger();
     constexpr int kWarps = kHermUpdThreads / 32;
     float2* us = hred;                                  // M x kDirChunk: u
@@ -651,7 +666,6 @@ __global__ void __launch_bounds__(kHermUpdThreads) dir_herm_update_kernel(const 
     const int r = lane & (kDirChunk - 1), half = lane >> 4;
     const bool inb = row0 + r < nj;
     const int col = c0 + row0 + r;
-    const long long k = __ldcg(a.k_done);
     const int hK = (NT + 1) >> 1;
     const int kb = half ? hK : 0, ke = half ? NT : hK;
     // v, s_i and H_i^H g_i of the chunk before the tile pass ends
@@ -666,7 +680,9 @@ __global__ void __launch_bounds__(kHermUpdThreads) dir_herm_update_kernel(const 
             ss[i * kDirChunk + r] = sv;
             cs[i * kDirChunk + r] = cv;
         }
-    pdl_wait();   // the tile sums
+    pdl_wait();   // the tile sums (and a deferred record, with its stop flag)
+    if (a.defer_record && stopped(a)) return;
+    const long long k = a.defer_record ? __ldcg(a.dctl + 1) : __ldcg(a.k_done);
     for (int i = warp; i < a.M; i += kWarps) {
         const int p = i * a.N + j;
         const long long tb = a.T_off[p];
@@ -740,11 +756,26 @@ __global__ void __launch_bounds__(kHermUpdThreads) dir_herm_update_kernel(const 
             for (int w = 0; w < kWarps; ++w) t += static_cast<double>(dred[w][q]);
             __stcg(a.res_chunk + static_cast<size_t>(chunk) * 5 + q, t);
         }
-        __threadfence();
-        last = atomicAdd(a.cnt_glob, 1u) == static_cast<unsigned>(a.nchunks - 1);
+        if (a.defer_record) {
+            // every CTA writes the same values; the next tile pass reads them
+            // after this grid ends
+            a.dctl[0] = k + 1;
+            a.dctl[2] = 1;
+            last = 0;
+        } else {
+            __threadfence();
+            last = atomicAdd(a.cnt_glob, 1u) == static_cast<unsigned>(a.nchunks - 1);
+        }
     }
     __syncthreads();
     if (last && warp == 0) finish_record(a, k, lane);
+}
+
+// the record left pending by the last update of a launch sequence
+__global__ void dir_record_kernel(const DirectArgs a) {
+    if (__ldcg(a.dctl + 2) == 0) return;
+    finish_record(a, __ldcg(a.dctl) - 1, threadIdx.x & 31);
+    if (threadIdx.x == 0) a.dctl[2] = 0;
 }
 
 // the tiles of the pass, in its order, from the full factors (setup, after
@@ -1211,6 +1242,11 @@ cudaError_t launch_dir_factor(const DirectArgs& a, cudaStream_t s) {
     } else {
         dir_factor_kernel<<<a.ctas, kDirFacThreads, 0, s>>>(a);
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_dir_record(const DirectArgs& a, cudaStream_t s) {
+    dir_record_kernel<<<1, 32, 0, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -330,6 +330,14 @@ struct DirectArgs {
     float2* CP;               // ntiles x kDirTile, by index: column sums L_IJ^H q_I (J < I)
     int ntiles;
     int herm_ctas;            // CTAs of the tile pass (one per SM)
+    // One column block: the record of iteration k is written by the next tile
+    // pass (or by the record kernel that ends a launch sequence), not by the
+    // update's last CTA.  dctl[0]: iterations updated (written by the update,
+    // read by the tile pass), dctl[1]: the iteration the tile pass summed
+    // (written by the tile pass, read by the update), dctl[2]: a record is
+    // pending.  No kernel reads a counter its own grid writes.
+    int defer_record;
+    long long* dctl;
     int check_stop;
     double eps_abs, eps_rel;
     float rho, kappa, inv_M;
@@ -341,6 +349,8 @@ cudaError_t launch_dir_cols(const DirectArgs& a, int mode, cudaStream_t s);
 // Q[slot of the device iteration count] = C + rho z (one column block)
 cudaError_t launch_dir_q(const DirectArgs& a, cudaStream_t s);
 cudaError_t launch_dir_factor(const DirectArgs& a, cudaStream_t s);
+// the pending record of the last iteration (defer_record), one warp
+cudaError_t launch_dir_record(const DirectArgs& a, cudaStream_t s);
 cudaError_t launch_dir_rows(const DirectArgs& a, cudaStream_t s);
 // the tiles of the tile pass from the full factors (the parts of a tile past n_j zero)
 cudaError_t launch_pack_herm(const float2* L, const long long* L_off, const int* L_pitch, const int* col_off,
