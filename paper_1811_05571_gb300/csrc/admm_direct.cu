@@ -563,20 +563,25 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
     }
     const bool live = !stopped(a);   // stopped by the previous update: release the pieces unread
     const size_t qslot = a.N == 1 ? static_cast<size_t>(k & 1) * a.P * a.npitch : 0;
-    // the warp's next tile and its q pairs, fetched one tile ahead
-    int4 tn = make_int4(0, 0, 0, 0);
+    // the warp's next tile and its q pairs, fetched one tile ahead, and the
+    // table entry of the tile after it two tiles ahead (the q loads depend on it)
+    auto entry = [&](int i) {
+        return i < ntile ? __ldg(a.T_seq + c + static_cast<long long>(i) * G) : make_int4(0, 0, 0, 0);
+    };
+    int4 tn = entry(warp), tn2 = entry(warp + kHermWarps);
     float4 nqJ = make_float4(0.f, 0.f, 0.f, 0.f), nqI = nqJ;
-    auto fetch = [&](int i) {
-        tn = __ldg(a.T_seq + c + static_cast<long long>(i) * G);
+    auto fetch = [&]() {
         const float2* qb = a.Q + qslot + static_cast<size_t>(tn.y) * a.npitch;
         nqJ = __ldg(reinterpret_cast<const float4*>(qb + tn.w * kDirTile) + lane);
         nqI = __ldg(reinterpret_cast<const float4*>(qb + tn.z * kDirTile) + lane);
     };
-    if (warp < ntile) fetch(warp);
+    if (warp < ntile) fetch();
     for (int i = warp; i < ntile; i += kHermWarps) {
         const int t = tn.x, I = tn.z, J = tn.w;
         const float4 qJ = nqJ, qI = nqI;
-        if (i + kHermWarps < ntile) fetch(i + kHermWarps);
+        tn = tn2;
+        tn2 = entry(i + 2 * kHermWarps);
+        if (i + kHermWarps < ntile) fetch();
         const bool diag = I == J;
         float2 c0 = make_float2(0.f, 0.f), c1 = make_float2(0.f, 0.f);
         bool ok = true;
@@ -680,12 +685,13 @@ __global__ void __launch_bounds__(kHermUpdThreads) dir_herm_update_kernel(const 
             ss[i * kDirChunk + r] = sv;
             cs[i * kDirChunk + r] = cv;
         }
+    // the first replica's tile offset (constant) before the wait
+    long long tb = warp < a.M ? __ldg(a.T_off + warp * a.N + j) : 0;
     pdl_wait();   // the tile sums (and a deferred record, with its stop flag)
     if (a.defer_record && stopped(a)) return;
     const long long k = a.defer_record ? __ldcg(a.dctl + 1) : __ldcg(a.k_done);
     for (int i = warp; i < a.M; i += kWarps) {
-        const int p = i * a.N + j;
-        const long long tb = a.T_off[p];
+        if (i != warp) tb = __ldg(a.T_off + i * a.N + j);
         // the contributions to row row0 + r: tiles (X, kk) for kk <= X (row
         // sums), tiles (kk, X) for kk > X (column sums)
         float2 acc = make_float2(0.f, 0.f);
