@@ -275,3 +275,42 @@ def test_lambda_zero_is_least_squares():
     x_ls = np.linalg.lstsq(p.H, p.g, rcond=None)[0]
     v = s.v().cpu().numpy().astype(np.complex128)
     assert np.linalg.norm(v - x_ls) <= 1e-4 * np.linalg.norm(x_ls)
+
+
+def test_tile_pass_solve_with_two_column_blocks():
+    """With several column blocks the tile pass's update keeps the record and
+    the row pass turns the stopping decision into the stop flag: a solve on
+    2 x 2 blocks of 1024 x 512 (the tile pass forced) ends where the
+    oracle's does."""
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(2048, 1024, 24, seed=63)
+    rho = _rho_cols(p, 2)
+    s = P.Solver(torch.from_numpy(p.H_c64()).cuda(), torch.from_numpy(p.g_c64()).cuda(), 2, 2, p.lam, rho,
+                 form="direct")
+    s.set_option(P.ADMM_OPT_DIR_FACTOR_PASS, 2)
+    assert s.info()["rows_per_stage"] == 64
+    done = s.solve(3000, 1e-5, 1e-4)
+    ref = oracle.run_split(p.H, p.g, 2, 2, p.lam, rho, 3000, eps=(1e-5, 1e-4))
+    assert ref.stopped_at is not None and abs(done - ref.stopped_at) <= 2, (done, ref.stopped_at)
+    assert A.stop_test(s.residuals(1)[0], 2 * p.n, rho, 1e-5, 1e-4)
+
+
+def test_tile_pass_new_data_vector_and_pass_switch():
+    """admm_set_g replaces the cached H_i^H g_i under the tile pass; switching
+    between the tile pass and the full-row pass mid-run continues the same
+    iteration (the deferred record and the iteration count carry over)."""
+    import paper_1811_05571_gb300 as P
+    p = synth.gaussian_problem(3600, 1100, 30, seed=64)
+    q = synth.gaussian_problem(3600, 1100, 30, seed=65)
+    s = direct_run(p, 3, 1, 10)
+    assert s.info()["rows_per_stage"] == 64
+    s.set_g(torch.from_numpy(q.g_c64()).cuda())
+    s.reset()
+    s.iterate(17)                                   # one 16-graph and one 1-graph on the tile pass
+    s.set_option(P.ADMM_OPT_DIR_FACTOR_PASS, 1)
+    s.iterate(20)                                   # full rows
+    s.set_option(P.ADMM_OPT_DIR_FACTOR_PASS, 2)
+    s.iterate(23)                                   # tiles again
+    assert s.status() == 0 and s.state()[0] == 60
+    ref = oracle.run_split(p.H, q.g, 3, 1, p.lam, p.rho, 60)
+    compare_all(s, ref, 3, 1)
