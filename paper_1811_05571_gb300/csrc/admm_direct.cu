@@ -480,6 +480,8 @@ __device__ __forceinline__ bool herm_wait_piece(const int* meta, uint64_t* full,
 constexpr int kHermPieces = kDirTile / kHermPieceRows;          // pieces per tile
 constexpr int kHermUpdThreads = 256;                             // the update kernel's CTA
 constexpr int kHermPieceBytes = kHermPieceRows * kDirTile * 8;  // 8 KB
+constexpr int kHermCopyBytes = kHermPieceBytes < 8192 ? kHermPieceBytes : 8192;   // bytes per bulk copy
+static_assert(kHermPieceBytes % kHermCopyBytes == 0, "whole copies per piece");
 static_assert(kHermSlots % kHermPieces == 0, "a tile's pieces sit in consecutive slots");
 
 __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel(const DirectArgs a) {
@@ -530,9 +532,9 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
                 mbar_arrive_expect_tx(&full[slot], static_cast<uint32_t>(kHermPieceBytes));
                 unsigned char* dst = hsm + static_cast<size_t>(slot) * kHermPieceBytes;
                 const unsigned char* sp = src + static_cast<size_t>(h) * kHermPieceBytes;
-                bulk_load_hint(dst, sp, kHermPieceBytes / 2, &full[slot], pol);
-                bulk_load_hint(dst + kHermPieceBytes / 2, sp + kHermPieceBytes / 2, kHermPieceBytes / 2, &full[slot],
-                               pol);
+#pragma unroll
+                for (int o = 0; o < kHermPieceBytes; o += kHermCopyBytes)
+                    bulk_load_hint(dst + o, sp + o, kHermCopyBytes, &full[slot], pol);
             }
         }
         // every copy into this CTA's shared memory lands before the CTA ends
