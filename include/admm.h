@@ -57,7 +57,7 @@ extern "C" {
 #define ADMM_ENOTPD        4  /* a factor rho I + H_b H_b^H was not positive definite in FP64 */
 #define ADMM_ENONFINITE    5  /* H or g holds NaN or Inf */
 #define ADMM_ETIMEOUT      6  /* a bounded in-kernel wait expired; the iteration state is undefined */
-#define ADMM_EUNSUPPORTED  7  /* a valid problem this build does not run (see admm_setup) */
+#define ADMM_EUNSUPPORTED  7  /* a valid problem this library does not run (see admm_setup) */
 #define ADMM_EDIVERGED     8  /* the iterates became NaN or Inf */
 
 /* element type of H and g in admm_setup / admm_set_g */
@@ -190,8 +190,9 @@ int admm_partition(int64_t total, int32_t parts, int64_t* offsets);
  * estimated data of every block), out[2] = N m / M + 2 n / N (both; may be
  * fractional).  All three are written whatever the split, so callers can
  * compare them (Section IV-B).  Host only, no GPU needed.  ADMM_EINVAL unless
- * m, n >= 1, 1 <= row_blocks, 1 <= col_blocks and out != NULL.  This build
- * runs every block on one GPU and exchanges nothing between nodes. */
+ * m, n >= 1, 1 <= row_blocks, 1 <= col_blocks and out != NULL.  The counts
+ * are the paper's; a handle runs every block on one GPU and exchanges nothing
+ * between nodes (the admm_shard_* calls exchange between ranks). */
 int admm_comm_elements(int64_t m, int64_t n, int32_t row_blocks, int32_t col_blocks, double* out);
 
 /* Plan of the persistent iteration kernel for an m x n problem split into
