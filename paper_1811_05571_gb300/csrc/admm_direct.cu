@@ -639,14 +639,16 @@ __global__ void __launch_bounds__((kHermWarps + 1) * 32, 1) dir_herm_tile_kernel
 
 // ---- panel sums + update (after the tile pass) ---------------------------------
 // One CTA per update chunk (kDirChunk columns of column block j), eight
-// warps.  Warp w takes the replicas i = w, w + 8, ...: the chunk's rows of u_b, each the sum of its
-// NT tile sums in tile order (lanes 0-15 the first half of the tiles, 16-31
-// the second, sixteen loads in flight, then the two halves added), kept in
-// shared memory with s_i and, with one column block, H_i^H g_i.  Then v over
-// the chunk (warp 0, replicas in order), the duals and the next q per replica,
-// and the chunk's residual partials (warps in order); the CTA that adds the
-// last chunk writes the iteration's record.  Shared memory: 3 M kDirChunk + kDirChunk
-// complex values.
+// warps.  Warp w takes the replicas i = w, w + 8, ...: the chunk's rows of
+// u_b, each the sum of its NT tile sums in tile order (lanes 0-15 the first
+// half of the tiles, 16-31 the second, sixteen loads in flight, then the two
+// halves added), kept in shared memory with s_i and, with one column block,
+// H_i^H g_i.  Then v over the chunk (warp 0, replicas in order), the duals
+// and the next q per replica, and the chunk's residual partials (warps in
+// order).  With several column blocks the CTA that adds the last chunk writes
+// the iteration's record; with one (defer_record) the next tile pass or the
+// record kernel writes it.  Shared memory: 3 M kDirChunk + kDirChunk complex
+// values.
 __global__ void __launch_bounds__(kHermUpdThreads) dir_herm_update_kernel(const DirectArgs a) {
     extern __shared__ float2 hred[];
     // launched once every tile CTA has seen the previous update complete, so
