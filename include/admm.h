@@ -87,13 +87,14 @@ extern "C" {
                                      0 turns recording off.  Resets the state. */
 #define ADMM_OPT_DIR_FACTOR_PASS 9  /* direct form: how u_b = L_b q_b reads the factors.  2: the
                                      lower triangle of the Hermitian L_b only, in 64 x 64 tiles
-                                     (about half the bytes; blocks of 256 columns and more, else
-                                     ADMM_EUNSUPPORTED): each tile adds L_IJ q_J to the rows of
-                                     panel I and, below the diagonal, L_IJ^H q_I to those of panel
-                                     J, summed per row in a fixed order; 1: full factor rows (plain
-                                     loads, or bulk copies for blocks of 1024-2048 columns); 0 (the
-                                     default): 2 for blocks of 1024 columns and more, else 1.  The
-                                     lemma form ignores it. */
+                                     (about half the bytes; blocks of 256 columns and more and at
+                                     most 512 row blocks, else ADMM_EUNSUPPORTED): each tile adds
+                                     L_IJ q_J to the rows of panel I and, below the diagonal,
+                                     L_IJ^H q_I to those of panel J, summed per row in a fixed
+                                     order; 1: full factor rows (plain loads, or bulk copies for
+                                     blocks of 1024-2048 columns); 0 (the default): 2 for blocks
+                                     of 1024 columns and more, else 1.  The lemma form ignores
+                                     it. */
 #define ADMM_OPT_H_FP16        6  /* 1: stream an FP16 copy of H (half the bytes per pass);
                                      0: stream the complex64 H (the default).  The first 1
                                      builds the copy: every 64-row group g of H gets the scale

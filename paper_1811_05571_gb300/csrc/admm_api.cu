@@ -1729,8 +1729,9 @@ int admm_set_option(admm_t* h, int32_t option, int64_t value) {
             if (value < 0 || value > 2) return fail(h, ADMM_EINVAL, "ADMM_OPT_DIR_FACTOR_PASS takes 0, 1 or 2");
             if (h->form != ADMM_FORM_DIRECT) return ADMM_OK;   // the lemma form has no factor pass
             if (value == 2 && !h->dir.herm)
-                return fail(h, ADMM_EUNSUPPORTED, "the tile pass needs blocks of %d columns or more",
-                            admm::kDirHermMinCols);
+                return fail(h, ADMM_EUNSUPPORTED,
+                            "the tile pass needs blocks of %d columns or more and at most %d row blocks",
+                            admm::kDirHermMinCols, admm::kDirHermMaxRowBlocks);
             if (h->dir.pass != static_cast<int>(value)) {
                 CK(h, cudaStreamSynchronize(h->dir.cap));
                 drop_direct_graphs(h->dir);
